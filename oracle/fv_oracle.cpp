@@ -1,0 +1,917 @@
+// FP64 CPU oracle of the second-order well-balanced path-conservative finite
+// volume scheme for the reduced Baer-Nunziato model (Gaburro, Castro, Dumbser,
+// "A well balanced diffuse interface method for complex nonhydrostatic free
+// surface flows").
+//
+// TEST INFRASTRUCTURE ONLY.  This file is the slow, plain reference that the
+// CUDA library is checked against.  It is called by the tests, by the smoke
+// check and by the timed CPU baseline, never by the product path, and it shares
+// no code, header, table or constant with the CUDA sources.
+//
+// Everything is plain double arithmetic following the paper's formulas in the
+// paper's order:
+//   * model, fluxes f, g and non-conservative matrices B1, B2:  Section 2.1,
+//     Eq. (ReducedBNmodel_nc), Eq. (BNsimplified_genForm);
+//   * Jacobians A1, A2 and the printed eigenstructure R, Lambda, R^-1: Section 3
+//     (matrices after Eq. (PC));
+//   * D+- fluctuations: Eq. (FIrstOrderDgeneric_x), Eq. (FIrstOrderDgeneric_y);
+//   * x faces: Osher viscosity with 3-point Gauss-Legendre on the segment path,
+//     Eq. (OsherMatrixFormal_approx), b4x = u_bar Delta alpha, Eq. (b_4^x);
+//   * y faces: well-balanced path Eq. (path), b4y Eq. (b_4^y), b3y Eq.
+//     (b^y_3_final), Osher-Romberg viscosity Eq. (ViscosityOR) with the Romberg
+//     nodes and weights of Eq. (RombergWeights);
+//   * reconstruction of fluctuations, Eqs. (FinalReconstruction2),
+//     (FluctuationForRec2), (reconstruction_fluctuation2), Barth-Jespersen
+//     limiter, half-step time derivative and Eq. (gradientEq+fluct);
+//   * cell-interior integral, Eq. (b^y_3_final_integral);
+//   * order switch alpha <= 10 eps (end of Section 3.4);
+//   * free-surface detector, Eq. (Free_surf_detector);
+//   * scheme, Eq. (Scheme).
+// Readings taken where the paper is silent or garbled (all gamma = 1):
+//   R-b3    the pressure part of b3 is the derivative of the product,
+//           d/ds (Phi_alpha Phi_p), with the exact equilibrium part removed:
+//           Delta(aE pf + af pE + af pf);
+//   R-int   at second order the interior integral carries the conservative
+//           part f(q_E) - f(q_W), g(q_N) - g(q_S) besides B grad q;
+//   R-dt    dt/dt-sign: dQ/dt = -(A1 dQ/dx + A2 dQ/dy);
+//   R-det   y0_i = y_L + dy * K_i, K_i = round(sum_j w_ij), w = 1 in solid
+//           cells and clamp((alpha - eps)/(1 - eps), 0, 1) in fluid cells;
+//           each w is first rounded to a multiple of 2^-32 so the column sum
+//           is exact; round half away from zero;
+//   R-eq    the stationary state of cell T_ij is Q^E_ij(y) = (alpha^E rho^E(y),
+//           0, 0, alpha^E) with alpha^E = alpha_ij (constant, the cell's own
+//           volume fraction, as in the equilibrium family u = 0, alpha = const)
+//           and rho^E(y) = rho0 exp(-g rho0 (y - y0_i)/k0) from the column's
+//           detected level; point values at centres, faces and path nodes;
+//           across a face whose two cells carry different alpha^E, b3 keeps the
+//           equilibrium part Delta(alpha^E p^E) of d/ds(Phi_alpha Phi_p);
+//   R-nb    neighbours' fluctuations use the cell's own column level K_i;
+//   R-bj    central slopes, min/max over the 3x3 stencil, tests at the 4 face
+//           midpoints; one limiter value Psi_ij per cell, the smallest of the
+//           conserved components' Barth-Jespersen factors;
+//   R-vel   u_bar in b4x and v_bar in b4y are the segment-path averages of the
+//           velocity taken with the quadrature of the viscosity: Gauss-Legendre
+//           average of u(Phi(s_k)) in x; in y, v(Phi(s_k)) on each Romberg
+//           sub-interval and the Romberg combination on the whole face (the
+//           printed sqrt(rho)-weighted Roe average loses the upwinding of
+//           alpha at the liquid-gas interface);
+//   R-pos   a cell whose reconstructed states at t^{n+1/2} (four face midpoints
+//           and barycentre) are not admissible (alpha <= 0 or alpha rho <= 0)
+//           is advanced at first order, like the alpha <= 10 eps switch;
+//   R-wall  a wall face sees the mirror (normal momentum negated) of the
+//           interior face state; a wall/solid edge neighbour in the
+//           reconstruction is the mirror of the cell's fluctuation; solid or
+//           outside diagonal neighbours are left out of the min/max;
+//   R-cfl   dt = CFL / max over fluid cells of (|u|+c)/dx + (|v|+c)/dy;
+//   R-sw    a cell with alpha <= 10 eps gets Psi = 0 and dQ/dt = 0;
+//   R-sign  sign(0) = 0.
+//
+// Parity-pinned by the tests listed next to each C entry point.
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+#include <map>
+#include <utility>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Model parameters (Section 2; Section 5 preamble for rho0, eps).
+// ---------------------------------------------------------------------------
+struct Model {
+  double rho0, k0, gamma, g, eps;
+};
+
+// Tait equation of state, Eq. (TaitLaw), with gamma = 1.
+double pressure(const Model& M, double rho) { return M.k0 * (rho / M.rho0 - 1.0); }
+
+// c^2 = gamma k0 / rho0 (rho/rho0)^(gamma-1)  (after Eq. (PC)); gamma = 1.
+double sound2(const Model& M, double /*rho*/) { return M.gamma * M.k0 / M.rho0; }
+
+struct Prim {
+  double rho, u, v, p, c2, c, a;
+};
+
+Prim prim(const Model& M, const double q[4]) {
+  Prim w;
+  w.a = q[3];
+  w.rho = q[0] / q[3];
+  w.u = q[1] / q[0];
+  w.v = q[2] / q[0];
+  w.p = pressure(M, w.rho);
+  w.c2 = sound2(M, w.rho);
+  w.c = std::sqrt(w.c2);
+  return w;
+}
+
+// Physical fluxes of Eq. (BNsimplified_genForm); the 5th (potential y) entry is 0.
+void flux_f(const Model& M, const double q[4], double out[5]) {
+  Prim w = prim(M, q);
+  out[0] = q[1];
+  out[1] = q[1] * w.u + w.a * w.p;
+  out[2] = q[1] * w.v;
+  out[3] = 0.0;
+  out[4] = 0.0;
+}
+
+void flux_g(const Model& M, const double q[4], double out[5]) {
+  Prim w = prim(M, q);
+  out[0] = q[2];
+  out[1] = q[1] * w.v;
+  out[2] = q[2] * w.v;
+  out[3] = 0.0;
+  out[4] = 0.0;
+}
+
+// Jacobians A1 = df/dQ + B1, A2 = dg/dQ + B2 of the augmented system.
+void jacobian_A1(const Model& M, const double q[4], double A[5][5]) {
+  Prim w = prim(M, q);
+  std::memset(A, 0, sizeof(double) * 25);
+  A[0][1] = 1.0;
+  A[1][0] = w.c2 - w.u * w.u;  A[1][1] = 2.0 * w.u;  A[1][3] = w.p - w.rho * w.c2;
+  A[2][0] = -w.u * w.v;        A[2][1] = w.v;        A[2][2] = w.u;
+  A[3][3] = w.u;
+}
+
+void jacobian_A2(const Model& M, const double q[4], double A[5][5]) {
+  Prim w = prim(M, q);
+  std::memset(A, 0, sizeof(double) * 25);
+  A[0][2] = 1.0;
+  A[1][0] = -w.u * w.v;        A[1][1] = w.v;        A[1][2] = w.u;
+  A[2][0] = w.c2 - w.v * w.v;  A[2][2] = 2.0 * w.v;  A[2][3] = w.p - w.rho * w.c2;
+  A[2][4] = w.a * w.rho * M.g;
+  A[3][3] = w.v;
+}
+
+// Printed eigenstructure of A1 (right eigenvectors, eigenvalues, inverse).
+void eigen_x(const Model& M, const double q[4], double R[5][5], double L[5], double Ri[5][5]) {
+  Prim w = prim(M, q);
+  const double c = w.c, c2 = w.c2, k = w.rho * c2 - w.p;
+  double r[5][5] = {
+      {1.0, 0.0, k, 0.0, 1.0},
+      {w.u - c, 0.0, w.u * k, 0.0, w.u + c},
+      {w.v, 1.0, 0.0, 0.0, w.v},
+      {0.0, 0.0, c2, 0.0, 0.0},
+      {0.0, 0.0, 0.0, 1.0, 0.0}};
+  double ri[5][5] = {
+      {0.5 * (c + w.u) / c, -1.0 / (2.0 * c), 0.0, -0.5 * k / c2, 0.0},
+      {-w.v, 0.0, 1.0, w.v * k / c2, 0.0},
+      {0.0, 0.0, 0.0, 1.0 / c2, 0.0},
+      {0.0, 0.0, 0.0, 0.0, 1.0},
+      {0.5 * (c - w.u) / c, 1.0 / (2.0 * c), 0.0, -0.5 * k / c2, 0.0}};
+  std::memcpy(R, r, sizeof r);
+  std::memcpy(Ri, ri, sizeof ri);
+  L[0] = w.u - c; L[1] = w.u; L[2] = w.u; L[3] = 0.0; L[4] = w.u + c;
+}
+
+// Printed eigenstructure of A2.
+void eigen_y(const Model& M, const double q[4], double R[5][5], double L[5], double Ri[5][5]) {
+  Prim w = prim(M, q);
+  const double c = w.c, c2 = w.c2, k = w.rho * c2 - w.p, arg = w.a * w.rho * M.g;
+  double r[5][5] = {
+      {1.0, 0.0, k, arg, 1.0},
+      {w.u, 1.0, 0.0, w.u * arg, w.u},
+      {w.v - c, 0.0, w.v * k, 0.0, w.v + c},
+      {0.0, 0.0, c2, 0.0, 0.0},
+      {0.0, 0.0, 0.0, w.v * w.v - c2, 0.0}};
+  double ri[5][5] = {
+      {0.5 * (c + w.v) / c, 0.0, -1.0 / (2.0 * c), -0.5 * k / c2, arg / (2.0 * c * (c - w.v))},
+      {-w.u, 1.0, 0.0, w.u * k / c2, 0.0},
+      {0.0, 0.0, 0.0, 1.0 / c2, 0.0},
+      {0.0, 0.0, 0.0, 0.0, 1.0 / (w.v * w.v - c2)},
+      {0.5 * (c - w.v) / c, 0.0, 1.0 / (2.0 * c), -0.5 * k / c2, arg / (2.0 * c * (c + w.v))}};
+  std::memcpy(R, r, sizeof r);
+  std::memcpy(Ri, ri, sizeof ri);
+  L[0] = w.v - c; L[1] = w.v; L[2] = w.v; L[3] = 0.0; L[4] = w.v + c;
+}
+
+double sgn(double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0); }
+
+// out = R diag(h(Lambda)) R^-1 x, applied as three products so that an unused
+// (zero) 5th input never meets a non-finite entry.
+void apply_eig(const double R[5][5], const double d[5], const double Ri[5][5], const double x[5],
+               double out[5]) {
+  double t[5];
+  for (int r = 0; r < 5; ++r) {
+    double s = 0.0;
+    for (int k = 0; k < 5; ++k)
+      if (x[k] != 0.0) s += Ri[r][k] * x[k];
+    t[r] = d[r] * s;
+  }
+  for (int r = 0; r < 5; ++r) {
+    double s = 0.0;
+    for (int k = 0; k < 5; ++k)
+      if (t[k] != 0.0) s += R[r][k] * t[k];
+    out[r] = s;
+  }
+}
+
+// |A1(q)| x = R1 |Lambda1| R1^-1 x.
+void abs_A1_apply(const Model& M, const double q[4], const double x[5], double out[5]) {
+  double R[5][5], Ri[5][5], L[5], d[5];
+  eigen_x(M, q, R, L, Ri);
+  for (int k = 0; k < 5; ++k) d[k] = std::fabs(L[k]);
+  apply_eig(R, d, Ri, x, out);
+}
+
+// sign(A2(q)) x = R2 sign(Lambda2) R2^-1 x.
+void sign_A2_apply(const Model& M, const double q[4], const double x[5], double out[5]) {
+  double R[5][5], Ri[5][5], L[5], d[5];
+  eigen_y(M, q, R, L, Ri);
+  for (int k = 0; k < 5; ++k) d[k] = sgn(L[k]);
+  apply_eig(R, d, Ri, x, out);
+}
+
+// ---------------------------------------------------------------------------
+// x direction: path-conservative Osher scheme, Section 3.2.
+// ---------------------------------------------------------------------------
+void dfluct_x(const Model& M, const double qm[4], const double qp[4], double Dm[4], double Dp[4]) {
+  const double s_gl[3] = {0.5 - std::sqrt(15.0) / 10.0, 0.5, 0.5 + std::sqrt(15.0) / 10.0};
+  const double w_gl[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
+  double fm[5], fp[5];
+  flux_f(M, qm, fm);
+  flux_f(M, qp, fp);
+  double dq[5] = {qp[0] - qm[0], qp[1] - qm[1], qp[2] - qm[2], qp[3] - qm[3], 0.0};
+  double V[5] = {0, 0, 0, 0, 0};
+  double ubar = 0.0;   // reading R-vel
+  for (int k = 0; k < 3; ++k) {
+    double phi[4];
+    for (int v = 0; v < 4; ++v) phi[v] = qm[v] + s_gl[k] * dq[v];
+    double t[5];
+    abs_A1_apply(M, phi, dq, t);
+    for (int v = 0; v < 5; ++v) V[v] += w_gl[k] * t[v];
+    ubar += w_gl[k] * prim(M, phi).u;
+  }
+  double B[5] = {0.0, 0.0, 0.0, ubar * dq[3], 0.0};
+  for (int v = 0; v < 4; ++v) {
+    Dm[v] = 0.5 * (fp[v] - fm[v] + B[v] - V[v]);
+    Dp[v] = 0.5 * (fp[v] - fm[v] + B[v] + V[v]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// y direction: well-balanced Osher-Romberg scheme, Section 3.3, at a face where
+// both states sit at the same height (second order): Phi = Phi^E + Phi^f with
+// Phi^E(s) the stationary contact alpha^E(s) = aEm + s (aEp - aEm), rho^E fixed.
+// ---------------------------------------------------------------------------
+struct YNode {
+  double q[4];   // full conserved state
+  double f[4];   // fluctuation (m^f, mu, mv, a^f)
+  double aE;     // alpha^E on the equilibrium path
+};
+
+YNode ynode(const double fm[4], double aEm, const double fp[4], double aEp, double rhoE, double s) {
+  YNode n;
+  n.aE = aEm + s * (aEp - aEm);
+  for (int v = 0; v < 4; ++v) n.f[v] = fm[v] + s * (fp[v] - fm[v]);
+  n.q[0] = n.aE * rhoE + n.f[0];
+  n.q[1] = n.f[1];
+  n.q[2] = n.f[2];
+  n.q[3] = n.aE + n.f[3];
+  return n;
+}
+
+// aE pf + af pE + af pf at one state (reading R-b3): the fluctuation of alpha p.
+double ap_fluct(const Model& M, const YNode& n, double rhoE) {
+  const double af = n.f[3];
+  const double a = n.q[3];
+  const double rhof = (n.f[0] - rhoE * af) / a;
+  const double pE = pressure(M, rhoE);
+  const double pf = sound2(M, rhoE) * rhof;   // p - pE, linear for gamma = 1
+  return n.aE * pf + af * pE + af * pf;
+}
+
+// B_Phi (qb - qa) for two states on the same face: (0, 0, b3, b4, 0), with the
+// path-average velocity vbar of the segment (reading R-vel).  b3 is the
+// fluctuation part plus the equilibrium part Delta(alpha^E p^E) (reading R-eq).
+void bterm_y(const Model& M, const YNode& a, const YNode& b, double rhoE, double vbar,
+             double out[5]) {
+  out[0] = 0.0;
+  out[1] = 0.0;
+  out[2] = ap_fluct(M, b, rhoE) - ap_fluct(M, a, rhoE) + (b.aE - a.aE) * pressure(M, rhoE);
+  out[3] = vbar * (b.q[3] - a.q[3]);
+  out[4] = 0.0;
+}
+
+void dfluct_y(const Model& M, const double fm[4], double aEm, const double fp[4], double aEp,
+              double rhoE, double Dm[4], double Dp[4]) {
+  // Romberg: s_k = (1/4, 3/4, 1/2), omega_k = (2/3, 2/3, -1/3), eps_k = (1/4, 1/4, 1/2).
+  const double sk[3] = {0.25, 0.75, 0.5};
+  const double wk[3] = {2.0 / 3.0, 2.0 / 3.0, -1.0 / 3.0};
+  const double ek[3] = {0.25, 0.25, 0.5};
+  YNode n0 = ynode(fm, aEm, fp, aEp, rhoE, 0.0);
+  YNode n1 = ynode(fm, aEm, fp, aEp, rhoE, 1.0);
+  double g0[5], g1[5], B01[5];
+  flux_g(M, n0.q, g0);
+  flux_g(M, n1.q, g1);
+  double vbar01 = 0.0;   // Romberg quadrature of the path velocity over [0, 1]
+  for (int k = 0; k < 3; ++k) vbar01 += wk[k] * prim(M, ynode(fm, aEm, fp, aEp, rhoE, sk[k]).q).v;
+  bterm_y(M, n0, n1, rhoE, vbar01, B01);
+  double V[5] = {0, 0, 0, 0, 0};
+  for (int k = 0; k < 3; ++k) {
+    YNode na = ynode(fm, aEm, fp, aEp, rhoE, sk[k] - ek[k]);
+    YNode nb = ynode(fm, aEm, fp, aEp, rhoE, sk[k] + ek[k]);
+    YNode nc = ynode(fm, aEm, fp, aEp, rhoE, sk[k]);
+    double ga[5], gb[5], Bab[5], Rk[5], t[5];
+    flux_g(M, na.q, ga);
+    flux_g(M, nb.q, gb);
+    bterm_y(M, na, nb, rhoE, prim(M, nc.q).v, Bab);
+    for (int v = 0; v < 5; ++v) Rk[v] = gb[v] - ga[v] + Bab[v];
+    sign_A2_apply(M, nc.q, Rk, t);
+    for (int v = 0; v < 5; ++v) V[v] += wk[k] * t[v] / (2.0 * ek[k]);
+  }
+  for (int v = 0; v < 4; ++v) {
+    Dm[v] = 0.5 * (g1[v] - g0[v] + B01[v] - V[v]);
+    Dp[v] = 0.5 * (g1[v] - g0[v] + B01[v] + V[v]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Grid, equilibrium and detector.
+// ---------------------------------------------------------------------------
+struct Grid {
+  int nx, ny;
+  double x0, y0, dx, dy;
+};
+
+struct Ctx {
+  Model M;
+  Grid G;
+  int sides[4];              // W, E, S, N: 0 wall, 1 transmissive
+  const uint8_t* solid;      // ny*nx
+  const double* Q;           // 4 planes
+  std::vector<int32_t> K;    // detected level per column
+  double dt;
+};
+
+inline size_t at(const Grid& G, int i, int j) { return (size_t)j * G.nx + i; }
+
+bool is_fluid(const Ctx& C, int i, int j) {
+  if (i < 0 || j < 0 || i >= C.G.nx || j >= C.G.ny) return false;
+  return C.solid[at(C.G, i, j)] == 0;
+}
+
+double kappa(const Model& M) { return M.g * M.rho0 / M.k0; }
+
+// Equilibrium density at height y_L + h * dy / 2 above the bottom, relative to level K
+// (h counts half cells: faces are even, centres odd).
+double rhoE_half(const Ctx& C, int h, int K) {
+  const double y_minus_y0 = (0.5 * h - K) * C.G.dy;
+  return C.M.rho0 * std::exp(-kappa(C.M) * y_minus_y0);
+}
+double rhoE_centre(const Ctx& C, int j, int K) { return rhoE_half(C, 2 * j + 1, K); }
+double rhoE_face(const Ctx& C, int jf, int K) { return rhoE_half(C, 2 * jf, K); }
+// Q^E_ij at the centre of row j for the volume fraction aE (reading R-eq).
+void QE_centre(const Ctx& C, int j, int K, double aE, double out[4]) {
+  out[0] = aE * rhoE_centre(C, j, K);
+  out[1] = 0.0;
+  out[2] = 0.0;
+  out[3] = aE;
+}
+
+// Eq. (Free_surf_detector) under reading R-det.
+int64_t detector_weight_fixed(const Model& M, double a, bool solid) {
+  double w;
+  if (solid) {
+    w = 1.0;
+  } else {
+    w = (a - M.eps) / (1.0 - M.eps);
+    if (w < 0.0) w = 0.0;
+    if (w > 1.0) w = 1.0;
+  }
+  return (int64_t)std::nearbyint(w * 4294967296.0);
+}
+
+void detect_levels(Ctx& C) {
+  const Grid& G = C.G;
+  C.K.assign(G.nx, 0);
+  for (int i = 0; i < G.nx; ++i) {
+    int64_t S = 0;
+    for (int j = 0; j < G.ny; ++j) {
+      const size_t c = at(G, i, j);
+      S += detector_weight_fixed(C.M, C.Q[3 * (size_t)G.nx * G.ny + c], C.solid[c] != 0);
+    }
+    C.K[i] = (int32_t)((S + ((int64_t)1 << 31)) >> 32);
+  }
+}
+
+// Reading R-cfl; returns the max signal rate (0 when there is no fluid cell).
+double max_rate(const Ctx& C) {
+  const Grid& G = C.G;
+  const size_t n = (size_t)G.nx * G.ny;
+  double mx = 0.0;
+  for (int j = 0; j < G.ny; ++j)
+    for (int i = 0; i < G.nx; ++i) {
+      const size_t c = at(G, i, j);
+      if (C.solid[c]) continue;
+      double q[4] = {C.Q[c], C.Q[n + c], C.Q[2 * n + c], C.Q[3 * n + c]};
+      Prim w = prim(C.M, q);
+      const double r = (std::fabs(w.u) + w.c) / G.dx + (std::fabs(w.v) + w.c) / G.dy;
+      if (r > mx) mx = r;
+    }
+  return mx;
+}
+
+// ---------------------------------------------------------------------------
+// Second-order well-balanced reconstruction (Section 3.4) of one fluid cell.
+// ---------------------------------------------------------------------------
+struct Rec {
+  double qW[4], qE[4];       // full states at the x-face midpoints, t^{n+1/2}
+  double fS[4], fN[4];       // fluctuations at the y-face midpoints, t^{n+1/2}
+  double qc[4];              // full state at the barycentre, t^{n+1/2}
+  double aE;                 // cell's alpha^E
+  double rhoES, rhoEN, rhoEc;
+  double dax, day;           // limited alpha slopes Psi_a d(a^f)/dx, /dy
+};
+
+void mirror(double q[4], int normal) { q[normal] = -q[normal]; }
+
+// Full state at a y face from its fluctuation.
+void y_full(const double f[4], double aE, double rhoE, double q[4]) {
+  q[0] = aE * rhoE + f[0];
+  q[1] = f[1];
+  q[2] = f[2];
+  q[3] = aE + f[3];
+}
+
+Rec reconstruct(const Ctx& C, int i, int j) {
+  const Grid& G = C.G;
+  const Model& M = C.M;
+  const size_t n = (size_t)G.nx * G.ny;
+  const int K = C.K[i];
+  const double aE = C.Q[3 * n + at(G, i, j)];
+  Rec r;
+  double QEc[4];
+  QE_centre(C, j, K, aE, QEc);
+  double Qf[4];
+  for (int v = 0; v < 4; ++v) Qf[v] = C.Q[v * n + at(G, i, j)] - QEc[v];
+
+  // Fluctuation of a neighbour w.r.t. column i's equilibrium (R-nb), or its ghost (R-wall).
+  auto nb_fluct = [&](int ii, int jj, int normal, int side, double out[4]) {
+    if (is_fluid(C, ii, jj)) {
+      double QEn[4];
+      QE_centre(C, jj, K, aE, QEn);
+      for (int v = 0; v < 4; ++v) out[v] = C.Q[v * n + at(G, ii, jj)] - QEn[v];
+      return;
+    }
+    const bool outside = ii < 0 || jj < 0 || ii >= G.nx || jj >= G.ny;
+    for (int v = 0; v < 4; ++v) out[v] = Qf[v];
+    if (!(outside && C.sides[side] == 1)) mirror(out, normal);
+  };
+  double fW[4], fE[4], fS[4], fN[4];
+  nb_fluct(i - 1, j, 1, 0, fW);
+  nb_fluct(i + 1, j, 1, 1, fE);
+  nb_fluct(i, j - 1, 2, 2, fS);
+  nb_fluct(i, j + 1, 2, 3, fN);
+
+  double gx[4], gy[4], psi[4];
+  for (int v = 0; v < 4; ++v) {
+    gx[v] = (fE[v] - fW[v]) / (2.0 * G.dx);
+    gy[v] = (fN[v] - fS[v]) / (2.0 * G.dy);
+  }
+  // Barth-Jespersen limiter (R-bj).
+  for (int v = 0; v < 4; ++v) {
+    double mx = Qf[v], mn = Qf[v];
+    const double cand[4] = {fW[v], fE[v], fS[v], fN[v]};
+    for (double x : cand) {
+      if (x > mx) mx = x;
+      if (x < mn) mn = x;
+    }
+    for (int dj = -1; dj <= 1; dj += 2)
+      for (int di = -1; di <= 1; di += 2)
+        if (is_fluid(C, i + di, j + dj)) {
+          double QEn[4];
+          QE_centre(C, j + dj, K, aE, QEn);
+          const double x = C.Q[v * n + at(G, i + di, j + dj)] - QEn[v];
+          if (x > mx) mx = x;
+          if (x < mn) mn = x;
+        }
+    const double deltas[4] = {-0.5 * G.dx * gx[v], 0.5 * G.dx * gx[v], -0.5 * G.dy * gy[v],
+                              0.5 * G.dy * gy[v]};
+    double p = 1.0;
+    for (double d : deltas) {
+      double phi = 1.0;
+      if (d > 0.0) phi = std::fmin(1.0, (mx - Qf[v]) / d);
+      else if (d < 0.0) phi = std::fmin(1.0, (mn - Qf[v]) / d);
+      if (phi < p) p = phi;
+    }
+    psi[v] = p;
+  }
+  double psi_cell = psi[0];
+  for (int v = 1; v < 4; ++v)
+    if (psi[v] < psi_cell) psi_cell = psi[v];
+  for (int v = 0; v < 4; ++v) psi[v] = psi_cell;
+
+  const double a_cell = C.Q[3 * n + at(G, i, j)];
+  double dtQ[4] = {0, 0, 0, 0};
+  if (a_cell <= 10.0 * M.eps) {
+    for (int v = 0; v < 4; ++v) psi[v] = 0.0;   // first order in near-gas cells (R-sw)
+  } else {
+    // dQ/dt = -(A1 dQ/dx + A2 dQ/dy) with grad Q = grad Q^E + Psi grad Q^f,
+    // Eq. (gradientEq+fluct).  grad Q^E = (d m^E/dy, 0, 0, 0, dy/dy = 1).  The
+    // equilibrium balance c^2 dm^E/dy + g m^E = 0 of row 3 is removed exactly.
+    double Qc[4];
+    for (int v = 0; v < 4; ++v) Qc[v] = QEc[v] + Qf[v];
+    double A1[5][5], A2[5][5];
+    jacobian_A1(M, Qc, A1);
+    jacobian_A2(M, Qc, A2);
+    double dx5[5] = {psi[0] * gx[0], psi[1] * gx[1], psi[2] * gx[2], psi[3] * gx[3], 0.0};
+    double dyf5[5] = {psi[0] * gy[0], psi[1] * gy[1], psi[2] * gy[2], psi[3] * gy[3], 0.0};
+    double t[5] = {0, 0, 0, 0, 0};
+    for (int r2 = 0; r2 < 5; ++r2)
+      for (int k = 0; k < 5; ++k) t[r2] += A1[r2][k] * dx5[k] + A2[r2][k] * dyf5[k];
+    Prim w = prim(M, Qc);
+    const double dmE = QEc[3] * (-kappa(M) * rhoE_centre(C, j, K));
+    // A2 grad Q^E minus the exact balance: rows 2 and 3.
+    t[1] += -w.u * w.v * dmE;
+    t[2] += -w.v * w.v * dmE + M.g * Qf[0];
+    for (int v = 0; v < 4; ++v) dtQ[v] = -t[v];
+  }
+  const double half_dt = 0.5 * C.dt;
+  r.aE = QEc[3];
+  r.rhoEc = rhoE_centre(C, j, K);
+  r.rhoES = rhoE_face(C, j, K);
+  r.rhoEN = rhoE_face(C, j + 1, K);
+  for (int v = 0; v < 4; ++v) {
+    const double base = Qf[v] + half_dt * dtQ[v];
+    r.qW[v] = QEc[v] + base - psi[v] * gx[v] * 0.5 * G.dx;
+    r.qE[v] = QEc[v] + base + psi[v] * gx[v] * 0.5 * G.dx;
+    r.fS[v] = base - psi[v] * gy[v] * 0.5 * G.dy;
+    r.fN[v] = base + psi[v] * gy[v] * 0.5 * G.dy;
+    r.qc[v] = QEc[v] + base;
+  }
+  // Reading R-pos.
+  double qN[4], qS[4];
+  y_full(r.fN, r.aE, r.rhoEN, qN);
+  y_full(r.fS, r.aE, r.rhoES, qS);
+  const double* states[5] = {r.qW, r.qE, qN, qS, r.qc};
+  bool ok = true;
+  for (int k = 0; k < 5; ++k)
+    if (!(states[k][0] > 0.0 && states[k][3] > 0.0)) ok = false;
+  if (!ok) {
+    for (int v = 0; v < 4; ++v) {
+      psi[v] = 0.0;
+      r.qW[v] = r.qE[v] = r.qc[v] = QEc[v] + Qf[v];
+      r.fS[v] = r.fN[v] = Qf[v];
+    }
+  }
+  r.dax = psi[3] * gx[3];
+  r.day = psi[3] * gy[3];
+  return r;
+}
+
+// x face between cells (iface-1, j) and (iface, j); L/R null when not fluid.
+void xface(const Ctx& C, const Rec* L, const Rec* R, int iface, double Dm[4], double Dp[4]) {
+  double qm[4], qp[4];
+  if (L && R) {
+    std::memcpy(qm, L->qE, sizeof qm);
+    std::memcpy(qp, R->qW, sizeof qp);
+  } else if (L) {
+    std::memcpy(qm, L->qE, sizeof qm);
+    std::memcpy(qp, L->qE, sizeof qp);
+    const bool transmissive = iface == C.G.nx && C.sides[1] == 1;
+    if (!transmissive) mirror(qp, 1);
+  } else {
+    std::memcpy(qp, R->qW, sizeof qp);
+    std::memcpy(qm, R->qW, sizeof qm);
+    const bool transmissive = iface == 0 && C.sides[0] == 1;
+    if (!transmissive) mirror(qm, 1);
+  }
+  dfluct_x(C.M, qm, qp, Dm, Dp);
+}
+
+// y face between cells (i, jface-1) and (i, jface).
+void yface(const Ctx& C, const Rec* B, const Rec* T, int jface, double Dm[4], double Dp[4]) {
+  double fm[4], fp[4], aEm, aEp, rhoE;
+  if (B && T) {
+    std::memcpy(fm, B->fN, sizeof fm);
+    std::memcpy(fp, T->fS, sizeof fp);
+    aEm = B->aE;
+    aEp = T->aE;
+    rhoE = B->rhoEN;
+  } else if (B) {
+    std::memcpy(fm, B->fN, sizeof fm);
+    std::memcpy(fp, B->fN, sizeof fp);
+    aEm = aEp = B->aE;
+    rhoE = B->rhoEN;
+    const bool transmissive = jface == C.G.ny && C.sides[3] == 1;
+    if (!transmissive) mirror(fp, 2);
+  } else {
+    std::memcpy(fp, T->fS, sizeof fp);
+    std::memcpy(fm, T->fS, sizeof fm);
+    aEm = aEp = T->aE;
+    rhoE = T->rhoES;
+    const bool transmissive = jface == 0 && C.sides[2] == 1;
+    if (!transmissive) mirror(fm, 2);
+  }
+  dfluct_y(C.M, fm, aEm, fp, aEp, rhoE, Dm, Dp);
+}
+
+// Eq. (Scheme) for one fluid cell with the interior integral of reading R-int.
+void update_cell(const Ctx& C, const Rec& r, int i, int j, const double DpW[4], const double DmE[4],
+                 const double DpS[4], const double DmN[4], double out[4]) {
+  const Grid& G = C.G;
+  const Model& M = C.M;
+  const size_t n = (size_t)G.nx * G.ny;
+  double fE[5], fW[5], gN[5], gS[5];
+  flux_f(M, r.qE, fE);
+  flux_f(M, r.qW, fW);
+  double qN[4], qS[4];
+  y_full(r.fN, r.aE, r.rhoEN, qN);
+  y_full(r.fS, r.aE, r.rhoES, qS);
+  flux_g(M, qN, gN);
+  flux_g(M, qS, gS);
+  Prim wc = prim(M, r.qc);
+  double Ix[4], Iy[4];
+  for (int v = 0; v < 4; ++v) {
+    Ix[v] = fE[v] - fW[v];
+    Iy[v] = gN[v] - gS[v];
+  }
+  Ix[3] += G.dx * wc.u * r.dax;
+  // Pressure and gravity fluctuation parts of Eq. (b^y_3_final_integral).
+  YNode nN, nS;
+  std::memcpy(nN.q, qN, sizeof qN); std::memcpy(nN.f, r.fN, sizeof qN); nN.aE = r.aE;
+  std::memcpy(nS.q, qS, sizeof qS); std::memcpy(nS.f, r.fS, sizeof qS); nS.aE = r.aE;
+  const double pressure_part = ap_fluct(M, nN, r.rhoEN) - ap_fluct(M, nS, r.rhoES);
+  double fc[4];
+  for (int v = 0; v < 4; ++v) fc[v] = r.qc[v] - (v == 0 ? r.aE * r.rhoEc : (v == 3 ? r.aE : 0.0));
+  const double af = fc[3];
+  const double rhof = (fc[0] - r.rhoEc * af) / r.qc[3];
+  const double gravity_part = (r.aE * rhof + af * r.rhoEc + af * rhof) * M.g * G.dy;
+  Iy[2] += pressure_part + gravity_part;
+  Iy[3] += G.dy * wc.v * r.day;
+  for (int v = 0; v < 4; ++v) {
+    const double q0 = C.Q[v * n + at(G, i, j)];
+    out[v] = q0 - C.dt / G.dx * (DpW[v] + DmE[v] + Ix[v]) - C.dt / G.dy * (DpS[v] + DmN[v] + Iy[v]);
+  }
+}
+
+bool admissible(const double q[4]) {
+  for (int v = 0; v < 4; ++v)
+    if (!std::isfinite(q[v])) return false;
+  return q[0] > 0.0 && q[3] > 0.0;
+}
+
+// One time step Q^n -> Q^{n+1}.  Returns 0, or 2 if a non-admissible state appears.
+int full_step(Ctx& C, double cfl, double* q_out) {
+  const Grid& G = C.G;
+  const size_t n = (size_t)G.nx * G.ny;
+  detect_levels(C);
+  const double rate = max_rate(C);
+  C.dt = rate > 0.0 ? cfl / rate : 0.0;
+  std::vector<Rec> rec(n);
+  std::vector<uint8_t> fl(n);
+  for (size_t c = 0; c < n; ++c) fl[c] = C.solid[c] == 0;
+#pragma omp parallel for schedule(static)
+  for (int j = 0; j < G.ny; ++j)
+    for (int i = 0; i < G.nx; ++i)
+      if (fl[at(G, i, j)]) rec[at(G, i, j)] = reconstruct(C, i, j);
+  auto rp = [&](int i, int j) -> const Rec* { return is_fluid(C, i, j) ? &rec[at(G, i, j)] : nullptr; };
+  const size_t nfx = (size_t)(G.nx + 1) * G.ny, nfy = (size_t)G.nx * (G.ny + 1);
+  std::vector<double> xm(4 * nfx, 0.0), xp(4 * nfx, 0.0), ym(4 * nfy, 0.0), yp(4 * nfy, 0.0);
+#pragma omp parallel for schedule(static)
+  for (int j = 0; j < G.ny; ++j)
+    for (int f = 0; f <= G.nx; ++f) {
+      const Rec* L = rp(f - 1, j);
+      const Rec* R = rp(f, j);
+      if (!L && !R) continue;
+      const size_t k = (size_t)j * (G.nx + 1) + f;
+      xface(C, L, R, f, &xm[4 * k], &xp[4 * k]);
+    }
+#pragma omp parallel for schedule(static)
+  for (int f = 0; f <= G.ny; ++f)
+    for (int i = 0; i < G.nx; ++i) {
+      const Rec* B = rp(i, f - 1);
+      const Rec* T = rp(i, f);
+      if (!B && !T) continue;
+      const size_t k = (size_t)f * G.nx + i;
+      yface(C, B, T, f, &ym[4 * k], &yp[4 * k]);
+    }
+  int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
+  for (int j = 0; j < G.ny; ++j)
+    for (int i = 0; i < G.nx; ++i) {
+      const size_t c = at(G, i, j);
+      double out[4] = {0, 0, 0, 0};
+      if (fl[c]) {
+        const size_t kw = (size_t)j * (G.nx + 1) + i, ke = kw + 1;
+        const size_t ks = (size_t)j * G.nx + i, kn = (size_t)(j + 1) * G.nx + i;
+        update_cell(C, rec[c], i, j, &xp[4 * kw], &xm[4 * ke], &yp[4 * ks], &ym[4 * kn], out);
+        if (!admissible(out)) bad = 1;
+      }
+      for (int v = 0; v < 4; ++v) q_out[v * n + c] = out[v];
+    }
+  return bad ? 2 : 0;
+}
+
+Ctx make_ctx(const int32_t* gi, const double* gd, const double* eos, const int32_t* sides,
+             const uint8_t* solid, const double* q) {
+  Ctx C;
+  C.G.nx = gi[0];
+  C.G.ny = gi[1];
+  C.G.x0 = gd[0];
+  C.G.y0 = gd[1];
+  C.G.dx = gd[2];
+  C.G.dy = gd[3];
+  C.M.rho0 = eos[0];
+  C.M.k0 = eos[1];
+  C.M.gamma = eos[2];
+  C.M.g = eos[3];
+  C.M.eps = eos[4];
+  for (int s = 0; s < 4; ++s) C.sides[s] = sides[s];
+  C.solid = solid;
+  C.Q = q;
+  C.dt = 0.0;
+  return C;
+}
+
+bool valid(const Ctx& C) {
+  return C.G.nx > 0 && C.G.ny > 0 && C.G.dx > 0.0 && C.G.dy > 0.0 && C.M.gamma == 1.0 &&
+         C.M.rho0 > 0.0 && C.M.k0 > 0.0 && C.M.eps > 0.0 && C.M.eps < 0.1;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C entry points (ctypes).  Arrays: grid ints {nx, ny}; grid doubles
+// {x0, y0, dx, dy}; eos {rho0, k0, gamma, g, eps}; sides {W, E, S, N};
+// q: 4 planes (m, mu, mv, a) of ny*nx doubles, x fastest.
+// Return 0 on success, 1 on invalid input, 2 on a non-admissible result.
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
+int orc_max_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+// n time steps; dt_hist (nullable) receives each dt, K_out (nullable) the levels
+// used by the last step.
+int orc_run(const int32_t* gi, const double* gd, const double* eos, const int32_t* sides,
+            const uint8_t* solid, const double* q_in, double* q_out, int nsteps, double cfl,
+            double* t_out, double* dt_hist, int32_t* K_out) {
+  Ctx C = make_ctx(gi, gd, eos, sides, solid, q_in);
+  if (!valid(C) || nsteps < 0 || !(cfl > 0.0)) return 1;
+  const size_t n4 = 4 * (size_t)C.G.nx * C.G.ny;
+  std::vector<double> a(q_in, q_in + n4), b(n4);
+  double t = 0.0;
+  int rc = 0;
+  for (int s = 0; s < nsteps; ++s) {
+    C.Q = a.data();
+    rc = full_step(C, cfl, b.data());
+    t += C.dt;
+    if (dt_hist) dt_hist[s] = C.dt;
+    a.swap(b);
+    if (rc) break;
+  }
+  if (K_out) {
+    C.Q = a.data();
+    if (nsteps > 0) {
+      for (int i = 0; i < C.G.nx; ++i) K_out[i] = C.K[i];
+    } else {
+      detect_levels(C);
+      for (int i = 0; i < C.G.nx; ++i) K_out[i] = C.K[i];
+    }
+  }
+  std::memcpy(q_out, a.data(), n4 * sizeof(double));
+  if (t_out) *t_out = t;
+  return rc;
+}
+
+// dt and levels of the state q (the quantities one step would use).
+int orc_dt_levels(const int32_t* gi, const double* gd, const double* eos, const int32_t* sides,
+                  const uint8_t* solid, const double* q, double cfl, double* dt, int32_t* K) {
+  Ctx C = make_ctx(gi, gd, eos, sides, solid, q);
+  if (!valid(C)) return 1;
+  detect_levels(C);
+  const double rate = max_rate(C);
+  *dt = rate > 0.0 ? cfl / rate : 0.0;
+  for (int i = 0; i < C.G.nx; ++i) K[i] = C.K[i];
+  return 0;
+}
+
+// One step evaluated only at the listed cells (cells[k] = j*nx + i, fluid only):
+// out[4*k + v] = Q^{n+1}_v at that cell.
+int orc_step_cells(const int32_t* gi, const double* gd, const double* eos, const int32_t* sides,
+                   const uint8_t* solid, const double* q, double cfl, const int64_t* cells,
+                   int ncells, double* out, double* dt_out) {
+  Ctx C = make_ctx(gi, gd, eos, sides, solid, q);
+  if (!valid(C)) return 1;
+  const Grid& G = C.G;
+  detect_levels(C);
+  const double rate = max_rate(C);
+  C.dt = rate > 0.0 ? cfl / rate : 0.0;
+  if (dt_out) *dt_out = C.dt;
+  int rc = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(| : rc)
+  for (int k = 0; k < ncells; ++k) {
+    const int i = (int)(cells[k] % G.nx), j = (int)(cells[k] / G.nx);
+    if (!is_fluid(C, i, j)) {
+      for (int v = 0; v < 4; ++v) out[4 * k + v] = 0.0;
+      continue;
+    }
+    Rec self = reconstruct(C, i, j);
+    Rec nb[4];
+    const Rec* p[4] = {nullptr, nullptr, nullptr, nullptr};
+    const int di[4] = {-1, 1, 0, 0}, dj[4] = {0, 0, -1, 1};
+    for (int s = 0; s < 4; ++s)
+      if (is_fluid(C, i + di[s], j + dj[s])) {
+        nb[s] = reconstruct(C, i + di[s], j + dj[s]);
+        p[s] = &nb[s];
+      }
+    double dmW[4], dpW[4], dmE[4], dpE[4], dmS[4], dpS[4], dmN[4], dpN[4];
+    xface(C, p[0], &self, i, dmW, dpW);
+    xface(C, &self, p[1], i + 1, dmE, dpE);
+    yface(C, p[2], &self, j, dmS, dpS);
+    yface(C, &self, p[3], j + 1, dmN, dpN);
+    update_cell(C, self, i, j, dpW, dmE, dpS, dmN, &out[4 * k]);
+    if (!admissible(&out[4 * k])) rc = 2;
+  }
+  return rc;
+}
+
+// ---- pieces exposed for the pin tests ----------------------------------------
+// model: {rho0, k0, gamma, g, eps}
+
+void orc_flux(const double* model, const double q[4], double f[5], double g[5]) {
+  Model M{model[0], model[1], model[2], model[3], model[4]};
+  flux_f(M, q, f);
+  flux_g(M, q, g);
+}
+
+void orc_jacobians(const double* model, const double q[4], double A1[25], double A2[25]) {
+  Model M{model[0], model[1], model[2], model[3], model[4]};
+  jacobian_A1(M, q, reinterpret_cast<double(*)[5]>(A1));
+  jacobian_A2(M, q, reinterpret_cast<double(*)[5]>(A2));
+}
+
+void orc_eigen(const double* model, const double q[4], int dir, double R[25], double L[5],
+               double Ri[25]) {
+  Model M{model[0], model[1], model[2], model[3], model[4]};
+  if (dir == 0)
+    eigen_x(M, q, reinterpret_cast<double(*)[5]>(R), L, reinterpret_cast<double(*)[5]>(Ri));
+  else
+    eigen_y(M, q, reinterpret_cast<double(*)[5]>(R), L, reinterpret_cast<double(*)[5]>(Ri));
+}
+
+void orc_abs_A1_apply(const double* model, const double q[4], const double x[5], double out[5]) {
+  Model M{model[0], model[1], model[2], model[3], model[4]};
+  abs_A1_apply(M, q, x, out);
+}
+
+void orc_sign_A2_apply(const double* model, const double q[4], const double x[5], double out[5]) {
+  Model M{model[0], model[1], model[2], model[3], model[4]};
+  sign_A2_apply(M, q, x, out);
+}
+
+void orc_dfluct_x(const double* model, const double qm[4], const double qp[4], double Dm[4],
+                  double Dp[4]) {
+  Model M{model[0], model[1], model[2], model[3], model[4]};
+  dfluct_x(M, qm, qp, Dm, Dp);
+}
+
+void orc_dfluct_y(const double* model, const double fm[4], double aEm, const double fp[4],
+                  double aEp, double rhoE, double Dm[4], double Dp[4]) {
+  Model M{model[0], model[1], model[2], model[3], model[4]};
+  dfluct_y(M, fm, aEm, fp, aEp, rhoE, Dm, Dp);
+}
+
+}  // extern "C"
+
+extern "C" {
+// Reconstruction of one fluid cell for inspection: out = qW[4], qE[4], fS[4], fN[4],
+// qc[4], aE, rhoES, rhoEN, rhoEc, dax, day, dt  (27 doubles).
+int orc_cell_rec(const int32_t* gi, const double* gd, const double* eos, const int32_t* sides,
+                 const uint8_t* solid, const double* q, double cfl, int i, int j, double* out) {
+  Ctx C = make_ctx(gi, gd, eos, sides, solid, q);
+  if (!valid(C) || !is_fluid(C, i, j)) return 1;
+  detect_levels(C);
+  const double rate = max_rate(C);
+  C.dt = rate > 0.0 ? cfl / rate : 0.0;
+  Rec r = reconstruct(C, i, j);
+  std::memcpy(out, r.qW, 4 * sizeof(double));
+  std::memcpy(out + 4, r.qE, 4 * sizeof(double));
+  std::memcpy(out + 8, r.fS, 4 * sizeof(double));
+  std::memcpy(out + 12, r.fN, 4 * sizeof(double));
+  std::memcpy(out + 16, r.qc, 4 * sizeof(double));
+  out[20] = r.aE; out[21] = r.rhoES; out[22] = r.rhoEN; out[23] = r.rhoEc;
+  out[24] = r.dax; out[25] = r.day; out[26] = C.dt;
+  return 0;
+}
+}  // extern "C"

@@ -1,0 +1,387 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: the printed
+eigenstructure must diagonalise the printed Jacobians, numpy's eigensolver gives
+|A| and sign(A), finite differences give df/dQ, exact quadrature identities hold
+in the linear case, the paper's Table 1 bounds the lake-at-rest errors, the
+exact isothermal Riemann solution and the elliptical-drop ODE (which reproduces
+the paper's printed semi-axes) bound the dynamics.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1806_04960_gb300 import cases
+from oracle_refs import drop_semi_axes, isothermal_riemann, read_golden
+
+K0 = 4.36e5
+RHO0 = 1000.0
+G = 9.81
+C2 = K0 / RHO0
+
+
+def random_states(n, seed, alpha_lo=0.05, vmax=3.0):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(n):
+        a = rng.uniform(alpha_lo, 1.0)
+        rho = RHO0 * rng.uniform(0.97, 1.03)
+        u, v = rng.uniform(-vmax, vmax, 2)
+        m = a * rho
+        out.append(np.array([m, m * u, m * v, a]))
+    return out
+
+
+def np_abs_sign(A):
+    w, V = np.linalg.eig(A)
+    w = w.real
+    V = V.real
+    Vi = np.linalg.inv(V)
+    absA = V @ np.diag(np.abs(w)) @ Vi
+    sgn = np.where(np.abs(w) < 1e-9 * np.abs(w).max(), 0.0, np.sign(w))
+    return absA, V @ np.diag(sgn) @ Vi
+
+
+# ---------------------------------------------------------------- eigenstructure
+
+@pytest.mark.parametrize("direction", [0, 1])
+def test_printed_eigenvectors_diagonalise_jacobian(direction):
+    for q in random_states(20, 11 + direction):
+        A1, A2 = O.jacobians(q)
+        A = A1 if direction == 0 else A2
+        R, L, Ri = O.eigen(q, direction)
+        assert np.allclose(R @ Ri, np.eye(5), atol=1e-9)
+        scale = np.abs(A @ R).max()
+        assert np.abs(A @ R - R @ np.diag(L)).max() <= 1e-12 * scale
+
+
+def fd_jacobian(fun, q, h=1e-6):
+    J = np.zeros((5, 5))
+    for k in range(4):
+        dq = np.zeros(4)
+        dq[k] = h * max(1.0, abs(q[k]))
+        J[:, k] = (fun(q + dq) - fun(q - dq)) / (2 * dq[k])
+    return J
+
+
+def test_jacobians_match_flux_derivatives():
+    """A1 - B1 = df/dQ and A2 - B2 = dg/dQ with B from Eq. (BNsimplified_genForm):
+    B1 grad Q = (0,0,0,u a_x), B2 grad Q = (0,0,(alpha p)_y + alpha rho g y_y, v a_y)."""
+    for q in random_states(10, 5):
+        A1, A2 = O.jacobians(q)
+        Jf = fd_jacobian(lambda s: O.flux(s)[0], q)
+        Jg = fd_jacobian(lambda s: O.flux(s)[1], q)
+        m, mu, mv, a = q
+        u, v = mu / m, mv / m
+        B1 = np.zeros((5, 5))
+        B1[3, 3] = u
+        # alpha p = a k0 (m / (a rho0) - 1): gradient w.r.t. (m, a), plus alpha rho g on y.
+        B2 = np.zeros((5, 5))
+        B2[2, 0] = K0 / RHO0
+        B2[2, 3] = -K0
+        B2[2, 4] = m * G
+        B2[3, 3] = v
+        assert np.allclose(A1, Jf + B1, rtol=1e-6, atol=1e-6)
+        assert np.allclose(A2, Jg + B2, rtol=1e-6, atol=1e-6)
+
+
+def test_abs_and_sign_match_numpy_eig():
+    for q in random_states(15, 7):
+        A1, A2 = O.jacobians(q)
+        absA1, _ = np_abs_sign(A1)
+        _, sgnA2 = np_abs_sign(A2)
+        x = np.array([3.0, -1.0, 2.0, 0.01, 0.0])
+        assert np.allclose(O.abs_A1_apply(q, x), absA1 @ x, rtol=1e-9, atol=1e-8)
+        assert np.allclose(O.sign_A2_apply(q, x), sgnA2 @ x, rtol=1e-9, atol=1e-8)
+
+
+# ---------------------------------------------------------------- face solvers
+
+def test_fluctuations_vanish_for_equal_states():
+    for q in random_states(10, 3):
+        Dm, Dp = O.dfluct_x(q, q)
+        assert np.all(Dm == 0) and np.all(Dp == 0)
+        rhoE = 999.0
+        f = q - np.array([q[3] * rhoE, 0, 0, q[3]])
+        Dm, Dp = O.dfluct_y(f, q[3], f, q[3], rhoE)
+        assert np.all(Dm == 0) and np.all(Dp == 0)
+        # the same full state split over different equilibria is still one state
+        f2 = q - np.array([0.5 * rhoE, 0, 0, 0.5])
+        Dm, Dp = O.dfluct_y(f, q[3], f2, 0.5, rhoE)
+        assert np.abs(Dm).max() < 1e-9 and np.abs(Dp).max() < 1e-9
+
+
+@pytest.mark.parametrize("scale", [0.7, 1.3])
+def test_linear_case_x_equals_abs_matrix(scale):
+    """u, v constant along the segment (q+ = lambda q-): A1 is constant on the
+    path and any quadrature gives D+ - D- = |A1| dq, D+ + D- = A1 dq."""
+    for q in random_states(8, 21):
+        qp = scale * q
+        qp[3] = scale * q[3]
+        dq = np.append(qp - q, 0.0)
+        A1, _ = O.jacobians(q)
+        absA, _ = np_abs_sign(A1)
+        Dm, Dp = O.dfluct_x(q, qp)
+        assert np.allclose(Dp - Dm, (absA @ dq)[:4], rtol=1e-9, atol=1e-7)
+        assert np.allclose(Dp + Dm, (A1 @ dq)[:4], rtol=1e-9, atol=1e-7)
+
+
+@pytest.mark.parametrize("scale", [0.8, 1.25])
+def test_linear_case_y_equals_abs_matrix(scale):
+    """Same for the Osher-Romberg y solver: with u, v constant along the path the
+    Romberg combination collapses to sign(A2) A2 dq = |A2| dq."""
+    rhoE = 1001.0
+    for q in random_states(8, 23):
+        qp = scale * q
+        dq = np.append(qp - q, 0.0)
+        _, A2 = O.jacobians(q)
+        absA, _ = np_abs_sign(A2)
+        aE = q[3]
+        fm = q - np.array([aE * rhoE, 0, 0, aE])
+        fp = qp - np.array([aE * rhoE, 0, 0, aE])
+        Dm, Dp = O.dfluct_y(fm, aE, fp, aE, rhoE)
+        assert np.allclose(Dp - Dm, (absA @ dq)[:4], rtol=1e-9, atol=1e-7)
+        assert np.allclose(Dp + Dm, (A2 @ dq)[:4], rtol=1e-9, atol=1e-7)
+
+
+def test_alpha_transport_is_upwind():
+    """Path-consistent velocity: with u > 0 at every quadrature node the upwind
+    cell receives no alpha fluctuation (D-_4 = 0), and vice versa."""
+    rng = np.random.Generator(np.random.PCG64(99))
+    for _ in range(20):
+        qm = random_states(1, int(rng.integers(1 << 30)))[0]
+        qp = random_states(1, int(rng.integers(1 << 30)))[0]
+        for sgn in (1.0, -1.0):
+            a, b = qm.copy(), qp.copy()
+            a[1] = sgn * abs(a[1]) + sgn * 0.1 * a[0]
+            b[1] = sgn * abs(b[1]) + sgn * 0.1 * b[0]
+            Dm, Dp = O.dfluct_x(a, b)
+            if sgn > 0:
+                assert abs(Dm[3]) < 1e-14
+            else:
+                assert abs(Dp[3]) < 1e-14
+            rhoE = 1000.0
+            a2, b2 = qm.copy(), qp.copy()
+            a2[2] = sgn * abs(a2[2]) + sgn * 0.1 * a2[0]
+            b2[2] = sgn * abs(b2[2]) + sgn * 0.1 * b2[0]
+            fm = a2 - np.array([a2[3] * rhoE, 0, 0, a2[3]])
+            fp = b2 - np.array([b2[3] * rhoE, 0, 0, b2[3]])
+            Dm, Dp = O.dfluct_y(fm, a2[3], fp, b2[3], rhoE)
+            if sgn > 0:
+                assert abs(Dm[3]) < 1e-14
+            else:
+                assert abs(Dp[3]) < 1e-14
+
+
+def test_wall_face_has_no_mass_flux():
+    """A wall face sees the mirror state; the y solver's mass flux
+    0.5 (g1(q-) + g1(q+)) - 0.5 V1 vanishes exactly, the x solver's to roundoff."""
+    for q in random_states(10, 31):
+        rhoE = 1000.5
+        f = q - np.array([q[3] * rhoE, 0, 0, q[3]])
+        g = f.copy()
+        g[2] = -g[2]
+        Dm, Dp = O.dfluct_y(f, q[3], g, q[3], rhoE)
+        # cell below the wall gets D-; its mass flux is g1(q-) + D-_1
+        assert Dm[0] + q[2] == 0.0
+        r = q.copy()
+        r[1] = -r[1]
+        Dm, Dp = O.dfluct_x(q, r)
+        assert abs(Dm[0] + q[1]) <= 1e-12 * abs(q[1]) + 1e-12
+
+
+# ---------------------------------------------------------------- detector
+
+def test_detector_finds_lake_level_with_obstacles():
+    c = cases.c1_lake()
+    dt, K = O.dt_levels(c)
+    assert np.all(K == 32)
+    c2 = cases.dambreak(64, 64, rects=cases.c2_rects(), lake_level=1.0)
+    _, K2 = O.dt_levels(c2)
+    assert np.all(K2 == 32)
+
+
+def test_detector_rounds_half_away_from_zero():
+    c = cases.dambreak(4, 8, lx=1.0, ly=1.0, x_col=2.0, h_col=0.5)
+    q = c.q.copy()
+    q[3][:, :] = c.eps
+    q[3][0:3, 0] = 1.0
+    q[3][3, 0] = c.eps + 0.5 * (1 - c.eps)      # w = 0.5 -> 3.5 rounds to 4
+    q[3][0:2, 1] = 1.0
+    q[3][2, 1] = c.eps + 0.49 * (1 - c.eps)     # 2.49 -> 2
+    q[0] = q[3] * RHO0
+    _, K = O.dt_levels(c, q=q)
+    assert K[0] == 4 and K[1] == 2 and K[2] == 0
+
+
+# ---------------------------------------------------------------- well balance
+
+def test_table1_lake_at_rest_within_paper_errors():
+    """Section 5.1: water at rest with and without the obstacle keeps the exact
+    profile; errors after t = 0.1 stay below the paper's t = 1 maxima."""
+    gold = {(r[0], float(r[1])): [float(x) for x in r[2:]] for r in read_golden("table1_lake_at_rest.txt")}
+    for obstacle in (True, False):
+        c = cases.lake_box(100, obstacle=obstacle)
+        fl = c.solid == 0
+        t = 0.0
+        q = c.q
+        while t < 0.1:
+            q, tt, _, _ = O.run(c, 50, q=q)
+            t += tt
+        rho = q[0][fl] / q[3][fl]
+        rho_ex = c.q[0][fl] / c.q[3][fl]
+        E_rho = np.abs(rho - rho_ex).max()
+        E_u = np.abs(q[1][fl] / q[0][fl]).max()
+        E_v = np.abs(q[2][fl] / q[0][fl]).max()
+        E_p = np.abs(c.k0 * (rho - rho_ex) / RHO0).max()
+        ref = gold[("obstacle" if obstacle else "flat", 1.0)]
+        assert E_rho <= max(ref[0], 1e-12), E_rho
+        assert E_u <= max(ref[1], 1e-13), E_u
+        assert E_v <= max(ref[2], 1e-13), E_v
+        assert E_p <= max(ref[3], 1e-9), E_p
+
+
+def test_lake_with_air_and_obstacle_stays_at_rest():
+    c = cases.c1_lake()
+    q, t, _, K = O.run(c, 200)
+    fl = c.solid == 0
+    assert np.all(K == 32)
+    assert np.abs(q[1]).max() < 1e-12 and np.abs(q[2]).max() < 1e-12
+    assert np.abs(q[0] - c.q[0])[fl].max() < 1e-11 * RHO0
+    assert np.array_equal(q[3], c.q[3])
+
+
+# ---------------------------------------------------------------- conservation, symmetry
+
+def test_mass_conserved_with_walls_and_cfl09_stable():
+    c = cases.c1()
+    q, t, dts, _ = O.run(c, 200)
+    fl = c.solid == 0
+    m0 = c.q[0].sum()
+    assert abs(q[0].sum() - m0) <= 1e-13 * m0
+    assert np.all(q[3][fl] > 0) and np.all(q[0][fl] > 0)
+    assert np.all(q[3][fl] <= 1.0 + 1e-12)
+    speed = np.hypot(q[1][fl], q[2][fl]) / q[0][fl]
+    assert speed.max() < 2.0 * math.sqrt(c.k0 / RHO0)
+    assert t > 0.1
+
+
+def test_mirror_symmetry_of_centred_column():
+    c = cases.dambreak(64, 32, x_col=10.0, h_col=1.0, lx=4.0, ly=2.0)
+    X = np.meshgrid(c.xc(), c.yc())[0]
+    q = c.q.copy()
+    liquid = (np.abs(X - 2.0) < 0.5) & (q[3] == 1.0)
+    q[3] = np.where(liquid, 1.0, c.eps)
+    q[0] = np.where(liquid, c.q[0], c.eps * RHO0)
+    c = c.with_state(q)
+    qa, _, _, _ = O.run(c, 60)
+    qb, _, _, _ = O.run(cases.mirror_x(c), 60)
+    mb = qb[:, :, ::-1].copy()
+    mb[1] = -mb[1]
+    for v in range(4):
+        scale = np.abs(qa[v]).max() + 1e-300
+        assert np.abs(qa[v] - mb[v]).max() <= 1e-10 * scale
+
+
+def test_drop_is_symmetric_in_x_and_y():
+    c = cases.drop(64, steps=20)
+    q, _, _, _ = O.run(c, 20)
+    # k0 = 2.25e9 turns density roundoff into pressure noise; 1e-8 is roundoff level.
+    assert np.abs(q[0] - q[0][:, ::-1]).max() <= 1e-8 * q[0].max()
+    assert np.abs(q[0] - q[0][::-1, :]).max() <= 1e-8 * q[0].max()
+    assert np.abs(q[1] + q[1][:, ::-1]).max() <= 1e-8 * np.abs(q[1]).max()
+    assert np.abs(q[2] + q[2][::-1, :]).max() <= 1e-8 * np.abs(q[2]).max()
+
+
+# ---------------------------------------------------------------- accuracy
+
+def run_to(c, t_end):
+    q = c.q
+    t = 0.0
+    while t < t_end * (1 - 1e-12):
+        dt, _ = O.dt_levels(c, q)
+        cfl = c.cfl if t + dt <= t_end else c.cfl * (t_end - t) / dt
+        q, tt, _, _ = O.run(c, 1, q=q, cfl=cfl)
+        t += tt
+    return q
+
+
+def test_second_order_self_convergence_on_smooth_bump():
+    res = {n: run_to(cases.smooth_bump(n), 0.006) for n in (32, 64, 128)}
+
+    def coarsen(q):
+        return 0.25 * (q[:, 0::2, 0::2] + q[:, 1::2, 0::2] + q[:, 0::2, 1::2] + q[:, 1::2, 1::2])
+
+    e1 = np.abs(res[32][0] - coarsen(res[64])[0]).mean()
+    e2 = np.abs(res[64][0] - coarsen(res[128])[0]).mean()
+    assert math.log2(e1 / e2) >= 1.8
+
+
+def test_isothermal_riemann_problem_converges_to_exact_solution():
+    """alpha = 1, g = 0: isothermal gas dynamics with c^2 = k0/rho0."""
+    c_s = math.sqrt(K0 / RHO0)
+    errs = []
+    for n in (100, 200, 400):
+        c = cases.riemann_x(n, rho_l=1010.0, rho_r=1000.0, u_l=0.5, u_r=-0.5)
+        t_end = 0.25 / c_s
+        q = run_to(c, t_end)
+        xi = (c.xc() - 0.5) / t_end
+        rho_ex, u_ex = isothermal_riemann(1010.0, 0.5, 1000.0, -0.5, c_s, xi)
+        rho = q[0][1] / q[3][1]
+        errs.append(np.abs(rho - rho_ex).mean())
+        assert np.array_equal(q[3], np.ones_like(q[3]))
+    assert errs[2] < errs[1] < errs[0]
+    assert math.log2(errs[0] / errs[2]) / 2 > 0.6
+    # two shocks of height ~25 smeared over ~2 of 400 cells: L1 ~ 0.25
+    assert errs[2] < 0.3
+
+
+def test_alpha_contact_translates_exactly_in_velocity():
+    """p = 0 (rho = rho0) with uniform u: u stays uniform and alpha is advected."""
+    errs = []
+    for n in (100, 200):
+        c = cases.contact_x(n, u0=1.0)
+        t_end = 0.2
+        q = run_to(c, t_end)
+        u = q[1] / q[0]
+        assert np.abs(u - 1.0).max() < 1e-12
+        assert np.abs(q[0] / q[3] - RHO0).max() < 1e-9
+        X = np.meshgrid(c.xc(), c.yc())[0]
+        a_ex = 0.5 + 0.4 * np.exp(-((X - 0.3 - t_end) / 0.08) ** 2)
+        errs.append(np.abs(q[3] - a_ex).mean())
+    assert errs[1] < 0.5 * errs[0]
+
+
+def test_drop_ode_reproduces_paper_values():
+    for t, b in read_golden("drop_semi_axis.txt"):
+        a_ode, b_ode = drop_semi_axes(float(t))
+        assert abs(b_ode - float(b)) <= 0.006 * float(b)
+        assert abs(a_ode * b_ode - 1.0) < 1e-6
+
+
+def drop_axes(c, q):
+    """Semi-axes from the alpha = 0.5 crossings on the positive x and y axes."""
+    n = c.nx
+    col = 0.5 * (q[3][:, n // 2 - 1] + q[3][:, n // 2])
+    y = c.yc()
+    up = np.flatnonzero((y[:-1] > 0) & (col[:-1] >= 0.5) & (col[1:] < 0.5))[0]
+    b = y[up] + (col[up] - 0.5) / (col[up] - col[up + 1]) * c.dy
+    row = 0.5 * (q[3][n // 2 - 1, :] + q[3][n // 2, :])
+    x = c.xc()
+    rt = np.flatnonzero((x[:-1] > 0) & (row[:-1] >= 0.5) & (row[1:] < 0.5))[0]
+    a = x[rt] + (row[rt] - 0.5) / (row[rt] - row[rt + 1]) * c.dx
+    return a, b
+
+
+def test_drop_semi_axis_follows_exact_solution():
+    """Section 5.2 on [-2,2]^2 at 192^2: the semi-axes at t = 0.0008 from the
+    alpha = 0.5 crossings match the exact solution within 1 %."""
+    c = cases.drop(192)
+    t_end = 0.0008
+    q = run_to(c, t_end)
+    a, b = drop_axes(c, q)
+    a_ode, b_ode = drop_semi_axes(t_end)
+    assert abs(b - b_ode) <= 0.01 * b_ode, (b, b_ode)
+    assert abs(a - a_ode) <= 0.01 * a_ode, (a, a_ode)
