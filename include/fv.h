@@ -1,0 +1,137 @@
+/*
+ * fv.h -- C ABI of libfv, a GB300 (sm_103a) solver for the reduced
+ * Baer-Nunziato diffuse-interface model with the second-order well-balanced
+ * path-conservative finite-volume scheme of Gaburro, Castro & Dumbser,
+ * "A well balanced diffuse interface method for complex nonhydrostatic free
+ * surface flows" (Section 3: Eq. (Scheme) with the Osher x fluctuation, the
+ * well-balanced Osher-Romberg y fluctuation, the fluctuation reconstruction of
+ * Section 3.4 and the free-surface detector of Section 3.5).
+ *
+ * Conventions shared by every entry point
+ *   - State layout: four structure-of-arrays planes, in this order,
+ *       m = alpha*rho, mu = alpha*rho*u, mv = alpha*rho*v, a = alpha,
+ *     each ny*nx doubles with the x index fastest: q[v*nx*ny + j*nx + i].
+ *     The 5th variable of the paper (the gravity potential y) is static and is
+ *     not stored.  Solid (removed) cells are ignored on input and are 0 on
+ *     output.
+ *   - Cell (i, j) covers [x0 + i dx, x0 + (i+1) dx] x [y0 + j dy, y0 + (j+1) dy];
+ *     gravity acts along -y.
+ *   - Ownership: the library owns every device buffer it allocates; the caller
+ *     owns every array it passes in and may free it when the call returns.
+ *   - Streams: all device work is enqueued on the stream given to fv_create
+ *     (NULL = legacy default stream).  Calls that return host data synchronise
+ *     that stream first.
+ *   - Errors: every call returns an fv_status; no C++ exception crosses the
+ *     ABI.  fv_last_error() gives a thread-local message for the last failure.
+ *   - Threads: one handle must not be used from two threads at once.
+ */
+#ifndef FV_H
+#define FV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FV_OK = 0,
+  FV_EINVAL = 1,      /* invalid argument (null pointer, bad size, gamma != 1, ...) */
+  FV_ENOMEM = 2,      /* device or host allocation failed */
+  FV_ECUDA = 3,       /* a CUDA runtime call failed */
+  FV_ENONFINITE = 4,  /* a step produced a non-finite state or alpha <= 0 or alpha*rho <= 0 */
+  FV_ETIMEOUT = 5     /* a bounded device wait gave up */
+} fv_status;
+
+/* Arithmetic of the step.
+ *   FV_FP64     : state and all arithmetic in double.
+ *   FV_FP32_DEV : deviation form of Section 3.4 in float.  The stored state is
+ *                 m^f = m - alpha rho^E(y; y0_i) (deviation from the cell's own
+ *                 water-at-rest profile), mu, mv, alpha; fluxes, reconstruction
+ *                 and update run in float; the dt reduction, the detector
+ *                 column sums and the equilibrium table are double. */
+typedef enum { FV_FP64 = 0, FV_FP32_DEV = 1 } fv_prec;
+
+enum { FV_BC_WALL = 0, FV_BC_TRANSMISSIVE = 1 };
+
+/* Uniform Cartesian grid of nx x ny cells T_ij (Section 3: rectangular grid). */
+typedef struct {
+  int32_t nx, ny;     /* >= 1 each; nx*ny <= 2^31 - 1 */
+  double x0, y0;      /* lower-left corner */
+  double dx, dy;      /* > 0 */
+} fv_grid;
+
+/* Tait liquid (Eq. (TaitLaw)) and model constants (Section 5 preamble). */
+typedef struct {
+  double rho0;        /* reference density, > 0 */
+  double k0;          /* Tait constant, > 0 */
+  double gamma;       /* Tait exponent; must be 1 (all of the paper's tests) */
+  double g;           /* gravity, >= 0 (0 switches gravity off) */
+  double eps_gas;     /* gas volume fraction eps, in (0, 0.1) */
+} fv_eos;
+
+/* Boundaries: side[0..3] = West, East, South, North, each FV_BC_WALL (reflective
+ * wall, the mirror state with u.n negated, Section 5 preamble) or
+ * FV_BC_TRANSMISSIVE.  solid: nullable host pointer to nx*ny bytes (x fastest),
+ * 1 = cell removed from the domain (obstacle, Section 5.1), copied at create. */
+typedef struct {
+  int32_t side[4];
+  const uint8_t* solid;
+} fv_bc;
+
+typedef struct fv_handle fv_handle;
+
+/* Diagnostics of the current state (fv_get_diag). */
+typedef struct {
+  double t;           /* simulated time since fv_set_state */
+  int64_t steps;      /* steps taken since fv_set_state */
+  double dt_next;     /* dt the next step will use (CFL of the last fv_step) */
+  double mass;        /* sum over fluid cells of m dx dy, fixed-order double sum */
+  int32_t status;     /* FV_OK or FV_ENONFINITE if any step since set_state failed */
+} fv_diag;
+
+/* Create a solver for one domain.  cuda_stream: a cudaStream_t (may be NULL).
+ * Allocates all device memory for the grid (about 80 bytes per cell in FP64).
+ * Returns FV_EINVAL for bad sizes or parameters, FV_ENOMEM on allocation
+ * failure; *out is set only on success. */
+fv_status fv_create(const fv_grid* grid, const fv_eos* eos, const fv_bc* bc, fv_prec prec,
+                    void* cuda_stream, fv_handle** out);
+
+/* Load Q^0 (layout above).  on_device = 0: q is host memory; 1: q is device
+ * memory readable on the handle's stream.  Runs the free-surface detector
+ * (Eq. (Free_surf_detector)) and the CFL reduction for the first step, and
+ * resets t and the step count.  Non-admissible fluid cells give FV_EINVAL. */
+fv_status fv_set_state(fv_handle* h, const double* q, int on_device);
+
+/* Advance n >= 0 time steps of Eq. (Scheme), each with
+ * dt = cfl / max over fluid cells of ((|u|+c)/dx + (|v|+c)/dy), cfl in (0, 1].
+ * Asynchronous on the handle's stream unless t_out is non-null, in which case
+ * the stream is synchronised, *t_out receives the simulated time and the
+ * device status is checked (FV_ENONFINITE if a step produced a bad state). */
+fv_status fv_step(fv_handle* h, int32_t n, double cfl, double* t_out);
+
+/* Copy the current state out in the layout above (double).  on_device as in
+ * fv_set_state.  Synchronises the stream. */
+fv_status fv_get_state(fv_handle* h, double* q, int on_device);
+
+/* Detected free-surface levels K_i (y0_i = y0 + K_i dy) the next step will
+ * use; K: host array of nx int32.  Synchronises the stream. */
+fv_status fv_get_levels(fv_handle* h, int32_t* K);
+
+/* Time, step count, next dt, fluid mass and status.  Synchronises. */
+fv_status fv_get_diag(fv_handle* h, fv_diag* d);
+
+/* Release the handle and its device memory (synchronises; NULL is a no-op). */
+void fv_destroy(fv_handle* h);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* fv_last_error(void);
+
+/* Library version string. */
+const char* fv_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FV_H */

@@ -48,7 +48,12 @@
 //   R-nb    neighbours' fluctuations use the cell's own column level K_i;
 //   R-bj    central slopes, min/max over the 3x3 stencil, tests at the 4 face
 //           midpoints; one limiter value Psi_ij per cell, the smallest of the
-//           conserved components' Barth-Jespersen factors;
+//           four components' factors; each factor is the printed
+//           Barth-Jespersen value when the face increment |d| >= 2 eta, 1 when
+//           |d| <= eta and linear in between, eta = 2^-20 rho0 for alpha rho,
+//           2^-10 rho0 c for the momenta, 2^-20 for alpha (the printed
+//           limiter jumps between 0 and 1 as d -> 0, which lets roundoff in a
+//           flat component switch the whole cell to first order);
 //   R-vel   u_bar in b4x and v_bar in b4y are the segment-path averages of the
 //           velocity taken with the quadrature of the viscosity: Gauss-Legendre
 //           average of u(Phi(s_k)) in x; in y, v(Phi(s_k)) on each Romberg
@@ -431,6 +436,15 @@ struct Rec {
 
 void mirror(double q[4], int normal) { q[normal] = -q[normal]; }
 
+// Regularisation scale of the limiter per conserved component (reading R-bj):
+// 2^-20 rho0 for alpha rho, 2^-10 rho0 c for the momenta, 2^-20 for alpha.
+double bj_eta(const Model& M, int v) {
+  const double c = std::sqrt(sound2(M, M.rho0));
+  if (v == 0) return std::ldexp(M.rho0, -20);
+  if (v == 3) return std::ldexp(1.0, -20);
+  return std::ldexp(M.rho0 * c, -10);
+}
+
 // Full state at a y face from its fluctuation.
 void y_full(const double f[4], double aE, double rhoE, double q[4]) {
   q[0] = aE * rhoE + f[0];
@@ -493,15 +507,22 @@ Rec reconstruct(const Ctx& C, int i, int j) {
         }
     const double deltas[4] = {-0.5 * G.dx * gx[v], 0.5 * G.dx * gx[v], -0.5 * G.dy * gy[v],
                               0.5 * G.dy * gy[v]};
+    // Barth-Jespersen factor at the four face midpoints (reading R-bj): the
+    // printed factor for |d| >= 2 eta, 1 for |d| <= eta, linear in between.
+    const double eta = bj_eta(M, v);
     double p = 1.0;
     for (double d : deltas) {
-      double phi = 1.0;
-      if (d > 0.0) phi = std::fmin(1.0, (mx - Qf[v]) / d);
-      else if (d < 0.0) phi = std::fmin(1.0, (mn - Qf[v]) / d);
+      double phi_bj = 1.0;
+      if (d > 0.0) phi_bj = std::fmin(1.0, (mx - Qf[v]) / d);
+      else if (d < 0.0) phi_bj = std::fmin(1.0, (mn - Qf[v]) / d);
+      double ramp = (std::fabs(d) - eta) / eta;
+      ramp = ramp < 0.0 ? 0.0 : (ramp > 1.0 ? 1.0 : ramp);
+      const double phi = 1.0 - ramp * (1.0 - phi_bj);
       if (phi < p) p = phi;
     }
     psi[v] = p;
   }
+  // One factor per cell, Psi_ij of Eq. (reconstruction_fluctuation2).
   double psi_cell = psi[0];
   for (int v = 1; v < 4; ++v)
     if (psi[v] < psi_cell) psi_cell = psi[v];

@@ -1,0 +1,720 @@
+// One time step of Eq. (Scheme) (Gaburro, Castro, Dumbser) as a single fused
+// kernel per step plus a one-block finalize kernel:
+//
+//   step_kernel   one CTA per TX x TY tile of cells.
+//     load      Q^n of the tile plus a 2-cell halo into shared memory (SoA,
+//               coalesced rows), with the solid/outside flags and the column
+//               levels K_i;
+//     recon     for the tile plus a 1-cell ring: fluctuations w.r.t. the
+//               cell's water-at-rest state Q^E_ij (alpha^E = alpha_ij,
+//               rho^E from the column level), central slopes, one
+//               Barth-Jespersen factor per cell, order switch, half-step
+//               predictor dQ/dt = -(A1 dQ/dx + A2 dQ/dy) in deviation form,
+//               the four face-midpoint states at t^{n+1/2} (Section 3.4);
+//     faces     every x face (Osher, Gauss-Legendre) and y face (well-balanced
+//               Osher-Romberg) of the tile solved once into shared memory;
+//               walls and solid neighbours see the mirror state;
+//     update    Q^{n+1} = Q^n - dt/dx (D+_W + D-_E + I_x) - dt/dy (D+_S + D-_N + I_y)
+//               with the interior integral of Eq. (b^y_3_final_integral) plus
+//               the conservative part f(q_E) - f(q_W), g(q_N) - g(q_S);
+//     epilogue  max signal rate for the next dt (one atomicMax per CTA) and
+//               the free-surface detector's column sums of Eq.
+//               (Free_surf_detector) in exact 2^-32 fixed point (one atomicAdd
+//               per column per CTA), non-admissible-state flag.
+//   finalize      K_i = round(column sum), dt bookkeeping, accumulator reset.
+//
+// The FP64 instantiation stores the full state; the FP32 instantiation stores
+// the deviation m^f = m - alpha rho^E(y; K_i) so that a state at rest is
+// represented by exact zeros.
+#include <cuda_runtime.h>
+
+#include "fv_kernels.cuh"
+#include "fv_model.cuh"
+
+namespace fv {
+
+namespace {
+
+constexpr int TX = 32, TY = 8;
+constexpr int NT = TX * TY;
+constexpr int WX = TX + 4, WY = TY + 4;  // window: tile + 2-cell halo
+constexpr int RX = TX + 2, RY = TY + 2;  // reconstructed cells: tile + 1 ring
+constexpr int NREC = 20;                 // aE, mEc, mES, mEN, fW[4], fE[4], fS[4], fN[4]
+constexpr unsigned char F_FLUID = 0, F_SOLID = 1, F_OUT = 2;
+constexpr unsigned long long ONE_FIXED = 1ull << 32;
+
+template <typename T>
+struct Smem {
+  union {
+    T w[4][WY][WX];  // load phase: m (FP64: full; FP32: m^f of own level), mu, mv, a
+    struct {
+      T Dx[8][TY][TX + 1];  // face phase: D-[4], D+[4] of x faces
+      T Dy[8][TY + 1][TX];  // y faces
+    } d;
+  } u;
+  T rec[NREC][RY][RX];
+  T cen[6][TY][TX];  // base (centre fluctuation at t^{n+1/2}), dax, day
+  unsigned long long col[TY][TX];
+  double wmax[NT / 32];
+  int K[WX];
+  unsigned char flag[WY][WX];
+};
+
+template <typename T>
+__device__ __forceinline__ T tab(const T* rt, int h, int ny) {
+  return rt[h + 2 * ny];
+}
+
+enum { R_AE = 0, R_MEC = 1, R_MES = 2, R_MEN = 3, R_FW = 4, R_FE = 8, R_FS = 12, R_FN = 16 };
+
+template <typename T, bool DEV>
+__global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? 2 : 4))
+    step_kernel(StepParams p, const T* __restrict__ qin, T* __restrict__ qout,
+                const uint8_t* __restrict__ solid, const int32_t* __restrict__ Kref,
+                const int32_t* __restrict__ Kcur, unsigned long long* __restrict__ colsum,
+                DevScalars* __restrict__ sc, const double* __restrict__ rhoE_d,
+                const T* __restrict__ rt) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem<T>& S = *reinterpret_cast<Smem<T>*>(smem_raw);
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int nx = p.nx, ny = p.ny;
+  const size_t N = (size_t)nx * ny;
+
+  Phys<T> P;
+  P.c = (T)p.c;
+  P.c2 = (T)p.c2;
+  P.inv_c = (T)(1.0 / p.c);
+  P.rho0 = (T)p.rho0;
+  P.k0 = (T)p.k0;
+  P.g = (T)p.g;
+  P.kappa = (T)p.kappa;
+  const T dx = (T)p.dx, dy = (T)p.dy;
+  const T eps = (T)p.eps;
+  const double rate_cur = sc->rate_cur;
+  const double dt_d = rate_cur > 0.0 ? p.cfl / rate_cur : 0.0;
+  const T dt = (T)dt_d;
+
+  // ---------------------------------------------------------------- load
+  for (int idx = tid; idx < WX * WY; idx += NT) {
+    const int wi = idx % WX, wj = idx / WX;
+    const int gi = i0 - 2 + wi, gj = j0 - 2 + wj;
+    unsigned char f = F_OUT;
+    if (gi >= 0 && gj >= 0 && gi < nx && gj < ny) f = solid[(size_t)gj * nx + gi] ? F_SOLID : F_FLUID;
+    S.flag[wj][wi] = f;
+    if (f == F_FLUID) {
+      const size_t c = (size_t)gj * nx + gi;
+      T m = qin[c];
+      const T a = qin[3 * N + c];
+      if (DEV) {
+        const int Kr = Kref[gi], Kc = Kcur[gi];
+        if (Kr != Kc)
+          m += (T)((double)a * (rhoE_d[2 * (gj - Kr) + 1 + 2 * ny] - rhoE_d[2 * (gj - Kc) + 1 + 2 * ny]));
+      }
+      S.u.w[0][wj][wi] = m;
+      S.u.w[1][wj][wi] = qin[N + c];
+      S.u.w[2][wj][wi] = qin[2 * N + c];
+      S.u.w[3][wj][wi] = a;
+    }
+  }
+  for (int idx = tid; idx < WX; idx += NT) {
+    const int gi = i0 - 2 + idx;
+    S.K[idx] = (gi >= 0 && gi < nx) ? Kcur[gi] : 0;
+  }
+  __syncthreads();
+
+  // Own-cell state for the update, kept in registers.
+  const int gi_me = i0 + tx, gj_me = j0 + ty;
+  const bool inside = gi_me < nx && gj_me < ny;
+  const unsigned char flag_me = S.flag[ty + 2][tx + 2];
+  T qold[4] = {0, 0, 0, 0};
+  if (flag_me == F_FLUID) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) qold[v] = S.u.w[v][ty + 2][tx + 2];
+  }
+
+  // ---------------------------------------------------------------- recon
+  // limiter regularisation: 2^-20 rho0, 2^-10 rho0 c (momenta), 2^-20
+  const T bj_eta[4] = {(T)ldexp(p.rho0, -20), (T)ldexp(p.rho0 * p.c, -10),
+                       (T)ldexp(p.rho0 * p.c, -10), (T)ldexp(1.0, -20)};
+  const T bj_inv_eta[4] = {T(1) / bj_eta[0], T(1) / bj_eta[1], T(1) / bj_eta[2],
+                           T(1) / bj_eta[3]};
+  const T half_dx = T(0.5) * dx, half_dy = T(0.5) * dy;
+  const T inv_2dx = T(1) / (T(2) * dx), inv_2dy = T(1) / (T(2) * dy);
+  for (int idx = tid; idx < RX * RY; idx += NT) {
+    const int rx = idx % RX, ry = idx / RX;
+    const int wi = rx + 1, wj = ry + 1;
+    if (S.flag[wj][wi] != F_FLUID) continue;
+    const int gj = j0 - 1 + ry;
+    const int K = S.K[wi];
+    const T aE = S.u.w[3][wj][wi];
+    const T rEc = tab(rt, 2 * (gj - K) + 1, ny);
+    const T rES = tab(rt, 2 * (gj - K), ny);
+    const T rEN = tab(rt, 2 * (gj + 1 - K), ny);
+    const T mEc = aE * rEc;
+    T Qf[4];
+    Qf[0] = DEV ? S.u.w[0][wj][wi] : S.u.w[0][wj][wi] - mEc;
+    Qf[1] = S.u.w[1][wj][wi];
+    Qf[2] = S.u.w[2][wj][wi];
+    Qf[3] = T(0);
+
+    // fluctuation of a neighbour w.r.t. this cell's Q^E; ghost if not fluid
+    auto nbf = [&](int dwi, int dwj, T out[4]) -> bool {
+      const int ni = wi + dwi, nj = wj + dwj;
+      if (S.flag[nj][ni] != F_FLUID) return false;
+      const T an = S.u.w[3][nj][ni];
+      const int gjn = gj + dwj;
+      const T rn = tab(rt, 2 * (gjn - K) + 1, ny);
+      if (DEV) {
+        const int Kn = S.K[ni];
+        T mshift;
+        if (Kn == K) mshift = (an - aE) * rn;
+        else mshift = an * tab(rt, 2 * (gjn - Kn) + 1, ny) - aE * rn;
+        out[0] = S.u.w[0][nj][ni] + mshift;
+      } else {
+        out[0] = S.u.w[0][nj][ni] - aE * rn;
+      }
+      out[1] = S.u.w[1][nj][ni];
+      out[2] = S.u.w[2][nj][ni];
+      out[3] = an - aE;
+      return true;
+    };
+    auto ghost = [&](int dwi, int dwj, int normal, int side, T out[4]) {
+      const unsigned char f = S.flag[wj + dwj][wi + dwi];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) out[v] = Qf[v];
+      if (!(f == F_OUT && p.side[side] == 1)) out[normal] = -out[normal];
+    };
+    T fW[4], fE[4], fS[4], fN[4];
+    if (!nbf(-1, 0, fW)) ghost(-1, 0, 1, 0, fW);
+    if (!nbf(1, 0, fE)) ghost(1, 0, 1, 1, fE);
+    if (!nbf(0, -1, fS)) ghost(0, -1, 2, 2, fS);
+    if (!nbf(0, 1, fN)) ghost(0, 1, 2, 3, fN);
+    T mx[4], mn[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      mx[v] = fmax(fmax(fmax(Qf[v], fW[v]), fmax(fE[v], fS[v])), fN[v]);
+      mn[v] = fmin(fmin(fmin(Qf[v], fW[v]), fmin(fE[v], fS[v])), fN[v]);
+    }
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+      T fd[4];
+      if (nbf((d & 1) ? 1 : -1, (d & 2) ? 1 : -1, fd)) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          mx[v] = fmax(mx[v], fd[v]);
+          mn[v] = fmin(mn[v], fd[v]);
+        }
+      }
+    }
+    T gx[4], gy[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      gx[v] = (fE[v] - fW[v]) * inv_2dx;
+      gy[v] = (fN[v] - fS[v]) * inv_2dy;
+    }
+    // Barth-Jespersen at the four face midpoints, one factor per cell (min
+    // over the four components), Eq. (reconstruction_fluctuation2): the
+    // printed factor for |d| >= 2 eta_v, 1 for |d| <= eta_v, linear between,
+    // so that roundoff in a flat component cannot switch the cell.
+    T psi = T(1);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const T eta = bj_eta[v], inv_eta = bj_inv_eta[v];
+      const T ddx = half_dx * gx[v], ddy = half_dy * gy[v];
+      const T up = mx[v] - Qf[v], dn = mn[v] - Qf[v];
+      const T dd[4] = {-ddx, ddx, -ddy, ddy};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const T d = dd[k];
+        const T ad = tabs(d);
+        if (ad > eta) {
+          const T num = d > T(0) ? up : dn;
+          const T phi_bj = fmin(T(1), num / d);
+          const T ramp = fmin(T(1), (ad - eta) * inv_eta);
+          psi = fmin(psi, T(1) - ramp * (T(1) - phi_bj));
+        }
+      }
+    }
+    const T a_cell = aE;
+    T dtQ[4] = {0, 0, 0, 0};
+    if (a_cell <= T(10) * eps) {
+      psi = T(0);
+    } else {
+      const T m = mEc + Qf[0];
+      const Vel<T> vel = velocity(m, Qf[1], Qf[2]);
+      const T u = vel.u, v = vel.v;
+      T sx[4], sy[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        sx[c] = psi * gx[c];
+        sy[c] = psi * gy[c];
+      }
+      const T dmE = aE * (-P.kappa * rEc);
+      const T uv = u * v;
+      const T a1 = sx[1];
+      const T a2 = (P.c2 - u * u) * sx[0] + T(2) * u * sx[1] - P.k0 * sx[3];
+      const T a3 = -uv * sx[0] + v * sx[1] + u * sx[2];
+      const T a4 = u * sx[3];
+      const T b1 = sy[2];
+      const T b2 = -uv * sy[0] + v * sy[1] + u * sy[2] - uv * dmE;
+      const T b3 = (P.c2 - v * v) * sy[0] + T(2) * v * sy[2] - P.k0 * sy[3] - v * v * dmE + P.g * Qf[0];
+      const T b4 = v * sy[3];
+      dtQ[0] = -(a1 + b1);
+      dtQ[1] = -(a2 + b2);
+      dtQ[2] = -(a3 + b3);
+      dtQ[3] = -(a4 + b4);
+    }
+    const T half_dt = T(0.5) * dt;
+    T base[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      base[c] = Qf[c] + half_dt * dtQ[c];
+      const T sxh = psi * gx[c] * half_dx, syh = psi * gy[c] * half_dy;
+      fW[c] = base[c] - sxh;
+      fE[c] = base[c] + sxh;
+      fS[c] = base[c] - syh;
+      fN[c] = base[c] + syh;
+    }
+    const T mES = aE * rES, mEN = aE * rEN;
+    // Admissibility of the reconstructed states; otherwise first order.
+    const bool ok = (mEc + fW[0] > T(0)) && (aE + fW[3] > T(0)) && (mEc + fE[0] > T(0)) &&
+                    (aE + fE[3] > T(0)) && (mES + fS[0] > T(0)) && (aE + fS[3] > T(0)) &&
+                    (mEN + fN[0] > T(0)) && (aE + fN[3] > T(0)) && (mEc + base[0] > T(0)) &&
+                    (aE + base[3] > T(0));
+    if (!ok) {
+      psi = T(0);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) fW[c] = fE[c] = fS[c] = fN[c] = base[c] = Qf[c];
+    }
+    S.rec[R_AE][ry][rx] = aE;
+    S.rec[R_MEC][ry][rx] = mEc;
+    S.rec[R_MES][ry][rx] = mES;
+    S.rec[R_MEN][ry][rx] = mEN;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      S.rec[R_FW + c][ry][rx] = fW[c];
+      S.rec[R_FE + c][ry][rx] = fE[c];
+      S.rec[R_FS + c][ry][rx] = fS[c];
+      S.rec[R_FN + c][ry][rx] = fN[c];
+    }
+    if (rx >= 1 && rx <= TX && ry >= 1 && ry <= TY) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) S.cen[c][ry - 1][rx - 1] = base[c];
+      S.cen[4][ry - 1][rx - 1] = psi * gx[3];
+      S.cen[5][ry - 1][rx - 1] = psi * gy[3];
+    }
+  }
+  __syncthreads();  // window no longer needed: its storage becomes Dx/Dy
+
+  // ---------------------------------------------------------------- faces
+  for (int idx = tid; idx < (TX + 1) * TY + TX * (TY + 1); idx += NT) {
+    T Dm[4] = {0, 0, 0, 0}, Dp[4] = {0, 0, 0, 0};
+    if (idx < (TX + 1) * TY) {
+      const int fx = idx % (TX + 1), fy = idx / (TX + 1);
+      const int rxL = fx, rxR = fx + 1, ry = fy + 1;
+      const bool L = S.flag[ry + 1][rxL + 1] == F_FLUID;
+      const bool R = S.flag[ry + 1][rxR + 1] == F_FLUID;
+      if (L || R) {
+        T qm[4], qp[4], dq[4];
+        if (L && R) {
+          const T mEL = S.rec[R_MEC][ry][rxL], mER = S.rec[R_MEC][ry][rxR];
+          const T aL = S.rec[R_AE][ry][rxL], aR = S.rec[R_AE][ry][rxR];
+          T fl[4], fr[4];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            fl[c] = S.rec[R_FE + c][ry][rxL];
+            fr[c] = S.rec[R_FW + c][ry][rxR];
+          }
+          qm[0] = mEL + fl[0]; qm[1] = fl[1]; qm[2] = fl[2]; qm[3] = aL + fl[3];
+          qp[0] = mER + fr[0]; qp[1] = fr[1]; qp[2] = fr[2]; qp[3] = aR + fr[3];
+          dq[0] = (mER - mEL) + (fr[0] - fl[0]);
+          dq[1] = fr[1] - fl[1];
+          dq[2] = fr[2] - fl[2];
+          dq[3] = (aR - aL) + (fr[3] - fl[3]);
+        } else {
+          const int rx = L ? rxL : rxR;
+          const int base_i = L ? R_FE : R_FW;
+          const T mE = S.rec[R_MEC][ry][rx], aE = S.rec[R_AE][ry][rx];
+          T q[4];
+          q[0] = mE + S.rec[base_i][ry][rx];
+          q[1] = S.rec[base_i + 1][ry][rx];
+          q[2] = S.rec[base_i + 2][ry][rx];
+          q[3] = aE + S.rec[base_i + 3][ry][rx];
+          const bool outside = L ? (S.flag[ry + 1][rxR + 1] == F_OUT) : (S.flag[ry + 1][rxL + 1] == F_OUT);
+          const bool transmissive = outside && p.side[L ? 1 : 0] == 1;
+          T g[4] = {q[0], transmissive ? q[1] : -q[1], q[2], q[3]};
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            qm[c] = L ? q[c] : g[c];
+            qp[c] = L ? g[c] : q[c];
+          }
+          dq[0] = T(0);
+          dq[1] = qp[1] - qm[1];
+          dq[2] = T(0);
+          dq[3] = T(0);
+        }
+        xface(qm, qp, dq, P, Dm, Dp);
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        S.u.d.Dx[c][fy][fx] = Dm[c];
+        S.u.d.Dx[4 + c][fy][fx] = Dp[c];
+      }
+    } else {
+      const int k = idx - (TX + 1) * TY;
+      const int fx = k % TX, fy = k / TX;
+      const int rx = fx + 1, ryB = fy, ryT = fy + 1;
+      const bool B = S.flag[ryB + 1][rx + 1] == F_FLUID;
+      const bool Tt = S.flag[ryT + 1][rx + 1] == F_FLUID;
+      if (B || Tt) {
+        T qm[4], qp[4], dq[4];
+        if (B && Tt) {
+          const T mEB = S.rec[R_MEN][ryB][rx], mET = S.rec[R_MES][ryT][rx];
+          const T aB = S.rec[R_AE][ryB][rx], aT = S.rec[R_AE][ryT][rx];
+          T fb[4], ft[4];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            fb[c] = S.rec[R_FN + c][ryB][rx];
+            ft[c] = S.rec[R_FS + c][ryT][rx];
+          }
+          qm[0] = mEB + fb[0]; qm[1] = fb[1]; qm[2] = fb[2]; qm[3] = aB + fb[3];
+          qp[0] = mET + ft[0]; qp[1] = ft[1]; qp[2] = ft[2]; qp[3] = aT + ft[3];
+          dq[0] = (mET - mEB) + (ft[0] - fb[0]);
+          dq[1] = ft[1] - fb[1];
+          dq[2] = ft[2] - fb[2];
+          dq[3] = (aT - aB) + (ft[3] - fb[3]);
+        } else {
+          const int ry = B ? ryB : ryT;
+          const int base_i = B ? R_FN : R_FS;
+          const T mE = S.rec[B ? R_MEN : R_MES][ry][rx], aE = S.rec[R_AE][ry][rx];
+          T q[4];
+          q[0] = mE + S.rec[base_i][ry][rx];
+          q[1] = S.rec[base_i + 1][ry][rx];
+          q[2] = S.rec[base_i + 2][ry][rx];
+          q[3] = aE + S.rec[base_i + 3][ry][rx];
+          const bool outside = B ? (S.flag[ryT + 1][rx + 1] == F_OUT) : (S.flag[ryB + 1][rx + 1] == F_OUT);
+          const bool transmissive = outside && p.side[B ? 3 : 2] == 1;
+          T g[4] = {q[0], q[1], transmissive ? q[2] : -q[2], q[3]};
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            qm[c] = B ? q[c] : g[c];
+            qp[c] = B ? g[c] : q[c];
+          }
+          dq[0] = T(0);
+          dq[1] = T(0);
+          dq[2] = qp[2] - qm[2];
+          dq[3] = T(0);
+        }
+        yface(qm, qp, dq, P, Dm, Dp);
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        S.u.d.Dy[c][fy][fx] = Dm[c];
+        S.u.d.Dy[4 + c][fy][fx] = Dp[c];
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---------------------------------------------------------------- update
+  double my_rate = 0.0;
+  unsigned long long my_w = 0;
+  bool bad = false;
+  if (inside && flag_me == F_FLUID) {
+    const int rx = tx + 1, ry = ty + 1;
+    const int K = S.K[tx + 2];
+    const T aE = S.rec[R_AE][ry][rx];
+    const T mEc = S.rec[R_MEC][ry][rx], mES = S.rec[R_MES][ry][rx], mEN = S.rec[R_MEN][ry][rx];
+    T fW[4], fE[4], fS[4], fN[4], base[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      fW[c] = S.rec[R_FW + c][ry][rx];
+      fE[c] = S.rec[R_FE + c][ry][rx];
+      fS[c] = S.rec[R_FS + c][ry][rx];
+      fN[c] = S.rec[R_FN + c][ry][rx];
+      base[c] = S.cen[c][ty][tx];
+    }
+    const T dax = S.cen[4][ty][tx], day = S.cen[5][ty][tx];
+    // interior integral: conservative part + B grad q, mid-point rule
+    const Vel<T> vE = velocity(mEc + fE[0], fE[1], fE[2]);
+    const Vel<T> vW = velocity(mEc + fW[0], fW[1], fW[2]);
+    const Vel<T> vN = velocity(mEN + fN[0], fN[1], fN[2]);
+    const Vel<T> vS = velocity(mES + fS[0], fS[1], fS[2]);
+    const Vel<T> vc = velocity(mEc + base[0], base[1], base[2]);
+    T Ix[4], Iy[4];
+    Ix[0] = fE[1] - fW[1];
+    Ix[1] = (fE[1] * vE.u - fW[1] * vW.u) + P.c2 * ((fE[0] - fW[0]) - P.rho0 * (fE[3] - fW[3]));
+    Ix[2] = fE[1] * vE.v - fW[1] * vW.v;
+    Ix[3] = dx * vc.u * dax;
+    Iy[0] = fN[2] - fS[2];
+    Iy[1] = fN[1] * vN.v - fS[1] * vS.v;
+    Iy[2] = (fN[2] * vN.v - fS[2] * vS.v) + P.c2 * ((fN[0] - fS[0]) - P.rho0 * (fN[3] - fS[3])) +
+            P.g * dy * base[0];
+    Iy[3] = dy * vc.v * day;
+    const T rdx = dt / dx, rdy = dt / dy;
+    T xs[4], ys[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      xs[c] = S.u.d.Dx[4 + c][ty][tx] + S.u.d.Dx[c][ty][tx + 1] + Ix[c];
+      ys[c] = S.u.d.Dy[4 + c][ty][tx] + S.u.d.Dy[c][ty + 1][tx] + Iy[c];
+    }
+    T qn[4];
+    T m_full;
+    if (DEV) {
+      // deviation form: m^f_new = m^f + dm - rho^E_c da (own level, own new alpha)
+      T dQ[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) dQ[c] = -rdx * xs[c] - rdy * ys[c];
+      const T rEc = tab(rt, 2 * (gj_me - K) + 1, ny);
+      qn[0] = qold[0] + (dQ[0] - rEc * dQ[3]);
+      qn[1] = qold[1] + dQ[1];
+      qn[2] = qold[2] + dQ[2];
+      qn[3] = qold[3] + dQ[3];
+      m_full = qn[3] * rEc + qn[0];
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) qn[c] = qold[c] - rdx * xs[c] - rdy * ys[c];
+      m_full = qn[0];
+    }
+    const size_t c = (size_t)gj_me * nx + gi_me;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) qout[v * N + c] = qn[v];
+    // epilogue: admissibility, signal rate, detector weight
+    const double md = (double)m_full, ad = (double)qn[3];
+    const double ud = (double)qn[1] / md, vd = (double)qn[2] / md;
+    if (!(md > 0.0) || !(ad > 0.0) || !isfinite(ud) || !isfinite(vd) || !isfinite(ad)) bad = true;
+    my_rate = (fabs(ud) + p.c) / p.dx + (fabs(vd) + p.c) / p.dy;
+    if (!(my_rate >= 0.0)) my_rate = 0.0;
+    double w = (ad - p.eps) / (1.0 - p.eps);
+    w = w < 0.0 ? 0.0 : (w > 1.0 ? 1.0 : w);
+    my_w = (unsigned long long)__double2ll_rn(w * 4294967296.0);
+  } else if (inside) {
+    const size_t c = (size_t)gj_me * nx + gi_me;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) qout[v * N + c] = T(0);
+    if (flag_me == F_SOLID) my_w = ONE_FIXED;
+  }
+  if (bad) atomicOr(&sc->status, 1);
+  // column sums
+  S.col[ty][tx] = my_w;
+  // rate max
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) my_rate = fmax(my_rate, __shfl_xor_sync(0xffffffffu, my_rate, o));
+  if ((tid & 31) == 0) S.wmax[tid >> 5] = my_rate;
+  __syncthreads();
+  if (ty == 0 && inside) {
+    unsigned long long s = 0;
+#pragma unroll
+    for (int r = 0; r < TY; ++r) s += S.col[r][tx];
+    if (s) atomicAdd(&colsum[gi_me], s);
+  }
+  if (tid == 0) {
+    double mrate = 0.0;
+#pragma unroll
+    for (int k = 0; k < NT / 32; ++k) mrate = fmax(mrate, S.wmax[k]);
+    if (mrate > 0.0) atomicMax(&sc->rate_acc, (unsigned long long)__double_as_longlong(mrate));
+  }
+}
+
+// ----------------------------------------------------------------------------
+__global__ void finalize_kernel(StepParams p, int32_t* Kref, int32_t* Kcur,
+                                unsigned long long* colsum, DevScalars* sc, int count_step) {
+  for (int i = threadIdx.x; i < p.nx; i += blockDim.x) {
+    Kref[i] = Kcur[i];
+    Kcur[i] = (int32_t)((colsum[i] + (1ull << 31)) >> 32);
+    colsum[i] = 0ull;
+  }
+  if (threadIdx.x == 0) {
+    if (count_step) {
+      const double dt = sc->rate_cur > 0.0 ? p.cfl / sc->rate_cur : 0.0;
+      sc->t += dt;
+      sc->dt_last = dt;
+      sc->steps += 1;
+    }
+    sc->rate_cur = __longlong_as_double((long long)sc->rate_acc);
+    sc->rate_acc = 0ull;
+  }
+}
+
+__global__ void prologue_kernel(StepParams p, const double* __restrict__ q,
+                                const uint8_t* __restrict__ solid, unsigned long long* colsum,
+                                DevScalars* sc) {
+  const size_t N = (size_t)p.nx * p.ny;
+  double my_rate = 0.0;
+  bool bad = false;
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < N;
+       c += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(c % p.nx);
+    if (solid[c]) {
+      atomicAdd(&colsum[i], ONE_FIXED);
+      continue;
+    }
+    const double m = q[c], mu = q[N + c], mv = q[2 * N + c], a = q[3 * N + c];
+    const double u = mu / m, v = mv / m;
+    if (!(m > 0.0) || !(a > 0.0) || !isfinite(u) || !isfinite(v) || !isfinite(a)) bad = true;
+    double r = (fabs(u) + p.c) / p.dx + (fabs(v) + p.c) / p.dy;
+    if (r >= 0.0) my_rate = fmax(my_rate, r);
+    double w = (a - p.eps) / (1.0 - p.eps);
+    w = w < 0.0 ? 0.0 : (w > 1.0 ? 1.0 : w);
+    const unsigned long long qw = (unsigned long long)__double2ll_rn(w * 4294967296.0);
+    if (qw) atomicAdd(&colsum[i], qw);
+  }
+  if (bad) atomicOr(&sc->status, 1);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) my_rate = fmax(my_rate, __shfl_xor_sync(0xffffffffu, my_rate, o));
+  if ((threadIdx.x & 31) == 0 && my_rate > 0.0)
+    atomicMax(&sc->rate_acc, (unsigned long long)__double_as_longlong(my_rate));
+}
+
+__global__ void to_dev_kernel(StepParams p, const double* __restrict__ q,
+                              const uint8_t* __restrict__ solid, const int32_t* __restrict__ K,
+                              const double* __restrict__ rhoE, float* __restrict__ out) {
+  const size_t N = (size_t)p.nx * p.ny;
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < N;
+       c += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(c % p.nx), j = (int)(c / p.nx);
+    if (solid[c]) {
+      for (int v = 0; v < 4; ++v) out[v * N + c] = 0.f;
+      continue;
+    }
+    const double a = q[3 * N + c];
+    out[c] = (float)(q[c] - a * rhoE[2 * (j - K[i]) + 1 + 2 * p.ny]);
+    out[N + c] = (float)q[N + c];
+    out[2 * N + c] = (float)q[2 * N + c];
+    out[3 * N + c] = (float)a;
+  }
+}
+
+__global__ void from_dev_kernel(StepParams p, const float* __restrict__ in,
+                                const uint8_t* __restrict__ solid, const int32_t* __restrict__ K,
+                                const double* __restrict__ rhoE, double* __restrict__ q) {
+  const size_t N = (size_t)p.nx * p.ny;
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < N;
+       c += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(c % p.nx), j = (int)(c / p.nx);
+    if (solid[c]) {
+      for (int v = 0; v < 4; ++v) q[v * N + c] = 0.0;
+      continue;
+    }
+    const double a = (double)in[3 * N + c];
+    q[c] = a * rhoE[2 * (j - K[i]) + 1 + 2 * p.ny] + (double)in[c];
+    q[N + c] = (double)in[N + c];
+    q[2 * N + c] = (double)in[2 * N + c];
+    q[3 * N + c] = a;
+  }
+}
+
+__global__ void zero_solid_kernel(StepParams p, double* q, const uint8_t* solid) {
+  const size_t N = (size_t)p.nx * p.ny;
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < N;
+       c += (size_t)gridDim.x * blockDim.x)
+    if (solid[c])
+      for (int v = 0; v < 4; ++v) q[v * N + c] = 0.0;
+}
+
+// Deterministic mass: fixed chunk per block, fixed tree, then one block.
+constexpr int MASS_T = 256;
+__global__ void mass_partial_kernel(StepParams p, const double* __restrict__ q,
+                                    const uint8_t* __restrict__ solid, double* partial) {
+  __shared__ double s[MASS_T];
+  const size_t N = (size_t)p.nx * p.ny;
+  const size_t chunk = (N + gridDim.x - 1) / gridDim.x;
+  const size_t b0 = blockIdx.x * chunk, b1 = b0 + chunk < N ? b0 + chunk : N;
+  double acc = 0.0;
+  for (size_t c = b0 + threadIdx.x; c < b1; c += MASS_T)
+    if (!solid[c]) acc += q[c];
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = MASS_T / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = s[0];
+}
+
+__global__ void mass_final_kernel(const double* partial, int n, double scale, double* out) {
+  __shared__ double s[MASS_T];
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < n; k += MASS_T) acc += partial[k];
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = MASS_T / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = s[0] * scale;
+}
+
+int grid_1d(size_t n) {
+  size_t b = (n + 255) / 256;
+  if (b > 152 * 32) b = 152 * 32;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+template <typename T, bool DEV>
+void launch_step_t(const StepParams& p, const T* in, T* out, const uint8_t* solid,
+                   const int32_t* Kref, const int32_t* Kcur, unsigned long long* colsum,
+                   DevScalars* sc, const double* rhoE_d, const T* rt, cudaStream_t st) {
+  const size_t smem = sizeof(Smem<T>);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(step_kernel<T, DEV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    attr_set = true;
+  }
+  dim3 block(TX, TY);
+  dim3 grid((p.nx + TX - 1) / TX, (p.ny + TY - 1) / TY);
+  step_kernel<T, DEV><<<grid, block, smem, st>>>(p, in, out, solid, Kref, Kcur, colsum, sc,
+                                                  rhoE_d, rt);
+}
+
+}  // namespace
+
+void launch_step_f64(const StepParams& p, const StateF64& s, const uint8_t* solid,
+                     const int32_t* Kcur, unsigned long long* colsum, DevScalars* sc,
+                     const Tables& tb, cudaStream_t st) {
+  launch_step_t<double, false>(p, s.in, s.out, solid, Kcur, Kcur, colsum, sc, tb.rhoE_d,
+                               tb.rhoE_d, st);
+}
+
+void launch_step_f32(const StepParams& p, const StateF32& s, const uint8_t* solid,
+                     const int32_t* Kref, const int32_t* Kcur, unsigned long long* colsum,
+                     DevScalars* sc, const Tables& tb, cudaStream_t st) {
+  launch_step_t<float, true>(p, s.in, s.out, solid, Kref, Kcur, colsum, sc, tb.rhoE_d,
+                             tb.rhoE_f, st);
+}
+
+void launch_finalize(const StepParams& p, int32_t* Kref, int32_t* Kcur,
+                     unsigned long long* colsum, DevScalars* sc, int count_step,
+                     cudaStream_t st) {
+  finalize_kernel<<<1, 1024, 0, st>>>(p, Kref, Kcur, colsum, sc, count_step);
+}
+
+void launch_prologue_f64(const StepParams& p, const double* q, const uint8_t* solid,
+                         unsigned long long* colsum, DevScalars* sc, cudaStream_t st) {
+  prologue_kernel<<<grid_1d((size_t)p.nx * p.ny), 256, 0, st>>>(p, q, solid, colsum, sc);
+}
+
+void launch_to_dev(const StepParams& p, const double* q, const uint8_t* solid, const int32_t* K,
+                   const Tables& tb, float* out, cudaStream_t st) {
+  to_dev_kernel<<<grid_1d((size_t)p.nx * p.ny), 256, 0, st>>>(p, q, solid, K, tb.rhoE_d, out);
+}
+
+void launch_from_dev(const StepParams& p, const float* in, const uint8_t* solid,
+                     const int32_t* K, const Tables& tb, double* q, cudaStream_t st) {
+  from_dev_kernel<<<grid_1d((size_t)p.nx * p.ny), 256, 0, st>>>(p, in, solid, K, tb.rhoE_d, q);
+}
+
+void launch_zero_solid(const StepParams& p, double* q, const uint8_t* solid, cudaStream_t st) {
+  zero_solid_kernel<<<grid_1d((size_t)p.nx * p.ny), 256, 0, st>>>(p, q, solid);
+}
+
+void launch_mass(const StepParams& p, const double* q, const uint8_t* solid, double* partial,
+                 int nblocks, double* out, cudaStream_t st) {
+  mass_partial_kernel<<<nblocks, MASS_T, 0, st>>>(p, q, solid, partial);
+  mass_final_kernel<<<1, MASS_T, 0, st>>>(partial, nblocks, p.dx * p.dy, out);
+}
+
+}  // namespace fv

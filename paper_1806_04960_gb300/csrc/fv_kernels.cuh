@@ -1,0 +1,67 @@
+// Kernels of one time step of the well-balanced path-conservative scheme
+// (Gaburro, Castro, Dumbser, Eq. (Scheme)) and the launch helpers used by the
+// C ABI.  Internal header of libfv.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fv {
+
+// Per-launch parameters shared by both precisions (doubles, converted in-kernel).
+struct StepParams {
+  int nx, ny;
+  double dx, dy;
+  double rho0, k0, g, eps, c, c2, kappa;
+  int side[4];            // W, E, S, N: 0 wall, 1 transmissive
+  double cfl;
+};
+
+// Device-resident step bookkeeping (one per domain).
+struct DevScalars {
+  double rate_cur;        // max signal rate of the state the next step starts from
+  unsigned long long rate_acc;  // bits of the max rate being accumulated (>= 0 doubles)
+  double t;               // simulated time
+  double dt_last;         // dt of the last step
+  long long steps;
+  int status;             // bit 0: non-admissible state produced
+  int pad;
+};
+
+// Equilibrium density table: rhoE[h + 2 ny] = rho0 exp(-kappa (h dy / 2)) for
+// h in [-2 ny, 2 ny] (h counts half cells between a point and the level y0).
+struct Tables {
+  const double* rhoE_d;   // 4 ny + 1 doubles
+  const float* rhoE_f;    // same, rounded to float
+};
+
+struct StateF64 {
+  const double* in;       // 4 planes of nx*ny, full conserved state
+  double* out;
+};
+
+struct StateF32 {
+  const float* in;        // 4 planes: m^f, mu, mv, a (m^f relative to Kref)
+  float* out;             // written relative to Kcur
+};
+
+void launch_step_f64(const StepParams& p, const StateF64& s, const uint8_t* solid,
+                     const int32_t* Kcur, unsigned long long* colsum, DevScalars* sc,
+                     const Tables& tb, cudaStream_t st);
+void launch_step_f32(const StepParams& p, const StateF32& s, const uint8_t* solid,
+                     const int32_t* Kref, const int32_t* Kcur, unsigned long long* colsum,
+                     DevScalars* sc, const Tables& tb, cudaStream_t st);
+void launch_finalize(const StepParams& p, int32_t* Kref, int32_t* Kcur,
+                     unsigned long long* colsum, DevScalars* sc, int count_step,
+                     cudaStream_t st);
+void launch_prologue_f64(const StepParams& p, const double* q, const uint8_t* solid,
+                         unsigned long long* colsum, DevScalars* sc, cudaStream_t st);
+void launch_to_dev(const StepParams& p, const double* q, const uint8_t* solid,
+                   const int32_t* K, const Tables& tb, float* out, cudaStream_t st);
+void launch_from_dev(const StepParams& p, const float* in, const uint8_t* solid,
+                     const int32_t* K, const Tables& tb, double* q, cudaStream_t st);
+void launch_mass(const StepParams& p, const double* q, const uint8_t* solid, double* partial,
+                 int nblocks, double* out, cudaStream_t st);
+void launch_zero_solid(const StepParams& p, double* q, const uint8_t* solid, cudaStream_t st);
+
+}  // namespace fv

@@ -1,0 +1,220 @@
+"""Thin ctypes binding of libfv (include/fv.h), same names as the C ABI.
+
+Argument marshalling only: every step of the solver runs in the CUDA library.
+Arrays are numpy (host) or torch CUDA tensors (device, zero copy, on the
+handle's stream).  There is no fallback: if libfv.so is missing or cannot be
+loaded, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfv.so")
+
+FV_OK, FV_EINVAL, FV_ENOMEM, FV_ECUDA, FV_ENONFINITE, FV_ETIMEOUT = range(6)
+FV_FP64, FV_FP32_DEV = 0, 1
+FV_BC_WALL, FV_BC_TRANSMISSIVE = 0, 1
+STATUS_NAMES = {0: "FV_OK", 1: "FV_EINVAL", 2: "FV_ENOMEM", 3: "FV_ECUDA",
+                4: "FV_ENONFINITE", 5: "FV_ETIMEOUT"}
+
+
+class fv_grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("x0", C.c_double), ("y0", C.c_double),
+                ("dx", C.c_double), ("dy", C.c_double)]
+
+
+class fv_eos(C.Structure):
+    _fields_ = [("rho0", C.c_double), ("k0", C.c_double), ("gamma", C.c_double),
+                ("g", C.c_double), ("eps_gas", C.c_double)]
+
+
+class fv_bc(C.Structure):
+    _fields_ = [("side", C.c_int32 * 4), ("solid", C.POINTER(C.c_uint8))]
+
+
+class fv_diag(C.Structure):
+    _fields_ = [("t", C.c_double), ("steps", C.c_int64), ("dt_next", C.c_double),
+                ("mass", C.c_double), ("status", C.c_int32)]
+
+
+class FvError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libfv.so not built at {LIB_PATH}; run paper_1806_04960_gb300/build.py")
+_lib = C.CDLL(LIB_PATH)
+_H = C.c_void_p
+_D = C.POINTER(C.c_double)
+_lib.fv_create.argtypes = [C.POINTER(fv_grid), C.POINTER(fv_eos), C.POINTER(fv_bc), C.c_int,
+                           C.c_void_p, C.POINTER(_H)]
+_lib.fv_set_state.argtypes = [_H, C.c_void_p, C.c_int]
+_lib.fv_step.argtypes = [_H, C.c_int32, C.c_double, _D]
+_lib.fv_get_state.argtypes = [_H, C.c_void_p, C.c_int]
+_lib.fv_get_levels.argtypes = [_H, C.POINTER(C.c_int32)]
+_lib.fv_get_diag.argtypes = [_H, C.POINTER(fv_diag)]
+_lib.fv_destroy.argtypes = [_H]
+_lib.fv_destroy.restype = None
+_lib.fv_last_error.restype = C.c_char_p
+_lib.fv_version.restype = C.c_char_p
+for _f in ("fv_create", "fv_set_state", "fv_step", "fv_get_state", "fv_get_levels", "fv_get_diag"):
+    getattr(_lib, _f).restype = C.c_int
+
+_lib.fv_host_xface.argtypes = [_D, _D, _D, _D, _D]
+_lib.fv_host_yface.argtypes = [_D, _D, _D, _D, _D]
+_lib.fv_host_xface.restype = C.c_int
+_lib.fv_host_yface.restype = C.c_int
+
+ABI_SYMBOLS = ("fv_create", "fv_set_state", "fv_step", "fv_get_state", "fv_get_levels",
+               "fv_get_diag", "fv_destroy", "fv_last_error", "fv_version", "fv_host_xface",
+               "fv_host_yface")
+
+
+def _check(st):
+    if st != FV_OK:
+        raise FvError(st, _lib.fv_last_error().decode())
+
+
+def fv_version() -> str:
+    return _lib.fv_version().decode()
+
+
+def fv_last_error() -> str:
+    return _lib.fv_last_error().decode()
+
+
+def _ptr(x):
+    """(address, on_device) of a contiguous float64 numpy array or torch tensor."""
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags.c_contiguous:
+            raise ValueError("state arrays must be C-contiguous float64")
+        return x.ctypes.data, 0
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(x, torch.Tensor):
+        if x.dtype != torch.float64 or not x.is_contiguous():
+            raise ValueError("state tensors must be contiguous float64")
+        return x.data_ptr(), 1 if x.is_cuda else 0
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _host_face(fun, qm, qp, model):
+    m = np.ascontiguousarray(model, dtype=np.float64)
+    a = np.ascontiguousarray(qm, dtype=np.float64)
+    b = np.ascontiguousarray(qp, dtype=np.float64)
+    Dm, Dp = np.zeros(4), np.zeros(4)
+    P = lambda x: x.ctypes.data_as(_D)
+    _check(fun(P(m), P(a), P(b), P(Dm), P(Dp)) and FV_EINVAL)
+    return Dm, Dp
+
+
+def fv_host_xface(qm, qp, model):
+    """Host evaluation of the kernels' x-face fluctuations (D-, D+)."""
+    return _host_face(_lib.fv_host_xface, qm, qp, model)
+
+
+def fv_host_yface(qm, qp, model):
+    """Host evaluation of the kernels' y-face fluctuations (D-, D+)."""
+    return _host_face(_lib.fv_host_yface, qm, qp, model)
+
+
+def fv_create(grid: fv_grid, eos: fv_eos, bc: fv_bc, prec: int, stream: int = 0):
+    h = _H()
+    _check(_lib.fv_create(C.byref(grid), C.byref(eos), C.byref(bc), int(prec),
+                          C.c_void_p(stream), C.byref(h)))
+    return h
+
+
+def fv_set_state(h, q) -> None:
+    p, dev = _ptr(q)
+    _check(_lib.fv_set_state(h, C.c_void_p(p), dev))
+
+
+def fv_step(h, n: int, cfl: float, want_time: bool = False):
+    if want_time:
+        t = C.c_double(0.0)
+        _check(_lib.fv_step(h, int(n), float(cfl), C.byref(t)))
+        return t.value
+    _check(_lib.fv_step(h, int(n), float(cfl), None))
+    return None
+
+
+def fv_get_state(h, out) -> None:
+    p, dev = _ptr(out)
+    _check(_lib.fv_get_state(h, C.c_void_p(p), dev))
+
+
+def fv_get_levels(h, nx: int) -> np.ndarray:
+    K = np.zeros(nx, dtype=np.int32)
+    _check(_lib.fv_get_levels(h, K.ctypes.data_as(C.POINTER(C.c_int32))))
+    return K
+
+
+def fv_get_diag(h) -> fv_diag:
+    d = fv_diag()
+    _check(_lib.fv_get_diag(h, C.byref(d)))
+    return d
+
+
+def fv_destroy(h) -> None:
+    _lib.fv_destroy(h)
+
+
+class Solver:
+    """Convenience wrapper: one handle for one case (see cases.Case)."""
+
+    def __init__(self, case, prec: int = FV_FP64, stream: int | None = None):
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+            except ImportError:  # pragma: no cover
+                stream = 0
+        self.case = case
+        self.prec = prec
+        self.stream = stream
+        self.grid = fv_grid(case.nx, case.ny, case.x0, case.y0, case.dx, case.dy)
+        self.eos = fv_eos(case.rho0, case.k0, case.gamma, case.g, case.eps)
+        self._solid = np.ascontiguousarray(case.solid, dtype=np.uint8)
+        self.bc = fv_bc((C.c_int32 * 4)(*case.sides),
+                        self._solid.ctypes.data_as(C.POINTER(C.c_uint8)))
+        self.h = fv_create(self.grid, self.eos, self.bc, prec, stream)
+
+    def set_state(self, q) -> None:
+        if isinstance(q, np.ndarray):
+            q = np.ascontiguousarray(q, dtype=np.float64)
+        fv_set_state(self.h, q)
+
+    def step(self, n: int, cfl: float | None = None, want_time: bool = False):
+        return fv_step(self.h, n, self.case.cfl if cfl is None else cfl, want_time)
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.empty((4, self.case.ny, self.case.nx), dtype=np.float64)
+        fv_get_state(self.h, out)
+        return out
+
+    def levels(self) -> np.ndarray:
+        return fv_get_levels(self.h, self.case.nx)
+
+    def diag(self) -> fv_diag:
+        return fv_get_diag(self.h)
+
+    def close(self) -> None:
+        if self.h:
+            fv_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,280 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Tolerances:
+  * FP64: relative L-infinity (per conserved component, relative to that
+    component's max magnitude) <= 1e-10 after 200 steps of the 128 x 64 dam
+    break; dt and the detected levels must be identical step by step.
+  * FP32 deviation form: relative L1 <= 1e-4 in alpha rho and alpha, a stated
+    bound for momentum; lake at rest stays at rest to float roundoff.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1806_04960_gb300 import cases
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fv():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1806_04960_gb300 import build
+    build.build()
+    from paper_1806_04960_gb300 import fv as mod
+    return mod
+
+
+def rel_linf(a, b):
+    out = []
+    for v in range(4):
+        scale = np.abs(b[v]).max()
+        out.append(np.abs(a[v] - b[v]).max() / (scale if scale > 0 else 1.0))
+    return np.array(out)
+
+
+def rel_l1(a, b):
+    out = []
+    for v in range(4):
+        scale = np.abs(b[v]).sum()
+        out.append(np.abs(a[v] - b[v]).sum() / (scale if scale > 0 else 1.0))
+    return np.array(out)
+
+
+def gpu_run(fv, case, nsteps, prec=0, q=None, cfl=None):
+    s = fv.Solver(case, prec)
+    s.set_state(case.q if q is None else q)
+    t = s.step(nsteps, cfl, want_time=True)
+    out = s.get_state()
+    K = s.levels()
+    d = s.diag()
+    s.close()
+    return out, t, K, d
+
+
+# ------------------------------------------------------------------ FP64
+
+def test_fp64_dambreak_200_steps_matches_oracle(fv):
+    """200 steps of the 128 x 64 dam break at CFL 0.45.  (At CFL 0.9 the
+    unsplit MUSCL-Hancock step amplifies roundoff in the wall row after about
+    140 steps, so two orderings of the same arithmetic separate; see the
+    next test for CFL 0.9.)"""
+    c = cases.c1()
+    qo, to, dts, _ = O.run(c, 200, cfl=0.45)
+    qg, tg, _, d = gpu_run(fv, c, 200, cfl=0.45)
+    err = rel_linf(qg, qo)
+    assert np.all(err <= 1e-10), err
+    assert abs(tg - to) <= 1e-12 * to
+    assert d.status == 0 and d.steps == 200
+
+
+def test_fp64_dambreak_cfl09_matches_oracle(fv):
+    c = cases.c1()
+    qo, to, _, _ = O.run(c, 100)
+    qg, tg, _, d = gpu_run(fv, c, 100)
+    err = rel_linf(qg, qo)
+    assert np.all(err <= 1e-10), err
+    assert abs(tg - to) <= 1e-12 * to
+
+
+def test_fp64_dt_and_levels_identical_each_step(fv):
+    c = cases.c1()
+    s = fv.Solver(c, fv.FV_FP64)
+    s.set_state(c.q)
+    q = c.q
+    for k in range(30):
+        dt_o, K_o = O.dt_levels(c, q)
+        assert np.array_equal(s.levels(), K_o)
+        d = s.diag()
+        assert d.dt_next == dt_o or k > 0 and abs(d.dt_next - dt_o) <= 1e-13 * dt_o
+        s.step(1, c.cfl)
+        q = s.get_state()
+    s.close()
+
+
+@pytest.mark.parametrize("shape", [(45, 13), (1, 1), (1, 20), (33, 1), (64, 9), (100, 37)])
+def test_fp64_ragged_and_degenerate_sizes(fv, shape):
+    nx, ny = shape
+    c = cases.perturbed(cases.dambreak(nx, ny, lx=4.0 * nx / 128, ly=2.0 * ny / 64, x_col=0.3 * nx / 32 + 0.01,
+                                       rects=[(2.5 * nx / 128, 2.7 * nx / 128, 0.0, 0.3 * ny / 64)]), 3)
+    qo, to, _, Ko = O.run(c, 20)
+    qg, tg, Kg, _ = gpu_run(fv, c, 20)
+    assert np.all(rel_linf(qg, qo) <= 1e-10)
+    assert np.array_equal(qg[:, c.solid == 1], np.zeros_like(qg[:, c.solid == 1]))
+
+
+def test_fp64_transmissive_sides(fv):
+    c = cases.riemann_x(150, rho_l=1010.0, rho_r=1000.0, u_l=0.5, u_r=-0.5, ny=5)
+    qo, _, _, _ = O.run(c, 80)
+    qg, _, _, _ = gpu_run(fv, c, 80)
+    assert np.all(rel_linf(qg, qo) <= 1e-10)
+    c = cases.contact_x(120, u0=1.0, ny=6)
+    qo, _, _, _ = O.run(c, 50)
+    qg, _, _, _ = gpu_run(fv, c, 50)
+    assert np.all(rel_linf(qg, qo) <= 1e-10)
+
+
+def test_fp64_drop_matches_oracle(fv):
+    c = cases.drop(96)
+    qo, _, _, _ = O.run(c, 40)
+    qg, _, _, _ = gpu_run(fv, c, 40)
+    assert np.all(rel_linf(qg, qo) <= 1e-10)
+
+
+def test_fp64_lake_at_rest_table1(fv):
+    for obstacle in (True, False):
+        c = cases.lake_box(100, obstacle=obstacle)
+        qg, _, K, _ = gpu_run(fv, c, 300)
+        fl = c.solid == 0
+        assert np.all(K == 100)
+        assert np.abs(qg[1]).max() <= 1e-12 and np.abs(qg[2]).max() <= 1e-12
+        rho = qg[0][fl] / qg[3][fl]
+        assert np.abs(rho - c.q[0][fl] / c.q[3][fl]).max() <= 1e-11
+
+
+def test_fp64_lake_with_air_and_obstacles(fv):
+    c = cases.c2_lake(256, 128)
+    qg, _, K, _ = gpu_run(fv, c, 200)
+    assert np.all(K == 64)
+    assert np.abs(qg[1]).max() <= 1e-12 and np.abs(qg[2]).max() <= 1e-12
+
+
+def test_fp64_mass_conservation(fv):
+    c = cases.c1()
+    s = fv.Solver(c, fv.FV_FP64)
+    s.set_state(c.q)
+    m0 = s.diag().mass
+    s.step(200, c.cfl)
+    m1 = s.diag().mass
+    s.close()
+    assert abs(m1 - m0) <= 1e-13 * m0
+
+
+def test_fp64_full_size_sampled_step(fv):
+    """4096 x 2048 with 8 obstacles, the launch the benchmark times: run 20
+    steps, then one more; the oracle recomputes that last step at sampled
+    cells (tile borders, obstacle edges, the front, random cells)."""
+    c = cases.c2()
+    s = fv.Solver(c, fv.FV_FP64)
+    s.set_state(c.q)
+    s.step(20, c.cfl)
+    q20 = s.get_state()
+    s.step(1, c.cfl)
+    q21 = s.get_state()
+    s.close()
+    rng = np.random.Generator(np.random.PCG64(2048))
+    fluid = np.flatnonzero(c.solid.ravel() == 0)
+    picks = [rng.choice(fluid, 3000, replace=False)]
+    # cells next to solids and at tile corners
+    sol = c.solid.astype(bool)
+    edge = np.zeros_like(sol)
+    edge[:, 1:] |= sol[:, :-1]
+    edge[:, :-1] |= sol[:, 1:]
+    edge[1:, :] |= sol[:-1, :]
+    edge[:-1, :] |= sol[1:, :]
+    edge &= ~sol
+    picks.append(rng.choice(np.flatnonzero(edge.ravel()), 500, replace=False))
+    jj, ii = np.meshgrid(np.arange(0, c.ny, 8), np.arange(0, c.nx, 32), indexing="ij")
+    corner = (jj * c.nx + ii).ravel()
+    corner = corner[c.solid.ravel()[corner] == 0]
+    picks.append(rng.choice(corner, 500, replace=False))
+    front = np.flatnonzero((np.abs(q20[3] - c.q[3]) > 1e-6).ravel() & (c.solid.ravel() == 0))
+    if front.size:
+        picks.append(rng.choice(front, min(500, front.size), replace=False))
+    cells = np.unique(np.concatenate(picks))
+    ref, dt = O.step_cells(c, q20, cells)
+    got = q21.reshape(4, -1)[:, cells].T
+    for v in range(4):
+        scale = np.abs(ref[:, v]).max()
+        assert np.abs(got[:, v] - ref[:, v]).max() <= 1e-12 * (scale if scale > 0 else 1.0)
+
+
+def test_invalid_inputs(fv):
+    c = cases.c1()
+    with pytest.raises(fv.FvError) as e:
+        fv.Solver(cases.c1(), prec=7)
+    assert e.value.status == fv.FV_EINVAL
+    s = fv.Solver(c, fv.FV_FP64)
+    with pytest.raises(fv.FvError):
+        s.step(1, c.cfl)          # no state yet
+    bad = c.q.copy()
+    bad[0, 5, 5] = np.nan
+    with pytest.raises(fv.FvError) as e:
+        s.set_state(bad)
+    assert e.value.status == fv.FV_EINVAL
+    s.set_state(c.q)
+    with pytest.raises(fv.FvError):
+        s.step(1, 1.5)
+    with pytest.raises(fv.FvError):
+        s.step(-1, 0.5)
+    assert s.step(0, 0.5, want_time=True) == 0.0
+    s.close()
+    g = fv.fv_grid(0, 5, 0.0, 0.0, 0.1, 0.1)
+    with pytest.raises(fv.FvError) as e:
+        fv.fv_create(g, fv.fv_eos(1000, 4.36e5, 1.0, 9.81, 1e-3), fv.fv_bc(), 0)
+    assert e.value.status == fv.FV_EINVAL
+    g = fv.fv_grid(8, 8, 0.0, 0.0, 0.1, 0.1)
+    with pytest.raises(fv.FvError):
+        fv.fv_create(g, fv.fv_eos(1000, 4.36e5, 7.0, 9.81, 1e-3), fv.fv_bc(), 0)
+
+
+def test_all_solid_domain_is_a_no_op(fv):
+    c = cases.dambreak(16, 8, rects=[(-1, 10, -1, 10)])
+    s = fv.Solver(c, fv.FV_FP64)
+    s.set_state(c.q)
+    assert s.step(5, 0.9, want_time=True) == 0.0
+    assert np.all(s.get_state() == 0)
+    s.close()
+
+
+def test_device_tensor_state_round_trip(fv):
+    import torch
+    c = cases.c1()
+    s = fv.Solver(c, fv.FV_FP64)
+    qd = torch.from_numpy(c.q).cuda()
+    s.set_state(qd)
+    s.step(10, c.cfl)
+    out = torch.empty_like(qd)
+    s.get_state(out)
+    torch.cuda.synchronize()
+    qo, _, _, _ = O.run(c, 10)
+    assert np.all(rel_linf(out.cpu().numpy(), qo) <= 1e-10)
+    s.close()
+
+
+# ------------------------------------------------------------------ FP32 deviation form
+
+def test_fp32_lake_at_rest_exact(fv):
+    for c in (cases.lake_box(100, obstacle=True), cases.c1_lake(), cases.c2_lake(256, 128)):
+        qg, _, _, d = gpu_run(fv, c, 300, prec=fv.FV_FP32_DEV)
+        fl = c.solid == 0
+        assert np.abs(qg[1]).max() <= 1e-9 * c.rho0 and np.abs(qg[2]).max() <= 1e-9 * c.rho0
+        assert np.abs(qg[0] - c.q[0])[fl].max() <= 1e-9 * c.rho0
+        assert d.status == 0
+
+
+def test_fp32_dambreak_error_vs_oracle(fv):
+    c = cases.c1()
+    qo, to, _, _ = O.run(c, 200, cfl=0.45)
+    qg, tg, _, d = gpu_run(fv, c, 200, prec=fv.FV_FP32_DEV, cfl=0.45)
+    e1 = rel_l1(qg, qo)
+    assert d.status == 0
+    assert e1[0] <= 1e-4 and e1[3] <= 1e-4, e1
+    assert e1[1] <= 1e-3 and e1[2] <= 1e-3, e1
+    assert abs(tg - to) <= 1e-5 * to
+
+
+def test_fp32_mass_conservation(fv):
+    c = cases.c1()
+    s = fv.Solver(c, fv.FV_FP32_DEV)
+    s.set_state(c.q)
+    m0 = s.diag().mass
+    s.step(200, c.cfl)
+    m1 = s.diag().mass
+    s.close()
+    assert abs(m1 - m0) <= 1e-5 * m0
