@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Throughput of the well-balanced path-conservative FV step on one GB300.
+
+Workload: the 4096 x 2048 dam break over 8 seeded obstacles on [0,4] x [0,2]
+(water column x < 1, y < 1 in hydrostatic balance, gas elsewhere, walls, CFL
+0.9).  One benchmark step = one time step of the whole grid: CFL rate, free-
+surface detector, reconstruction, every x and y face, interior integral and
+update.  Metric: million cell-updates per second (MCUPS).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  The headline `value` is the FP32 deviation-form path
+(dtype f32); the FP64 path is reported under "fp64" in the same line.  Under
+torchrun (N > 1) every rank advances its own replica of the workload (the
+method has no data-parallel split without a halo exchange; replicas only) and
+`value` is the total over ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "million cell-updates/s at 1 GB300 (FP64 vs FP32 at stated error)"
+UNIT = "MCUPS"
+WORKLOAD = "dambreak_8obstacles_4096x2048"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--only", choices=("f32", "f64"), default=None,
+                    help="time one path only (profiling runs)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if not self.path or not os.path.exists(self.path):
+            return out
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return out
+        try:
+            sm = [float(r[1]) for r in rows]
+            out["sm_mhz"] = statistics.median(sm)
+            out["sm_max_mhz"] = float(rows[0][2])
+        except ValueError:
+            pass
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = set()
+        for r in rows:
+            for k, name in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        out["reasons"] = sorted(reasons)
+        out["samples"] = len(rows)
+        return out
+
+
+# --------------------------------------------------------------------------- peaks
+def peaks():
+    """Roofline denominators: measured HBM copy bandwidth from MEASURED_PEAKS.json;
+    plain-ALU peaks from unit counts and clock (152 SMs x 128 FP32 lanes x 2 flops
+    x max SM clock; FP64 at the nominal 1.25 TFLOP/s of this part)."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    hbm, sm_max = 6800.0, 2070.0
+    src = "fallback"
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            hbm = float(d.get("hbm_gbs", hbm))
+            sm_max = float(d.get("sm_max_mhz", sm_max))
+            src = "measured"
+        except (ValueError, OSError):
+            pass
+    fp32 = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    return {"hbm_gbs": hbm, "hbm_src": src, "fp32_tflops": fp32, "fp64_tflops": 1.25}
+
+
+# --------------------------------------------------------------------------- CPU oracle
+def oracle_band(case, rows: int):
+    """A bounded sample of the workload: its bottom `rows` rows as a domain of
+    their own (same per-cell work, walls all round)."""
+    from dataclasses import replace
+    q = case.q[:, :rows, :].copy()
+    return replace(case, ny=rows, q=q, solid=case.solid[:rows, :].copy(), name=case.name + f"_band{rows}")
+
+
+def time_oracle(case, rows: int, steps: int, warm: int = 1):
+    from oracle import oracle
+    band = oracle_band(case, rows)
+    q = band.q
+    if warm:
+        q, _, _, _ = oracle.run(band, warm, q=q)
+    t0 = time.perf_counter()
+    oracle.run(band, steps, q=q)
+    dt = time.perf_counter() - t0
+    return band.nx * band.ny * steps / dt / 1e6, dt, oracle.max_threads(), band
+
+
+# --------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1806_04960_gb300 import cases
+    from oracle import oracle
+    oracle.build()
+    case = cases.c2()
+    budget_s = 150.0
+    # size the sample so that warmup + steps fit the budget
+    probe_rows = 128
+    mc, dt, cores, _ = time_oracle(case, probe_rows, 1, warm=0)
+    per_cell_s = dt / (case.nx * probe_rows)
+    total = max(1, args.steps + args.warmup)
+    rows = int(budget_s / total / per_cell_s / case.nx)
+    rows = max(16, min(case.ny, rows))
+    from paper_1806_04960_gb300.cases import Case  # noqa: F401
+    band = oracle_band(case, rows)
+    q = band.q
+    if args.warmup:
+        q, _, _, _ = oracle.run(band, args.warmup, q=q)
+    t0 = time.perf_counter()
+    oracle.run(band, args.steps, q=q)
+    el = time.perf_counter() - t0
+    value = band.nx * band.ny * args.steps / el / 1e6
+    sample = f"bottom {rows} of 2048 rows of the workload as their own walled domain, {args.steps} steps"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "nx": case.nx, "ny": case.ny,
+                                        "sample_rows": rows, "cfl": case.cfl},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- our arm
+def measure_path(fv, case, prec, steps, warmup, stream_sync, barrier, device_index):
+    s = fv.Solver(case, prec)
+    s.set_state(case.q)
+    if warmup:
+        s.step(warmup, case.cfl)
+    stream_sync()
+    barrier()
+    with ClockSampler(device_index) as clk:
+        kernel_ms, total_ms = s.step_timed(steps, case.cfl)
+    barrier()
+    d = s.diag()
+    s.close()
+    return {"kernel_ms": kernel_ms, "total_ms": total_ms, "status": d.status, "t": d.t,
+            "clocks": clk.summary()}
+
+
+def measure_e2e(fv, case, prec, steps):
+    """Through the public API with host buffers: upload Q^0 from pinned host
+    memory, advance `steps` steps each returning the simulated time to the host,
+    download the final state to pinned host memory."""
+    import torch
+    s = fv.Solver(case, prec)
+    qh = torch.from_numpy(case.q).pin_memory()
+    out = torch.empty_like(qh).pin_memory()
+    s.set_state(qh)          # warm the path once
+    s.step(2, case.cfl)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.set_state(qh)
+    for _ in range(steps):
+        s.step(1, case.cfl, want_time=True)
+    s.get_state(out)
+    el = time.perf_counter() - t0
+    s.close()
+    nbytes = 4 * case.nx * case.ny * 8
+    return {"value": case.nx * case.ny * steps / el / 1e6, "unit": UNIT,
+            "h2d_bytes_per_step": nbytes / steps,
+            "d2h_bytes_per_step": (nbytes + 8 * steps) / steps}
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        barrier = dist.barrier
+    else:
+        dist = None
+        barrier = lambda: None  # noqa: E731
+    torch.cuda.set_device(local)
+    from paper_1806_04960_gb300 import build
+    if rank == 0 or world == 1:
+        build.build()
+    if dist is not None:
+        dist.barrier()
+    from paper_1806_04960_gb300 import cases, fv
+
+    case = cases.c2()
+    steps, warmup = max(1, args.steps), max(3, args.warmup)
+    ops = fv.fv_host_cell_ops()
+    pk = peaks()
+    res = {}
+    paths = (("f32", fv.FV_FP32_DEV), ("f64", fv.FV_FP64))
+    if args.only:
+        paths = tuple(x for x in paths if x[0] == args.only)
+    for name, prec in paths:
+        k = steps if name == "f32" or args.only else max(1, min(steps, 40))
+        res[name] = measure_path(fv, case, prec, k, warmup, torch.cuda.synchronize, barrier, local)
+        res[name]["steps"] = k
+
+    def per_rank_max(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    cells = case.nx * case.ny
+    line_paths = {}
+    for name in res:
+        r = res[name]
+        tot = per_rank_max(r["total_ms"])
+        ker = per_rank_max(r["kernel_ms"])
+        ms_step = tot / r["steps"]
+        value = world * cells / (ms_step * 1e-3) / 1e6
+        kms = ker / r["steps"]
+        flops = ops["flops"] * cells
+        achieved = flops / (kms * 1e-3) / 1e12
+        peak = pk["fp32_tflops"] if name == "f32" else pk["fp64_tflops"]
+        bytes_alg = (33 if name == "f32" else 65) * cells
+        line_paths[name] = {
+            "value": value, "ms_per_step": ms_step, "kernel_ms_per_step": kms,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "flops_per_cell": ops["flops"],
+                         "hbm_achieved_gbs": bytes_alg / (kms * 1e-3) / 1e9,
+                         "hbm_frac": bytes_alg / (kms * 1e-3) / 1e9 / pk["hbm_gbs"]},
+            "status": r["status"], "clocks": r["clocks"], "steps": r["steps"]}
+
+    e2e = None if args.no_e2e else measure_e2e(fv, case, fv.FV_FP32_DEV, min(steps, 50))
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            mc, dt, cores, band = time_oracle(case, 512, 2, warm=1)
+            cpu = {"value": mc, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": f"bottom 512 of 2048 rows of the workload as their own walled domain, "
+                             f"2 timed steps after 1 warm-up, {dt:.1f} s"}
+        except Exception as e:  # pragma: no cover
+            cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle",
+                   "sample": f"failed: {e}"}
+    if rank == 0 and args.only:
+        r = line_paths[args.only]
+        print(json.dumps({"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world,
+                          "steps": r["steps"], "warmup": warmup, "ms_per_step": r["ms_per_step"],
+                          "dtype": args.only, "roofline": r["roofline"], "clocks": r["clocks"],
+                          "status": r["status"], "config": {"workload": WORKLOAD}}), flush=True)
+    elif rank == 0:
+        f32 = line_paths["f32"]
+        f64 = line_paths["f64"]
+        line = {
+            "metric": METRIC, "value": f32["value"], "unit": UNIT, "n_gpus": world,
+            "steps": f32["steps"], "warmup": warmup, "ms_per_step": f32["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nx": case.nx, "ny": case.ny, "cells": cells,
+                       "obstacles": 8, "cfl": case.cfl, "precision": "fp32 deviation form",
+                       "l2": "inputs larger than L2 (state 134 MB f32 / 268 MB f64 per buffer, "
+                             "double-buffered)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": f32["roofline"],
+            "clocks": f32["clocks"],
+            "gpu_launches": 2 * f32["steps"],
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "fp64": {"value": f64["value"], "unit": UNIT, "ms_per_step": f64["ms_per_step"],
+                     "steps": f64["steps"], "dtype": "f64", "roofline": f64["roofline"],
+                     "clocks": f64["clocks"]},
+            "status": {"f32": f32["status"], "f64": f64["status"]},
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -110,6 +110,13 @@ fv_status fv_set_state(fv_handle* h, const double* q, int on_device);
  * device status is checked (FV_ENONFINITE if a step produced a bad state). */
 fv_status fv_step(fv_handle* h, int32_t n, double cfl, double* t_out);
 
+/* fv_step plus timing: CUDA events recorded on the handle's stream around
+ * every launch of the fused step kernel give *kernel_ms, the summed device
+ * time of those launches, and *total_ms, the device time of the whole call
+ * (step kernels plus the per-step finalize kernel).  Synchronises the stream;
+ * either output pointer may be null.  Errors as fv_step. */
+fv_status fv_step_timed(fv_handle* h, int32_t n, double cfl, double* kernel_ms, double* total_ms);
+
 /* Copy the current state out in the layout above (double).  on_device as in
  * fv_set_state.  Synchronises the stream. */
 fv_status fv_get_state(fv_handle* h, double* q, int on_device);

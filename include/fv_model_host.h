@@ -26,6 +26,14 @@ extern "C" {
 int fv_host_xface(const double* model, const double* qm, const double* qp, double* Dm, double* Dp);
 int fv_host_yface(const double* model, const double* qm, const double* qp, double* Dm, double* Dp);
 
+/* Algorithmic operation count of one cell-update of the kernels (one
+ * second-order reconstruction with predictor, one x face, one y face, the
+ * interior integral of Eq. (Scheme), the update and the epilogue), obtained by
+ * running the kernels' per-cell arithmetic on a counting type on the host:
+ * out[0..4] = additions, multiplications, divisions, square roots,
+ * comparisons.  Returns 0, or 1 on a null pointer. */
+int fv_host_cell_ops(double* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -247,6 +247,57 @@ fv_status fv_step(fv_handle* h, int32_t n, double cfl, double* t_out) {
   return FV_OK;
 }
 
+fv_status fv_step_timed(fv_handle* h, int32_t n, double cfl, double* kernel_ms,
+                        double* total_ms) {
+  if (!h) return fail(FV_EINVAL, "fv_step_timed: null handle");
+  if (n < 0) return fail(FV_EINVAL, "fv_step_timed: n must be >= 0");
+  if (!(cfl > 0.0) || !(cfl <= 1.0)) return fail(FV_EINVAL, "fv_step_timed: cfl must be in (0, 1]");
+  if (!h->has_state) return fail(FV_EINVAL, "fv_step_timed: no state (call fv_set_state first)");
+  h->cfl = cfl;
+  const StepParams p = params_of(h, cfl);
+  Tables tb{h->d_rhoE, h->d_rhoE_f};
+  std::vector<cudaEvent_t> ev(2 * (size_t)n + 2);
+  for (auto& e : ev) FV_CUDA(cudaEventCreate(&e));
+  fv_status st = FV_OK;
+  cudaError_t err = cudaEventRecord(ev[2 * n], h->stream);
+  for (int32_t k = 0; k < n && err == cudaSuccess; ++k) {
+    const int a = h->cur, b = 1 - h->cur;
+    err = cudaEventRecord(ev[2 * k], h->stream);
+    if (h->prec == FV_FP64) {
+      StateF64 s{(const double*)h->d_q[a], (double*)h->d_q[b]};
+      launch_step_f64(p, s, h->d_solid, h->d_Kcur, h->d_colsum, h->d_sc, tb, h->stream);
+    } else {
+      StateF32 s{(const float*)h->d_q[a], (float*)h->d_q[b]};
+      launch_step_f32(p, s, h->d_solid, h->d_Kref, h->d_Kcur, h->d_colsum, h->d_sc, tb, h->stream);
+    }
+    if (err == cudaSuccess) err = cudaEventRecord(ev[2 * k + 1], h->stream);
+    launch_finalize(p, h->d_Kref, h->d_Kcur, h->d_colsum, h->d_sc, 1, h->stream);
+    h->cur = b;
+  }
+  if (err == cudaSuccess) err = cudaEventRecord(ev[2 * n + 1], h->stream);
+  if (err == cudaSuccess) err = cudaGetLastError();
+  if (err == cudaSuccess) err = cudaStreamSynchronize(h->stream);
+  double ksum = 0.0, tot = 0.0;
+  for (int32_t k = 0; k < n && err == cudaSuccess; ++k) {
+    float ms = 0.f;
+    err = cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]);
+    ksum += ms;
+  }
+  if (err == cudaSuccess) {
+    float ms = 0.f;
+    err = cudaEventElapsedTime(&ms, ev[2 * n], ev[2 * n + 1]);
+    tot = ms;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (err != cudaSuccess) return cuda_fail(err, "fv_step_timed");
+  if (kernel_ms) *kernel_ms = ksum;
+  if (total_ms) *total_ms = tot;
+  DevScalars sc;
+  FV_CUDA(cudaMemcpy(&sc, h->d_sc, sizeof(sc), cudaMemcpyDeviceToHost));
+  if (sc.status) st = fail(FV_ENONFINITE, "fv_step_timed: a step produced a non-admissible state");
+  return st;
+}
+
 fv_status fv_get_state(fv_handle* h, double* q, int on_device) {
   if (!h || !q) return fail(FV_EINVAL, "fv_get_state: null argument");
   if (!h->has_state) return fail(FV_EINVAL, "fv_get_state: no state");

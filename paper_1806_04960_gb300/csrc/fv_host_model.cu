@@ -30,6 +30,133 @@ extern "C" int fv_host_yface(const double* model, const double* qm, const double
                              double* Dp) {
   if (!model || !qm || !qp || !Dm || !Dp) return 1;
   const double dq[4] = {qp[0] - qm[0], qp[1] - qm[1], qp[2] - qm[2], qp[3] - qm[3]};
-  fv::yface<double>(qm, qp, dq, phys(model), Dm, Dp);
+  const fv::Phys<double> P = phys(model);
+  fv::yface<double>(qm, qp, dq, P.c2 * (dq[0] - P.rho0 * dq[3]), P, Dm, Dp);
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Algorithmic operation count of one cell-update, obtained by running the
+// kernels' own per-cell arithmetic on a counting scalar type on the host.
+// One cell-update = one reconstruction (second-order branch, predictor on,
+// every limiter test active), one x face, one y face, the interior integral,
+// the update and the epilogue (signal rate, detector weight).  Recomputation
+// of halo cells by neighbouring tiles is not counted.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Ops {
+  long long add = 0, mul = 0, div = 0, sqrt = 0, cmp = 0;
+};
+Ops g_ops;
+
+struct CD {
+  double v;
+  CD(double x = 0.0) : v(x) {}
+};
+inline CD operator+(CD a, CD b) { ++g_ops.add; return CD(a.v + b.v); }
+inline CD operator-(CD a, CD b) { ++g_ops.add; return CD(a.v - b.v); }
+inline CD operator*(CD a, CD b) { ++g_ops.mul; return CD(a.v * b.v); }
+inline CD operator/(CD a, CD b) { ++g_ops.div; return CD(a.v / b.v); }
+inline CD operator-(CD a) { return CD(-a.v); }
+inline CD& operator+=(CD& a, CD b) { a = a + b; return a; }
+inline CD& operator-=(CD& a, CD b) { a = a - b; return a; }
+inline bool operator<(CD a, CD b) { ++g_ops.cmp; return a.v < b.v; }
+inline bool operator>(CD a, CD b) { ++g_ops.cmp; return a.v > b.v; }
+inline bool operator<=(CD a, CD b) { ++g_ops.cmp; return a.v <= b.v; }
+inline CD fmin(CD a, CD b) { ++g_ops.cmp; return CD(a.v < b.v ? a.v : b.v); }
+inline CD fmax(CD a, CD b) { ++g_ops.cmp; return CD(a.v > b.v ? a.v : b.v); }
+
+}  // namespace
+
+// out[0..4] = additions/subtractions, multiplications, divisions, square roots,
+// comparisons (min, max, abs, compare) of one cell-update.
+extern "C" int fv_host_cell_ops(double* out) {
+  if (!out) return 1;
+  using T = CD;
+  fv::Phys<T> P;
+  P.rho0 = 1000.0;
+  P.k0 = 4.36e5;
+  P.g = 9.81;
+  P.c2 = 436.0;
+  P.c = std::sqrt(436.0);
+  P.inv_c = 1.0 / std::sqrt(436.0);
+  P.kappa = 9.81 * 1000.0 / 4.36e5;
+  fv::ReconConsts<T> R;
+  R.half_dx = R.half_dy = 1.0 / 64.0;
+  R.inv_2dx = R.inv_2dy = 16.0;
+  R.ten_eps = 0.01;
+  R.half_dt = 1e-4;
+  for (int v = 0; v < 4; ++v) {
+    R.eta[v] = 1e-9;
+    R.inv_eta[v] = 1e9;
+  }
+  // a generic liquid cell in motion with all four neighbours fluid
+  const double q0[4] = {1003.0, 520.0, -130.0, 0.93};
+  g_ops = Ops();
+  // neighbour fluctuations (8 neighbours: one multiply-subtract each for m, one
+  // subtraction for alpha) and the stencil min/max are part of the kernel body
+  T Qf[4] = {T(2.0), T(520.0), T(-130.0), T(0.0)};
+  T nb[8][4];
+  const double shift[8] = {-3.1, 4.2, -1.7, 2.5, 0.7, -0.9, 1.3, -2.2};
+  for (int k = 0; k < 8; ++k) {
+    T rn = T(1001.0 + 0.1 * k), an = T(0.93 + 0.001 * shift[k]);
+    T mraw = T(1003.0 + shift[k]);
+    nb[k][0] = mraw - T(0.93) * rn;
+    nb[k][1] = T(520.0 + 11.0 * shift[k]);
+    nb[k][2] = T(-130.0 + 7.0 * shift[k]);
+    nb[k][3] = an - T(0.93);
+  }
+  T fW[4], fE[4], fS[4], fN[4], mx[4], mn[4];
+  for (int v = 0; v < 4; ++v) {
+    fW[v] = nb[0][v];
+    fE[v] = nb[1][v];
+    fS[v] = nb[2][v];
+    fN[v] = nb[3][v];
+    mx[v] = fmax(fmax(fmax(Qf[v], fW[v]), fmax(fE[v], fS[v])), fN[v]);
+    mn[v] = fmin(fmin(fmin(Qf[v], fW[v]), fmin(fE[v], fS[v])), fN[v]);
+    for (int d = 4; d < 8; ++d) {
+      mx[v] = fmax(mx[v], nb[d][v]);
+      mn[v] = fmin(mn[v], nb[d][v]);
+    }
+  }
+  const T aE = T(0.93), rEc = T(1001.0), rES = T(1001.2), rEN = T(1000.8);
+  const T mEc = aE * rEc, mES = aE * rES, mEN = aE * rEN;
+  T base[4], ga[2];
+  fv::recon_core(Qf, fW, fE, fS, fN, mx, mn, aE, mEc, mES, mEN, rEc, P, R, base, ga);
+  // one x face and one y face per cell
+  {
+    const T qm[4] = {q0[0], q0[1], q0[2], q0[3]};
+    const T qp[4] = {q0[0] + 2.0, q0[1] - 30.0, q0[2] + 5.0, q0[3] - 0.01};
+    T dq[4], Dm[4], Dp[4];
+    for (int c = 0; c < 4; ++c) dq[c] = qp[c] - qm[c];
+    fv::xface(qm, qp, dq, P, Dm, Dp);
+    for (int c = 0; c < 4; ++c) dq[c] = qp[c] - qm[c];
+    const T dap = P.c2 * ((T(1000.1) - P.rho0) * T(0.0) + (dq[0] - P.rho0 * dq[3]));
+    fv::yface(qm, qp, dq, dap, P, Dm, Dp);
+  }
+  T Ix[4], Iy[4];
+  fv::interior_terms(fW, fE, fS, fN, base, mEc, mES, mEN, ga[0], ga[1], T(1.0 / 32), T(1.0 / 32), P,
+                     Ix, Iy);
+  // update: Q^{n+1} = Q^n - dt/dx (D+_W + D-_E + I_x) - dt/dy (D+_S + D-_N + I_y)
+  const T rdx = T(1e-4) / T(1.0 / 32), rdy = T(1e-4) / T(1.0 / 32);
+  T qn[4];
+  for (int c = 0; c < 4; ++c) {
+    const T xs = T(0.1) + T(0.2) + Ix[c];
+    const T ys = T(0.3) + T(0.4) + Iy[c];
+    qn[c] = T(q0[c]) - rdx * xs - rdy * ys;
+  }
+  // epilogue: velocities, signal rate, detector weight
+  const T r = T(1.0) / qn[0];
+  const T u = qn[1] * r, v = qn[2] * r;
+  const T rate = (fv::tabs(u) + P.c) * T(32.0) + (fv::tabs(v) + P.c) * T(32.0);
+  T w = (qn[3] - T(1e-3)) * T(1.0 / 0.999);
+  w = fmin(fmax(w, T(0.0)), T(1.0));
+  (void)rate;
+  out[0] = (double)g_ops.add;
+  out[1] = (double)g_ops.mul;
+  out[2] = (double)g_ops.div;
+  out[3] = (double)g_ops.sqrt;
+  out[4] = (double)g_ops.cmp;
   return 0;
 }

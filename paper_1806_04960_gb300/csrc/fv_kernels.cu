@@ -91,6 +91,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? 2 : 4))
   P.kappa = (T)p.kappa;
   const T dx = (T)p.dx, dy = (T)p.dy;
   const T eps = (T)p.eps;
+  const T inv_dx = (T)(1.0 / p.dx), inv_dy = (T)(1.0 / p.dy), inv_1meps = (T)(1.0 / (1.0 - p.eps));
   const double rate_cur = sc->rate_cur;
   const double dt_d = rate_cur > 0.0 ? p.cfl / rate_cur : 0.0;
   const T dt = (T)dt_d;
@@ -139,8 +140,18 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? 2 : 4))
                        (T)ldexp(p.rho0 * p.c, -10), (T)ldexp(1.0, -20)};
   const T bj_inv_eta[4] = {T(1) / bj_eta[0], T(1) / bj_eta[1], T(1) / bj_eta[2],
                            T(1) / bj_eta[3]};
-  const T half_dx = T(0.5) * dx, half_dy = T(0.5) * dy;
-  const T inv_2dx = T(1) / (T(2) * dx), inv_2dy = T(1) / (T(2) * dy);
+  ReconConsts<T> RC;
+  RC.half_dx = T(0.5) * dx;
+  RC.half_dy = T(0.5) * dy;
+  RC.inv_2dx = T(1) / (T(2) * dx);
+  RC.inv_2dy = T(1) / (T(2) * dy);
+  RC.ten_eps = T(10) * eps;
+  RC.half_dt = T(0.5) * dt;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    RC.eta[v] = bj_eta[v];
+    RC.inv_eta[v] = bj_inv_eta[v];
+  }
   for (int idx = tid; idx < RX * RY; idx += NT) {
     const int rx = idx % RX, ry = idx / RX;
     const int wi = rx + 1, wj = ry + 1;
@@ -207,86 +218,9 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? 2 : 4))
         }
       }
     }
-    T gx[4], gy[4];
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      gx[v] = (fE[v] - fW[v]) * inv_2dx;
-      gy[v] = (fN[v] - fS[v]) * inv_2dy;
-    }
-    // Barth-Jespersen at the four face midpoints, one factor per cell (min
-    // over the four components), Eq. (reconstruction_fluctuation2): the
-    // printed factor for |d| >= 2 eta_v, 1 for |d| <= eta_v, linear between,
-    // so that roundoff in a flat component cannot switch the cell.
-    T psi = T(1);
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const T eta = bj_eta[v], inv_eta = bj_inv_eta[v];
-      const T ddx = half_dx * gx[v], ddy = half_dy * gy[v];
-      const T up = mx[v] - Qf[v], dn = mn[v] - Qf[v];
-      const T dd[4] = {-ddx, ddx, -ddy, ddy};
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const T d = dd[k];
-        const T ad = tabs(d);
-        if (ad > eta) {
-          const T num = d > T(0) ? up : dn;
-          const T phi_bj = fmin(T(1), num / d);
-          const T ramp = fmin(T(1), (ad - eta) * inv_eta);
-          psi = fmin(psi, T(1) - ramp * (T(1) - phi_bj));
-        }
-      }
-    }
-    const T a_cell = aE;
-    T dtQ[4] = {0, 0, 0, 0};
-    if (a_cell <= T(10) * eps) {
-      psi = T(0);
-    } else {
-      const T m = mEc + Qf[0];
-      const Vel<T> vel = velocity(m, Qf[1], Qf[2]);
-      const T u = vel.u, v = vel.v;
-      T sx[4], sy[4];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        sx[c] = psi * gx[c];
-        sy[c] = psi * gy[c];
-      }
-      const T dmE = aE * (-P.kappa * rEc);
-      const T uv = u * v;
-      const T a1 = sx[1];
-      const T a2 = (P.c2 - u * u) * sx[0] + T(2) * u * sx[1] - P.k0 * sx[3];
-      const T a3 = -uv * sx[0] + v * sx[1] + u * sx[2];
-      const T a4 = u * sx[3];
-      const T b1 = sy[2];
-      const T b2 = -uv * sy[0] + v * sy[1] + u * sy[2] - uv * dmE;
-      const T b3 = (P.c2 - v * v) * sy[0] + T(2) * v * sy[2] - P.k0 * sy[3] - v * v * dmE + P.g * Qf[0];
-      const T b4 = v * sy[3];
-      dtQ[0] = -(a1 + b1);
-      dtQ[1] = -(a2 + b2);
-      dtQ[2] = -(a3 + b3);
-      dtQ[3] = -(a4 + b4);
-    }
-    const T half_dt = T(0.5) * dt;
-    T base[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      base[c] = Qf[c] + half_dt * dtQ[c];
-      const T sxh = psi * gx[c] * half_dx, syh = psi * gy[c] * half_dy;
-      fW[c] = base[c] - sxh;
-      fE[c] = base[c] + sxh;
-      fS[c] = base[c] - syh;
-      fN[c] = base[c] + syh;
-    }
     const T mES = aE * rES, mEN = aE * rEN;
-    // Admissibility of the reconstructed states; otherwise first order.
-    const bool ok = (mEc + fW[0] > T(0)) && (aE + fW[3] > T(0)) && (mEc + fE[0] > T(0)) &&
-                    (aE + fE[3] > T(0)) && (mES + fS[0] > T(0)) && (aE + fS[3] > T(0)) &&
-                    (mEN + fN[0] > T(0)) && (aE + fN[3] > T(0)) && (mEc + base[0] > T(0)) &&
-                    (aE + base[3] > T(0));
-    if (!ok) {
-      psi = T(0);
-#pragma unroll
-      for (int c = 0; c < 4; ++c) fW[c] = fE[c] = fS[c] = fN[c] = base[c] = Qf[c];
-    }
+    T base[4], ga[2];
+    recon_core(Qf, fW, fE, fS, fN, mx, mn, aE, mEc, mES, mEN, rEc, P, RC, base, ga);
     S.rec[R_AE][ry][rx] = aE;
     S.rec[R_MEC][ry][rx] = mEc;
     S.rec[R_MES][ry][rx] = mES;
@@ -301,8 +235,8 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? 2 : 4))
     if (rx >= 1 && rx <= TX && ry >= 1 && ry <= TY) {
 #pragma unroll
       for (int c = 0; c < 4; ++c) S.cen[c][ry - 1][rx - 1] = base[c];
-      S.cen[4][ry - 1][rx - 1] = psi * gx[3];
-      S.cen[5][ry - 1][rx - 1] = psi * gy[3];
+      S.cen[4][ry - 1][rx - 1] = ga[0];
+      S.cen[5][ry - 1][rx - 1] = ga[1];
     }
   }
   __syncthreads();  // window no longer needed: its storage becomes Dx/Dy
@@ -369,6 +303,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? 2 : 4))
       const bool Tt = S.flag[ryT + 1][rx + 1] == F_FLUID;
       if (B || Tt) {
         T qm[4], qp[4], dq[4];
+        T dap = T(0);
         if (B && Tt) {
           const T mEB = S.rec[R_MEN][ryB][rx], mET = S.rec[R_MES][ryT][rx];
           const T aB = S.rec[R_AE][ryB][rx], aT = S.rec[R_AE][ryT][rx];
@@ -384,6 +319,11 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? 2 : 4))
           dq[1] = ft[1] - fb[1];
           dq[2] = ft[2] - fb[2];
           dq[3] = (aT - aB) + (ft[3] - fb[3]);
+          // jump of alpha p: equilibrium part (rho^E_f - rho0) Delta alpha^E is
+          // exactly zero at the level face; fluctuation part c2 (dm^f - rho0 da^f)
+          const int K = S.K[rx + 1];
+          const T rEf = tab(rt, 2 * (j0 - 1 + ryT - K), ny);
+          dap = P.c2 * ((rEf - P.rho0) * (aT - aB) + ((ft[0] - fb[0]) - P.rho0 * (ft[3] - fb[3])));
         } else {
           const int ry = B ? ryB : ryT;
           const int base_i = B ? R_FN : R_FS;
@@ -406,7 +346,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? 2 : 4))
           dq[2] = qp[2] - qm[2];
           dq[3] = T(0);
         }
-        yface(qm, qp, dq, P, Dm, Dp);
+        yface(qm, qp, dq, dap, P, Dm, Dp);
       }
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
@@ -436,22 +376,8 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? 2 : 4))
       base[c] = S.cen[c][ty][tx];
     }
     const T dax = S.cen[4][ty][tx], day = S.cen[5][ty][tx];
-    // interior integral: conservative part + B grad q, mid-point rule
-    const Vel<T> vE = velocity(mEc + fE[0], fE[1], fE[2]);
-    const Vel<T> vW = velocity(mEc + fW[0], fW[1], fW[2]);
-    const Vel<T> vN = velocity(mEN + fN[0], fN[1], fN[2]);
-    const Vel<T> vS = velocity(mES + fS[0], fS[1], fS[2]);
-    const Vel<T> vc = velocity(mEc + base[0], base[1], base[2]);
     T Ix[4], Iy[4];
-    Ix[0] = fE[1] - fW[1];
-    Ix[1] = (fE[1] * vE.u - fW[1] * vW.u) + P.c2 * ((fE[0] - fW[0]) - P.rho0 * (fE[3] - fW[3]));
-    Ix[2] = fE[1] * vE.v - fW[1] * vW.v;
-    Ix[3] = dx * vc.u * dax;
-    Iy[0] = fN[2] - fS[2];
-    Iy[1] = fN[1] * vN.v - fS[1] * vS.v;
-    Iy[2] = (fN[2] * vN.v - fS[2] * vS.v) + P.c2 * ((fN[0] - fS[0]) - P.rho0 * (fN[3] - fS[3])) +
-            P.g * dy * base[0];
-    Iy[3] = dy * vc.v * day;
+    interior_terms(fW, fE, fS, fN, base, mEc, mES, mEN, dax, day, dx, dy, P, Ix, Iy);
     const T rdx = dt / dx, rdy = dt / dy;
     T xs[4], ys[4];
 #pragma unroll
@@ -481,14 +407,29 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? 2 : 4))
 #pragma unroll
     for (int v = 0; v < 4; ++v) qout[v * N + c] = qn[v];
     // epilogue: admissibility, signal rate, detector weight
-    const double md = (double)m_full, ad = (double)qn[3];
-    const double ud = (double)qn[1] / md, vd = (double)qn[2] / md;
-    if (!(md > 0.0) || !(ad > 0.0) || !isfinite(ud) || !isfinite(vd) || !isfinite(ad)) bad = true;
-    my_rate = (fabs(ud) + p.c) / p.dx + (fabs(vd) + p.c) / p.dy;
-    if (!(my_rate >= 0.0)) my_rate = 0.0;
-    double w = (ad - p.eps) / (1.0 - p.eps);
-    w = w < 0.0 ? 0.0 : (w > 1.0 ? 1.0 : w);
-    my_w = (unsigned long long)__double2ll_rn(w * 4294967296.0);
+    if (DEV) {
+      // float path: in float; the max is taken in double by the reduction
+      const T r = rcp(m_full);
+      const T u = qn[1] * r, v = qn[2] * r;
+      if (!(m_full > T(0)) || !(qn[3] > T(0)) || !isfinite(u) || !isfinite(v) || !isfinite(qn[3]))
+        bad = true;
+      const T rt_ = (tabs(u) + P.c) * inv_dx + (tabs(v) + P.c) * inv_dy;
+      my_rate = rt_ >= T(0) ? (double)rt_ : 0.0;
+      T w = (qn[3] - eps) * inv_1meps;
+      w = w < T(0) ? T(0) : (w > T(1) ? T(1) : w);
+      my_w = (unsigned long long)__float2ll_rn((float)w * 4294967296.0f);
+    } else {
+      // double path: same expressions as the definition (IEEE division), so dt
+      // and the detected levels are reproducible
+      const double md = (double)m_full, ad = (double)qn[3];
+      const double ud = (double)qn[1] / md, vd = (double)qn[2] / md;
+      if (!(md > 0.0) || !(ad > 0.0) || !isfinite(ud) || !isfinite(vd) || !isfinite(ad)) bad = true;
+      my_rate = (fabs(ud) + p.c) / p.dx + (fabs(vd) + p.c) / p.dy;
+      if (!(my_rate >= 0.0)) my_rate = 0.0;
+      double w = (ad - p.eps) / (1.0 - p.eps);
+      w = w < 0.0 ? 0.0 : (w > 1.0 ? 1.0 : w);
+      my_w = (unsigned long long)__double2ll_rn(w * 4294967296.0);
+    }
   } else if (inside) {
     const size_t c = (size_t)gj_me * nx + gi_me;
 #pragma unroll

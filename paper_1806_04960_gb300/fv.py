@@ -57,23 +57,28 @@ _lib.fv_create.argtypes = [C.POINTER(fv_grid), C.POINTER(fv_eos), C.POINTER(fv_b
 _lib.fv_set_state.argtypes = [_H, C.c_void_p, C.c_int]
 _lib.fv_step.argtypes = [_H, C.c_int32, C.c_double, _D]
 _lib.fv_get_state.argtypes = [_H, C.c_void_p, C.c_int]
+_lib.fv_step_timed.argtypes = [_H, C.c_int32, C.c_double, _D, _D]
 _lib.fv_get_levels.argtypes = [_H, C.POINTER(C.c_int32)]
 _lib.fv_get_diag.argtypes = [_H, C.POINTER(fv_diag)]
 _lib.fv_destroy.argtypes = [_H]
 _lib.fv_destroy.restype = None
 _lib.fv_last_error.restype = C.c_char_p
 _lib.fv_version.restype = C.c_char_p
-for _f in ("fv_create", "fv_set_state", "fv_step", "fv_get_state", "fv_get_levels", "fv_get_diag"):
+for _f in ("fv_create", "fv_set_state", "fv_step", "fv_step_timed", "fv_get_state",
+           "fv_get_levels", "fv_get_diag"):
     getattr(_lib, _f).restype = C.c_int
 
 _lib.fv_host_xface.argtypes = [_D, _D, _D, _D, _D]
 _lib.fv_host_yface.argtypes = [_D, _D, _D, _D, _D]
 _lib.fv_host_xface.restype = C.c_int
+_lib.fv_host_cell_ops.argtypes = [_D]
+_lib.fv_host_cell_ops.restype = C.c_int
 _lib.fv_host_yface.restype = C.c_int
 
-ABI_SYMBOLS = ("fv_create", "fv_set_state", "fv_step", "fv_get_state", "fv_get_levels",
+ABI_SYMBOLS = ("fv_create", "fv_set_state", "fv_step", "fv_step_timed", "fv_get_state",
+               "fv_get_levels",
                "fv_get_diag", "fv_destroy", "fv_last_error", "fv_version", "fv_host_xface",
-               "fv_host_yface")
+               "fv_host_yface", "fv_host_cell_ops")
 
 
 def _check(st):
@@ -126,6 +131,16 @@ def fv_host_yface(qm, qp, model):
     return _host_face(_lib.fv_host_yface, qm, qp, model)
 
 
+def fv_host_cell_ops() -> dict:
+    """Operation counts of one cell-update of the kernels (see fv_model_host.h)."""
+    out = np.zeros(5)
+    _check(_lib.fv_host_cell_ops(out.ctypes.data_as(_D)) and FV_EINVAL)
+    names = ("add", "mul", "div", "sqrt", "cmp")
+    d = {k: int(v) for k, v in zip(names, out)}
+    d["flops"] = d["add"] + d["mul"] + d["div"] + d["sqrt"]
+    return d
+
+
 def fv_create(grid: fv_grid, eos: fv_eos, bc: fv_bc, prec: int, stream: int = 0):
     h = _H()
     _check(_lib.fv_create(C.byref(grid), C.byref(eos), C.byref(bc), int(prec),
@@ -145,6 +160,13 @@ def fv_step(h, n: int, cfl: float, want_time: bool = False):
         return t.value
     _check(_lib.fv_step(h, int(n), float(cfl), None))
     return None
+
+
+def fv_step_timed(h, n: int, cfl: float):
+    """(kernel_ms, total_ms) of n steps, timed with CUDA events on the stream."""
+    k, t = C.c_double(0.0), C.c_double(0.0)
+    _check(_lib.fv_step_timed(h, int(n), float(cfl), C.byref(k), C.byref(t)))
+    return k.value, t.value
 
 
 def fv_get_state(h, out) -> None:
@@ -195,6 +217,9 @@ class Solver:
 
     def step(self, n: int, cfl: float | None = None, want_time: bool = False):
         return fv_step(self.h, n, self.case.cfl if cfl is None else cfl, want_time)
+
+    def step_timed(self, n: int, cfl: float | None = None):
+        return fv_step_timed(self.h, n, self.case.cfl if cfl is None else cfl)
 
     def get_state(self, out=None):
         if out is None:

