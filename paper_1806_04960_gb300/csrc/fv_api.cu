@@ -224,6 +224,7 @@ fv_status fv_step(fv_handle* h, int32_t n, double cfl, double* t_out) {
   h->cfl = cfl;
   const StepParams p = params_of(h, cfl);
   Tables tb{h->d_rhoE, h->d_rhoE_f};
+  if (n > 0) launch_prepare(cfl, h->d_sc, h->stream);
   for (int32_t k = 0; k < n; ++k) {
     const int a = h->cur, b = 1 - h->cur;
     if (h->prec == FV_FP64) {
@@ -259,6 +260,7 @@ fv_status fv_step_timed(fv_handle* h, int32_t n, double cfl, double* kernel_ms,
   std::vector<cudaEvent_t> ev(2 * (size_t)n + 2);
   for (auto& e : ev) FV_CUDA(cudaEventCreate(&e));
   fv_status st = FV_OK;
+  if (n > 0) launch_prepare(cfl, h->d_sc, h->stream);
   cudaError_t err = cudaEventRecord(ev[2 * n], h->stream);
   for (int32_t k = 0; k < n && err == cudaSuccess; ++k) {
     const int a = h->cur, b = 1 - h->cur;

@@ -28,6 +28,8 @@
 // represented by exact zeros.
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include "fv_kernels.cuh"
 #include "fv_model.cuh"
 
@@ -60,6 +62,46 @@ struct Smem {
   unsigned char flag[WY][WX];
 };
 
+// Per-precision constants, built once on the host.
+template <typename T>
+struct KConsts {
+  Phys<T> P;
+  ReconConsts<T> R;  // half_dt is filled in the kernel
+  T dx, dy, eps, inv_dx, inv_dy, inv_1meps;
+};
+
+template <typename T>
+KConsts<T> make_consts(const StepParams& p) {
+  KConsts<T> k;
+  k.P.c = (T)p.c;
+  k.P.c2 = (T)p.c2;
+  k.P.inv_c = (T)(1.0 / p.c);
+  k.P.rho0 = (T)p.rho0;
+  k.P.k0 = (T)p.k0;
+  k.P.g = (T)p.g;
+  k.P.kappa = (T)p.kappa;
+  k.R.half_dx = (T)(0.5 * p.dx);
+  k.R.half_dy = (T)(0.5 * p.dy);
+  k.R.inv_2dx = (T)(1.0 / (2.0 * p.dx));
+  k.R.inv_2dy = (T)(1.0 / (2.0 * p.dy));
+  k.R.ten_eps = (T)(10.0 * p.eps);
+  k.R.half_dt = (T)0;
+  // limiter ramp scales: 2^-20 rho0, 2^-10 rho0 c (momenta), 2^-20 (alpha)
+  const double eta[4] = {std::ldexp(p.rho0, -20), std::ldexp(p.rho0 * p.c, -10),
+                         std::ldexp(p.rho0 * p.c, -10), std::ldexp(1.0, -20)};
+  for (int v = 0; v < 4; ++v) {
+    k.R.eta[v] = (T)eta[v];
+    k.R.inv_eta[v] = (T)(1.0 / eta[v]);
+  }
+  k.dx = (T)p.dx;
+  k.dy = (T)p.dy;
+  k.eps = (T)p.eps;
+  k.inv_dx = (T)(1.0 / p.dx);
+  k.inv_dy = (T)(1.0 / p.dy);
+  k.inv_1meps = (T)(1.0 / (1.0 - p.eps));
+  return k;
+}
+
 template <typename T>
 __device__ __forceinline__ T tab(const T* rt, int h, int ny) {
   return rt[h + 2 * ny];
@@ -69,7 +111,7 @@ enum { R_AE = 0, R_MEC = 1, R_MES = 2, R_MEN = 3, R_FW = 4, R_FE = 8, R_FS = 12,
 
 template <typename T, bool DEV>
 __global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? 2 : 4))
-    step_kernel(StepParams p, const T* __restrict__ qin, T* __restrict__ qout,
+    step_kernel(StepParams p, KConsts<T> kc, const T* __restrict__ qin, T* __restrict__ qout,
                 const uint8_t* __restrict__ solid, const int32_t* __restrict__ Kref,
                 const int32_t* __restrict__ Kcur, unsigned long long* __restrict__ colsum,
                 DevScalars* __restrict__ sc, const double* __restrict__ rhoE_d,
@@ -81,41 +123,42 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? 2 : 4))
   const int nx = p.nx, ny = p.ny;
   const size_t N = (size_t)nx * ny;
 
-  Phys<T> P;
-  P.c = (T)p.c;
-  P.c2 = (T)p.c2;
-  P.inv_c = (T)(1.0 / p.c);
-  P.rho0 = (T)p.rho0;
-  P.k0 = (T)p.k0;
-  P.g = (T)p.g;
-  P.kappa = (T)p.kappa;
-  const T dx = (T)p.dx, dy = (T)p.dy;
-  const T eps = (T)p.eps;
-  const T inv_dx = (T)(1.0 / p.dx), inv_dy = (T)(1.0 / p.dy), inv_1meps = (T)(1.0 / (1.0 - p.eps));
-  const double rate_cur = sc->rate_cur;
-  const double dt_d = rate_cur > 0.0 ? p.cfl / rate_cur : 0.0;
-  const T dt = (T)dt_d;
+  const Phys<T>& P = kc.P;
+  // boundary kinds as scalars (a runtime index into the parameter struct would
+  // place it in local memory)
+  const bool trW = p.side[0] == 1, trE = p.side[1] == 1, trS = p.side[2] == 1, trN = p.side[3] == 1;
+  const T dx = kc.dx, dy = kc.dy, eps = kc.eps;
+  const T inv_dx = kc.inv_dx, inv_dy = kc.inv_dy, inv_1meps = kc.inv_1meps;
+  // dt of this step, computed once per step by the finalize/prepare kernels
+  const T dt = sizeof(T) == 8 ? (T)sc->dt_cur : (T)sc->dt_cur_f;
 
   // ---------------------------------------------------------------- load
-  for (int idx = tid; idx < WX * WY; idx += NT) {
-    const int wi = idx % WX, wj = idx / WX;
-    const int gi = i0 - 2 + wi, gj = j0 - 2 + wj;
-    unsigned char f = F_OUT;
-    if (gi >= 0 && gj >= 0 && gi < nx && gj < ny) f = solid[(size_t)gj * nx + gi] ? F_SOLID : F_FLUID;
-    S.flag[wj][wi] = f;
-    if (f == F_FLUID) {
-      const size_t c = (size_t)gj * nx + gi;
-      T m = qin[c];
-      const T a = qin[3 * N + c];
-      if (DEV) {
-        const int Kr = Kref[gi], Kc = Kcur[gi];
-        if (Kr != Kc)
-          m += (T)((double)a * (rhoE_d[2 * (gj - Kr) + 1 + 2 * ny] - rhoE_d[2 * (gj - Kc) + 1 + 2 * ny]));
+  // Each warp loads whole window rows: its 32 lanes the 128-byte-aligned
+  // centre (coalesced), lanes 0-3 the two halo columns on either side.
+  const int lane = tid & 31, warp = tid >> 5;
+  for (int wj = warp; wj < WY; wj += NT / 32) {
+    const int gj = j0 - 2 + wj;
+    for (int pass = 0; pass < 2; ++pass) {
+      if (pass == 1 && lane >= 4) break;
+      const int wi = pass == 0 ? lane + 2 : (lane < 2 ? lane : TX + lane);
+      const int gi = i0 - 2 + wi;
+      unsigned char f = F_OUT;
+      if (gi >= 0 && gj >= 0 && gi < nx && gj < ny) f = solid[(size_t)gj * nx + gi] ? F_SOLID : F_FLUID;
+      S.flag[wj][wi] = f;
+      if (f == F_FLUID) {
+        const size_t c = (size_t)gj * nx + gi;
+        T m = qin[c];
+        const T a = qin[3 * N + c];
+        if (DEV) {
+          // re-base m^f from the level it was stored with to this step's level
+          const int Kr = Kref[gi], Kc = Kcur[gi];
+          if (Kr != Kc) m += a * (tab(rt, 2 * (gj - Kr) + 1, ny) - tab(rt, 2 * (gj - Kc) + 1, ny));
+        }
+        S.u.w[0][wj][wi] = m;
+        S.u.w[1][wj][wi] = qin[N + c];
+        S.u.w[2][wj][wi] = qin[2 * N + c];
+        S.u.w[3][wj][wi] = a;
       }
-      S.u.w[0][wj][wi] = m;
-      S.u.w[1][wj][wi] = qin[N + c];
-      S.u.w[2][wj][wi] = qin[2 * N + c];
-      S.u.w[3][wj][wi] = a;
     }
   }
   for (int idx = tid; idx < WX; idx += NT) {
@@ -135,23 +178,8 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? 2 : 4))
   }
 
   // ---------------------------------------------------------------- recon
-  // limiter regularisation: 2^-20 rho0, 2^-10 rho0 c (momenta), 2^-20
-  const T bj_eta[4] = {(T)ldexp(p.rho0, -20), (T)ldexp(p.rho0 * p.c, -10),
-                       (T)ldexp(p.rho0 * p.c, -10), (T)ldexp(1.0, -20)};
-  const T bj_inv_eta[4] = {T(1) / bj_eta[0], T(1) / bj_eta[1], T(1) / bj_eta[2],
-                           T(1) / bj_eta[3]};
-  ReconConsts<T> RC;
-  RC.half_dx = T(0.5) * dx;
-  RC.half_dy = T(0.5) * dy;
-  RC.inv_2dx = T(1) / (T(2) * dx);
-  RC.inv_2dy = T(1) / (T(2) * dy);
-  RC.ten_eps = T(10) * eps;
+  ReconConsts<T> RC = kc.R;
   RC.half_dt = T(0.5) * dt;
-#pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    RC.eta[v] = bj_eta[v];
-    RC.inv_eta[v] = bj_inv_eta[v];
-  }
   for (int idx = tid; idx < RX * RY; idx += NT) {
     const int rx = idx % RX, ry = idx / RX;
     const int wi = rx + 1, wj = ry + 1;
@@ -194,7 +222,11 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? 2 : 4))
       const unsigned char f = S.flag[wj + dwj][wi + dwi];
 #pragma unroll
       for (int v = 0; v < 4; ++v) out[v] = Qf[v];
-      if (!(f == F_OUT && p.side[side] == 1)) out[normal] = -out[normal];
+      const bool tr = side == 0 ? trW : side == 1 ? trE : side == 2 ? trS : trN;
+      if (!(f == F_OUT && tr)) {
+        if (normal == 1) out[1] = -out[1];
+        else out[2] = -out[2];
+      }
     };
     T fW[4], fE[4], fS[4], fN[4];
     if (!nbf(-1, 0, fW)) ghost(-1, 0, 1, 0, fW);
@@ -276,7 +308,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? 2 : 4))
           q[2] = S.rec[base_i + 2][ry][rx];
           q[3] = aE + S.rec[base_i + 3][ry][rx];
           const bool outside = L ? (S.flag[ry + 1][rxR + 1] == F_OUT) : (S.flag[ry + 1][rxL + 1] == F_OUT);
-          const bool transmissive = outside && p.side[L ? 1 : 0] == 1;
+          const bool transmissive = outside && (L ? trE : trW);
           T g[4] = {q[0], transmissive ? q[1] : -q[1], q[2], q[3]};
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
@@ -334,7 +366,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? 2 : 4))
           q[2] = S.rec[base_i + 2][ry][rx];
           q[3] = aE + S.rec[base_i + 3][ry][rx];
           const bool outside = B ? (S.flag[ryT + 1][rx + 1] == F_OUT) : (S.flag[ryB + 1][rx + 1] == F_OUT);
-          const bool transmissive = outside && p.side[B ? 3 : 2] == 1;
+          const bool transmissive = outside && (B ? trN : trS);
           T g[4] = {q[0], q[1], transmissive ? q[2] : -q[2], q[3]};
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
@@ -358,7 +390,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? 2 : 4))
   __syncthreads();
 
   // ---------------------------------------------------------------- update
-  double my_rate = 0.0;
+  T my_rate = T(0);
   unsigned long long my_w = 0;
   bool bad = false;
   if (inside && flag_me == F_FLUID) {
@@ -414,18 +446,19 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? 2 : 4))
       if (!(m_full > T(0)) || !(qn[3] > T(0)) || !isfinite(u) || !isfinite(v) || !isfinite(qn[3]))
         bad = true;
       const T rt_ = (tabs(u) + P.c) * inv_dx + (tabs(v) + P.c) * inv_dy;
-      my_rate = rt_ >= T(0) ? (double)rt_ : 0.0;
+      my_rate = rt_ >= T(0) ? rt_ : T(0);
       T w = (qn[3] - eps) * inv_1meps;
       w = w < T(0) ? T(0) : (w > T(1) ? T(1) : w);
-      my_w = (unsigned long long)__float2ll_rn((float)w * 4294967296.0f);
+      // 2^-24 resolution in float, placed on the common 2^-32 fixed-point scale
+      my_w = (unsigned long long)__float2uint_rn((float)w * 16777216.0f) << 8;
     } else {
       // double path: same expressions as the definition (IEEE division), so dt
       // and the detected levels are reproducible
       const double md = (double)m_full, ad = (double)qn[3];
       const double ud = (double)qn[1] / md, vd = (double)qn[2] / md;
       if (!(md > 0.0) || !(ad > 0.0) || !isfinite(ud) || !isfinite(vd) || !isfinite(ad)) bad = true;
-      my_rate = (fabs(ud) + p.c) / p.dx + (fabs(vd) + p.c) / p.dy;
-      if (!(my_rate >= 0.0)) my_rate = 0.0;
+      const double rd = (fabs(ud) + p.c) / p.dx + (fabs(vd) + p.c) / p.dy;
+      my_rate = rd >= 0.0 ? (T)rd : T(0);
       double w = (ad - p.eps) / (1.0 - p.eps);
       w = w < 0.0 ? 0.0 : (w > 1.0 ? 1.0 : w);
       my_w = (unsigned long long)__double2ll_rn(w * 4294967296.0);
@@ -439,10 +472,11 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? 2 : 4))
   if (bad) atomicOr(&sc->status, 1);
   // column sums
   S.col[ty][tx] = my_w;
-  // rate max
+  // rate max (in T; one double per warp)
+  T r_t = my_rate;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) my_rate = fmax(my_rate, __shfl_xor_sync(0xffffffffu, my_rate, o));
-  if ((tid & 31) == 0) S.wmax[tid >> 5] = my_rate;
+  for (int o = 16; o > 0; o >>= 1) r_t = fmax(r_t, __shfl_xor_sync(0xffffffffu, r_t, o));
+  if ((tid & 31) == 0) S.wmax[tid >> 5] = (double)r_t;
   __syncthreads();
   if (ty == 0 && inside) {
     unsigned long long s = 0;
@@ -475,7 +509,15 @@ __global__ void finalize_kernel(StepParams p, int32_t* Kref, int32_t* Kcur,
     }
     sc->rate_cur = __longlong_as_double((long long)sc->rate_acc);
     sc->rate_acc = 0ull;
+    sc->dt_cur = sc->rate_cur > 0.0 ? p.cfl / sc->rate_cur : 0.0;
+    sc->dt_cur_f = (float)sc->dt_cur;
   }
+}
+
+// dt of the next step from the current rate and the cfl of this call.
+__global__ void prepare_kernel(double cfl, DevScalars* sc) {
+  sc->dt_cur = sc->rate_cur > 0.0 ? cfl / sc->rate_cur : 0.0;
+  sc->dt_cur_f = (float)sc->dt_cur;
 }
 
 __global__ void prologue_kernel(StepParams p, const double* __restrict__ q,
@@ -607,8 +649,8 @@ void launch_step_t(const StepParams& p, const T* in, T* out, const uint8_t* soli
   }
   dim3 block(TX, TY);
   dim3 grid((p.nx + TX - 1) / TX, (p.ny + TY - 1) / TY);
-  step_kernel<T, DEV><<<grid, block, smem, st>>>(p, in, out, solid, Kref, Kcur, colsum, sc,
-                                                  rhoE_d, rt);
+  step_kernel<T, DEV><<<grid, block, smem, st>>>(p, make_consts<T>(p), in, out, solid, Kref, Kcur,
+                                                  colsum, sc, rhoE_d, rt);
 }
 
 }  // namespace
@@ -631,6 +673,10 @@ void launch_finalize(const StepParams& p, int32_t* Kref, int32_t* Kcur,
                      unsigned long long* colsum, DevScalars* sc, int count_step,
                      cudaStream_t st) {
   finalize_kernel<<<1, 1024, 0, st>>>(p, Kref, Kcur, colsum, sc, count_step);
+}
+
+void launch_prepare(double cfl, DevScalars* sc, cudaStream_t st) {
+  prepare_kernel<<<1, 1, 0, st>>>(cfl, sc);
 }
 
 void launch_prologue_f64(const StepParams& p, const double* q, const uint8_t* solid,

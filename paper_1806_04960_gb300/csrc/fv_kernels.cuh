@@ -24,8 +24,9 @@ struct DevScalars {
   double t;               // simulated time
   double dt_last;         // dt of the last step
   long long steps;
+  double dt_cur;          // dt of the next step (cfl / rate_cur)
+  float dt_cur_f;         // same, rounded to float
   int status;             // bit 0: non-admissible state produced
-  int pad;
 };
 
 // Equilibrium density table: rhoE[h + 2 ny] = rho0 exp(-kappa (h dy / 2)) for
@@ -54,6 +55,7 @@ void launch_step_f32(const StepParams& p, const StateF32& s, const uint8_t* soli
 void launch_finalize(const StepParams& p, int32_t* Kref, int32_t* Kcur,
                      unsigned long long* colsum, DevScalars* sc, int count_step,
                      cudaStream_t st);
+void launch_prepare(double cfl, DevScalars* sc, cudaStream_t st);
 void launch_prologue_f64(const StepParams& p, const double* q, const uint8_t* solid,
                          unsigned long long* colsum, DevScalars* sc, cudaStream_t st);
 void launch_to_dev(const StepParams& p, const double* q, const uint8_t* solid,
