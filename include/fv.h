@@ -131,6 +131,38 @@ fv_status fv_get_diag(fv_handle* h, fv_diag* d);
 /* Release the handle and its device memory (synchronises; NULL is a no-op). */
 void fv_destroy(fv_handle* h);
 
+/* Largest grid fv_step_static accepts (size of its static scratch array). */
+#define FV_STATIC_MAX_NX 8192
+#define FV_STATIC_MAX_NY 8192
+
+/* One FP64 time step that allocates no device memory.  The paper has no
+ * counterpart: this is for callers that cannot call cudaMalloc, such as an
+ * application that owns all of its GPU memory through its own pool, or a
+ * latency-critical loop where cudaMalloc's implicit synchronisation is not
+ * acceptable.  It computes exactly what fv_set_state + one fv_step compute in
+ * FV_FP64, from q_in to q_out, keeping its scratch (detector column sums,
+ * levels, equilibrium table, step scalars; about 385 KB) in one file-scope
+ * device array that every GPU loading the library holds until the process
+ * exits.
+ *   grid, eos, side[4]: as for fv_create (host pointers); grid must satisfy
+ *     nx <= FV_STATIC_MAX_NX and ny <= FV_STATIC_MAX_NY, else FV_EINVAL.
+ *   solid: device pointer, nx*ny bytes (1 = removed cell).
+ *   q_in, q_out: device pointers to the 4-plane double state (layout above);
+ *     they must not alias.  Solid cells of q_out are written as 0.
+ *   cfl in (0, 1]; cuda_stream: the stream for all work (NULL = default).
+ *   dt_out: nullable host pointer; if given, the stream is synchronised and
+ *     *dt_out receives the step's dt (FV_ENONFINITE if q_out is not
+ *     admissible); otherwise the call is asynchronous.
+ * Calls no allocating routine.  The first call on a device looks up the
+ * array's device address with that device current; make that first call
+ * before any stream capture.  Every call reuses the same array, which keeps
+ * the previous call's contents (the accumulators are cleared at the start of
+ * each call), so calls whose work overlaps on a GPU (other streams, other host
+ * threads) race and must be serialised by the caller. */
+fv_status fv_step_static(const fv_grid* grid, const fv_eos* eos, const int32_t side[4],
+                         const uint8_t* solid, const double* q_in, double* q_out, double cfl,
+                         void* cuda_stream, double* dt_out);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* fv_last_error(void);
 

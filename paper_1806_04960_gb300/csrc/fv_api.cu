@@ -36,6 +36,8 @@ fv_status cuda_fail(cudaError_t e, const char* where) {
 
 }  // namespace
 
+void fv::set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+
 struct fv_handle {
   fv_grid grid;
   fv_eos eos;

@@ -66,4 +66,7 @@ void launch_mass(const StepParams& p, const double* q, const uint8_t* solid, dou
                  int nblocks, double* out, cudaStream_t st);
 void launch_zero_solid(const StepParams& p, double* q, const uint8_t* solid, cudaStream_t st);
 
+// Message returned by fv_last_error() on this thread.
+void set_last_error(const char* msg);
+
 }  // namespace fv

@@ -72,13 +72,16 @@ _lib.fv_host_xface.argtypes = [_D, _D, _D, _D, _D]
 _lib.fv_host_yface.argtypes = [_D, _D, _D, _D, _D]
 _lib.fv_host_xface.restype = C.c_int
 _lib.fv_host_cell_ops.argtypes = [_D]
+_lib.fv_step_static.argtypes = [C.POINTER(fv_grid), C.POINTER(fv_eos), C.POINTER(C.c_int32),
+                                C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, _D]
+_lib.fv_step_static.restype = C.c_int
 _lib.fv_host_cell_ops.restype = C.c_int
 _lib.fv_host_yface.restype = C.c_int
 
 ABI_SYMBOLS = ("fv_create", "fv_set_state", "fv_step", "fv_step_timed", "fv_get_state",
                "fv_get_levels",
                "fv_get_diag", "fv_destroy", "fv_last_error", "fv_version", "fv_host_xface",
-               "fv_host_yface", "fv_host_cell_ops")
+               "fv_host_yface", "fv_host_cell_ops", "fv_step_static")
 
 
 def _check(st):
