@@ -138,6 +138,26 @@ def peaks():
     return {"hbm_gbs": hbm, "hbm_src": src, "fp32_tflops": fp32, "fp64_tflops": 1.25}
 
 
+def recorded_traffic():
+    """DRAM bytes per step-kernel launch from the committed ncu record, if the
+    kernel sources still hash to the captured value; else None."""
+    import hashlib
+    rec = os.path.join(ROOT, "profiles", "step_kernel_dram.txt")
+    srcs = [os.path.join(ROOT, "paper_1806_04960_gb300", "csrc", f)
+            for f in ("fv_kernels.cu", "fv_model.cuh")]
+    if not os.path.exists(rec) or not all(os.path.exists(f) for f in srcs):
+        return {}
+    h = hashlib.sha256(b"".join(open(f, "rb").read() for f in srcs)).hexdigest()
+    vals = {}
+    for line in open(rec):
+        parts = line.split()
+        if len(parts) == 2 and not line.startswith("#"):
+            vals[parts[0]] = parts[1]
+    if vals.get("sources_sha256") != h:
+        return {}
+    return {k: float(v) for k, v in vals.items() if k in ("f32", "f64")}
+
+
 # --------------------------------------------------------------------------- CPU oracle
 def oracle_band(case, rows: int):
     """A bounded sample of the workload: its bottom `rows` rows as a domain of
@@ -279,6 +299,7 @@ def run_ours(args):
         return float(t.item())
 
     cells = case.nx * case.ny
+    traffic = recorded_traffic()
     line_paths = {}
     for name in res:
         r = res[name]
@@ -294,7 +315,7 @@ def run_ours(args):
         line_paths[name] = {
             "value": value, "ms_per_step": ms_step, "kernel_ms_per_step": kms,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": traffic.get(name),
                          "flops_per_cell": ops["flops"],
                          "hbm_achieved_gbs": bytes_alg / (kms * 1e-3) / 1e9,
                          "hbm_frac": bytes_alg / (kms * 1e-3) / 1e9 / pk["hbm_gbs"]},
