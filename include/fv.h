@@ -131,6 +131,42 @@ fv_status fv_get_diag(fv_handle* h, fv_diag* d);
 /* Release the handle and its device memory (synchronises; NULL is a no-op). */
 void fv_destroy(fv_handle* h);
 
+/* ---- Batched ensemble of independent domains (configs of uneven sizes,
+ * parameter sweeps).  Each domain has its own grid, equation of state,
+ * boundaries, free-surface levels, dt (its own CFL condition) and time; one
+ * ensemble step advances every domain by one of its own steps.  A step is one
+ * persistent launch over the tiles of all domains plus one per-domain finalize
+ * launch; fv_batch_step captures n steps into a CUDA graph on an internal
+ * stream (ordered after and before the stream given at create) and replays it.
+ * The paper runs one domain at a time; the per-domain arithmetic is the same as
+ * fv_step's. */
+typedef struct fv_batch fv_batch;
+
+/* ndom >= 1 domains; grids, eos, bcs: host arrays of ndom entries (each as for
+ * fv_create; solid masks are copied).  Errors as fv_create. */
+fv_status fv_batch_create(int32_t ndom, const fv_grid* grids, const fv_eos* eos, const fv_bc* bcs,
+                          fv_prec prec, void* cuda_stream, fv_batch** out);
+
+/* State of domain dom (layout as fv_set_state; on_device as there).  Every
+ * domain needs a state before the first fv_batch_step.  Synchronises. */
+fv_status fv_batch_set_state(fv_batch* b, int32_t dom, const double* q, int on_device);
+
+/* n ensemble steps with CFL number cfl (each domain its own dt).
+ * Asynchronous with respect to the host. */
+fv_status fv_batch_step(fv_batch* b, int32_t n, double cfl);
+
+/* As fv_batch_step; *total_ms receives the device time of the n steps (CUDA
+ * events on the internal stream).  Synchronises. */
+fv_status fv_batch_step_timed(fv_batch* b, int32_t n, double cfl, double* total_ms);
+
+/* State, diagnostics and domain count (as the single-domain calls). */
+fv_status fv_batch_get_state(fv_batch* b, int32_t dom, double* q, int on_device);
+fv_status fv_batch_get_diag(fv_batch* b, int32_t dom, fv_diag* d);
+int32_t fv_batch_size(const fv_batch* b);
+
+/* Release the ensemble (synchronises; NULL is a no-op). */
+void fv_batch_destroy(fv_batch* b);
+
 /* Largest grid fv_step_static accepts (size of its static scratch array). */
 #define FV_STATIC_MAX_NX 8192
 #define FV_STATIC_MAX_NY 8192

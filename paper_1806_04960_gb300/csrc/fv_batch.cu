@@ -1,0 +1,363 @@
+// Batched ensemble of independent domains (C ABI declared in include/fv.h).
+//
+// Every domain has its own grid, equation of state, boundaries, level
+// detector, dt and time.  One step of the ensemble is one persistent launch of
+// batch_step_kernel over the tiles of all domains (round-robin over a grid of
+// a few CTAs per SM) followed by one per-domain finalize launch.  n steps are
+// captured once into a CUDA graph on an internal stream and replayed.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <map>
+#include <new>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "fv.h"
+#include "fv_kernels.cuh"
+
+using namespace fv;
+
+namespace {
+
+fv_status bfail(fv_status s, const std::string& m) {
+  fv::set_last_error(m.c_str());
+  return s;
+}
+
+#define BV_CUDA(call)                                                                   \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) return bfail(FV_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+struct fv_batch {
+  int ndom = 0;
+  fv_prec prec = FV_FP64;
+  cudaStream_t user = nullptr;
+  cudaStream_t inner = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  std::vector<BatchDomainDesc> desc;
+  std::vector<fv_grid> grids;
+  std::vector<fv_eos> eos;
+  unsigned char* pool = nullptr;  // all per-domain device buffers
+  void* d_table = nullptr;
+  int4* d_tiles = nullptr;
+  int ntiles = 0;
+  double* d_stage = nullptr;       // double staging for set/get (largest domain)
+  double* d_partial = nullptr;
+  double* d_mass = nullptr;
+  int cur = 0;
+  std::vector<char> has_state;
+  std::map<std::tuple<int, double, int>, cudaGraphExec_t> graphs;
+};
+
+static void batch_release(fv_batch* b) {
+  if (!b) return;
+  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  cudaFree(b->pool);
+  cudaFree(b->d_table);
+  cudaFree(b->d_tiles);
+  cudaFree(b->d_stage);
+  cudaFree(b->d_partial);
+  cudaFree(b->d_mass);
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->ev_out) cudaEventDestroy(b->ev_out);
+  if (b->inner) cudaStreamDestroy(b->inner);
+  delete b;
+}
+
+static StepParams bparams(const fv_grid& g, const fv_eos& e, const int32_t side[4], double cfl) {
+  StepParams p;
+  p.nx = g.nx;
+  p.ny = g.ny;
+  p.dx = g.dx;
+  p.dy = g.dy;
+  p.rho0 = e.rho0;
+  p.k0 = e.k0;
+  p.g = e.g;
+  p.eps = e.eps_gas;
+  p.c2 = e.k0 / e.rho0;
+  p.c = std::sqrt(p.c2);
+  p.kappa = e.g * e.rho0 / e.k0;
+  for (int s = 0; s < 4; ++s) p.side[s] = side[s];
+  p.cfl = cfl;
+  return p;
+}
+
+extern "C" {
+
+fv_status fv_batch_create(int32_t ndom, const fv_grid* grids, const fv_eos* eos, const fv_bc* bcs,
+                          fv_prec prec, void* cuda_stream, fv_batch** out) {
+  if (ndom < 1 || !grids || !eos || !bcs || !out) return bfail(FV_EINVAL, "fv_batch_create: bad arguments");
+  if (prec != FV_FP64 && prec != FV_FP32_DEV) return bfail(FV_EINVAL, "fv_batch_create: bad precision");
+  for (int k = 0; k < ndom; ++k) {
+    const fv_grid& g = grids[k];
+    const fv_eos& e = eos[k];
+    if (g.nx < 1 || g.ny < 1 || (long long)g.nx * g.ny > 2147483647LL || !(g.dx > 0.0) || !(g.dy > 0.0))
+      return bfail(FV_EINVAL, "fv_batch_create: bad grid of domain " + std::to_string(k));
+    if (e.gamma != 1.0 || !(e.rho0 > 0.0) || !(e.k0 > 0.0) || !(e.g >= 0.0) || !(e.eps_gas > 0.0) ||
+        !(e.eps_gas < 0.1))
+      return bfail(FV_EINVAL, "fv_batch_create: bad equation of state of domain " + std::to_string(k));
+    for (int s = 0; s < 4; ++s)
+      if (bcs[k].side[s] != FV_BC_WALL && bcs[k].side[s] != FV_BC_TRANSMISSIVE)
+        return bfail(FV_EINVAL, "fv_batch_create: bad boundary of domain " + std::to_string(k));
+  }
+  fv_batch* b = new (std::nothrow) fv_batch();
+  if (!b) return bfail(FV_ENOMEM, "fv_batch_create: host allocation");
+  b->ndom = ndom;
+  b->prec = prec;
+  b->user = (cudaStream_t)cuda_stream;
+  b->grids.assign(grids, grids + ndom);
+  b->eos.assign(eos, eos + ndom);
+  b->has_state.assign(ndom, 0);
+  const bool f64 = prec == FV_FP64;
+  const size_t elem = f64 ? sizeof(double) : sizeof(float);
+  // one pool for every domain's buffers
+  std::vector<size_t> off(ndom);
+  size_t total = 0, maxN = 0;
+  for (int k = 0; k < ndom; ++k) {
+    const size_t N = (size_t)grids[k].nx * grids[k].ny, nx = grids[k].nx, ny = grids[k].ny;
+    maxN = N > maxN ? N : maxN;
+    off[k] = total;
+    total += 2 * up256(4 * N * elem) + up256(N) + 2 * up256(nx * 4) + up256(nx * 8) +
+             up256(sizeof(DevScalars)) + up256((4 * ny + 1) * 8) + up256((4 * ny + 1) * 4);
+  }
+  cudaError_t e = cudaMalloc((void**)&b->pool, total);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_table, batch_table_bytes(ndom, f64));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_stage, 4 * maxN * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_partial, 1024 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_mass, sizeof(double));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->inner, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    batch_release(b);
+    return bfail(FV_ENOMEM, std::string("fv_batch_create: ") + cudaGetErrorString(e));
+  }
+  batch_grid_size(f64);  // kernel attributes and occupancy, outside any capture
+  std::vector<int4> tiles;
+  b->desc.resize(ndom);
+  for (int k = 0; k < ndom; ++k) {
+    const fv_grid& g = grids[k];
+    const size_t N = (size_t)g.nx * g.ny, nx = g.nx, ny = g.ny;
+    unsigned char* p = b->pool + off[k];
+    BatchDomainDesc& d = b->desc[k];
+    d.p = bparams(g, eos[k], bcs[k].side, 0.9);
+    d.q[0] = p; p += up256(4 * N * elem);
+    d.q[1] = p; p += up256(4 * N * elem);
+    unsigned char* solid = p; p += up256(N);
+    d.solid = solid;
+    d.Kref = (int32_t*)p; p += up256(nx * 4);
+    d.Kcur = (int32_t*)p; p += up256(nx * 4);
+    d.colsum = (unsigned long long*)p; p += up256(nx * 8);
+    d.sc = (DevScalars*)p; p += up256(sizeof(DevScalars));
+    double* rt = (double*)p; p += up256((4 * ny + 1) * 8);
+    float* rtf = (float*)p;
+    d.rhoE_d = rt;
+    d.rhoE_f = rtf;
+    std::vector<uint8_t> hs(N, 0);
+    if (bcs[k].solid)
+      for (size_t c = 0; c < N; ++c) hs[c] = bcs[k].solid[c] ? 1 : 0;
+    std::vector<double> ht(4 * ny + 1);
+    std::vector<float> hf(4 * ny + 1);
+    const double kappa = eos[k].g * eos[k].rho0 / eos[k].k0;
+    for (long h2 = -2L * (long)ny; h2 <= 2L * (long)ny; ++h2) {
+      const double val = eos[k].rho0 * std::exp(-kappa * (0.5 * (double)h2) * g.dy);
+      ht[h2 + 2L * ny] = val;
+      hf[h2 + 2L * ny] = (float)val;
+    }
+    e = cudaMemcpy(solid, hs.data(), N, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(rt, ht.data(), ht.size() * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(rtf, hf.data(), hf.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(d.colsum, 0, nx * 8);
+    if (e == cudaSuccess) e = cudaMemset(d.sc, 0, sizeof(DevScalars));
+    if (e == cudaSuccess) e = cudaMemset(d.Kref, 0, nx * 4);
+    if (e == cudaSuccess) e = cudaMemset(d.Kcur, 0, nx * 4);
+    if (e == cudaSuccess) e = cudaMemset(d.q[0], 0, 4 * N * elem);
+    if (e == cudaSuccess) e = cudaMemset(d.q[1], 0, 4 * N * elem);
+    if (e != cudaSuccess) {
+      batch_release(b);
+      return bfail(FV_ECUDA, std::string("fv_batch_create: ") + cudaGetErrorString(e));
+    }
+    const int tx = (g.nx + 31) / 32, ty = (g.ny + 7) / 8;
+    for (int j = 0; j < ty; ++j)
+      for (int i = 0; i < tx; ++i) tiles.push_back(make_int4(k, i, j, 0));
+  }
+  std::vector<unsigned char> table(batch_table_bytes(ndom, f64));
+  batch_fill_table(b->desc.data(), ndom, f64, table.data());
+  b->ntiles = (int)tiles.size();
+  e = cudaMemcpy(b->d_table, table.data(), table.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_tiles, tiles.size() * sizeof(int4));
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    batch_release(b);
+    return bfail(FV_ECUDA, std::string("fv_batch_create: ") + cudaGetErrorString(e));
+  }
+  *out = b;
+  return FV_OK;
+}
+
+fv_status fv_batch_set_state(fv_batch* b, int32_t dom, const double* q, int on_device) {
+  if (!b || !q || dom < 0 || dom >= b->ndom) return bfail(FV_EINVAL, "fv_batch_set_state: bad arguments");
+  const BatchDomainDesc& d = b->desc[dom];
+  const size_t N = (size_t)d.p.nx * d.p.ny;
+  const StepParams& p = d.p;
+  const bool f64 = b->prec == FV_FP64;
+  double* target = f64 ? (double*)d.q[b->cur] : b->d_stage;
+  cudaStream_t st = b->inner;
+  BV_CUDA(cudaEventRecord(b->ev_in, b->user));
+  BV_CUDA(cudaStreamWaitEvent(st, b->ev_in, 0));
+  BV_CUDA(cudaMemcpyAsync(target, q, 4 * N * sizeof(double),
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  launch_zero_solid(p, target, d.solid, st);
+  BV_CUDA(cudaMemsetAsync(d.sc, 0, sizeof(DevScalars), st));
+  BV_CUDA(cudaMemsetAsync(d.colsum, 0, p.nx * sizeof(unsigned long long), st));
+  launch_prologue_f64(p, target, d.solid, d.colsum, d.sc, st);
+  launch_finalize(p, d.Kref, d.Kcur, d.colsum, d.sc, 0, st);
+  BV_CUDA(cudaMemcpyAsync(d.Kref, d.Kcur, p.nx * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+  if (!f64) {
+    Tables tb{d.rhoE_d, d.rhoE_f};
+    launch_to_dev(p, b->d_stage, d.solid, d.Kcur, tb, (float*)d.q[b->cur], st);
+  }
+  BV_CUDA(cudaGetLastError());
+  DevScalars sc;
+  BV_CUDA(cudaMemcpyAsync(&sc, d.sc, sizeof(sc), cudaMemcpyDeviceToHost, st));
+  BV_CUDA(cudaStreamSynchronize(st));
+  if (sc.status) {
+    BV_CUDA(cudaMemset(d.sc, 0, sizeof(DevScalars)));
+    b->has_state[dom] = 0;
+    return bfail(FV_EINVAL, "fv_batch_set_state: non-admissible fluid cell in domain " + std::to_string(dom));
+  }
+  b->has_state[dom] = 1;
+  return FV_OK;
+}
+
+static fv_status batch_run(fv_batch* b, int32_t n, double cfl, double* total_ms) {
+  if (!b) return bfail(FV_EINVAL, "fv_batch_step: null batch");
+  if (n < 0) return bfail(FV_EINVAL, "fv_batch_step: n must be >= 0");
+  if (!(cfl > 0.0) || !(cfl <= 1.0)) return bfail(FV_EINVAL, "fv_batch_step: cfl must be in (0, 1]");
+  for (int k = 0; k < b->ndom; ++k)
+    if (!b->has_state[k]) return bfail(FV_EINVAL, "fv_batch_step: domain " + std::to_string(k) + " has no state");
+  if (n == 0) return FV_OK;
+  const bool f64 = b->prec == FV_FP64;
+  const auto key = std::make_tuple((int)n, cfl, b->cur);
+  cudaGraphExec_t exec = nullptr;
+  auto it = b->graphs.find(key);
+  if (it != b->graphs.end()) {
+    exec = it->second;
+  } else {
+    cudaGraph_t graph = nullptr;
+    BV_CUDA(cudaStreamBeginCapture(b->inner, cudaStreamCaptureModeThreadLocal));
+    launch_batch_prepare(f64, b->d_table, b->ndom, cfl, b->inner);
+    int par = b->cur;
+    for (int32_t k = 0; k < n; ++k) {
+      launch_batch_step(f64, b->d_table, b->d_tiles, b->ntiles, par, b->inner);
+      launch_batch_finalize(f64, b->d_table, b->ndom, cfl, 1, b->inner);
+      par ^= 1;
+    }
+    cudaError_t e = cudaStreamEndCapture(b->inner, &graph);
+    if (e != cudaSuccess) return bfail(FV_ECUDA, std::string("fv_batch_step: capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return bfail(FV_ECUDA, std::string("fv_batch_step: instantiate: ") + cudaGetErrorString(e));
+    if (b->graphs.size() > 16) {
+      for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+      b->graphs.clear();
+    }
+    b->graphs[key] = exec;
+  }
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  if (total_ms) {
+    BV_CUDA(cudaEventCreate(&t0));
+    BV_CUDA(cudaEventCreate(&t1));
+  }
+  BV_CUDA(cudaEventRecord(b->ev_in, b->user));
+  BV_CUDA(cudaStreamWaitEvent(b->inner, b->ev_in, 0));
+  if (total_ms) BV_CUDA(cudaEventRecord(t0, b->inner));
+  BV_CUDA(cudaGraphLaunch(exec, b->inner));
+  if (total_ms) BV_CUDA(cudaEventRecord(t1, b->inner));
+  BV_CUDA(cudaEventRecord(b->ev_out, b->inner));
+  BV_CUDA(cudaStreamWaitEvent(b->user, b->ev_out, 0));
+  b->cur ^= (n & 1);
+  if (total_ms) {
+    BV_CUDA(cudaEventSynchronize(t1));
+    float ms = 0.f;
+    BV_CUDA(cudaEventElapsedTime(&ms, t0, t1));
+    *total_ms = ms;
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+  }
+  return FV_OK;
+}
+
+fv_status fv_batch_step(fv_batch* b, int32_t n, double cfl) { return batch_run(b, n, cfl, nullptr); }
+
+fv_status fv_batch_step_timed(fv_batch* b, int32_t n, double cfl, double* total_ms) {
+  if (!total_ms) return bfail(FV_EINVAL, "fv_batch_step_timed: null total_ms");
+  return batch_run(b, n, cfl, total_ms);
+}
+
+fv_status fv_batch_get_state(fv_batch* b, int32_t dom, double* q, int on_device) {
+  if (!b || !q || dom < 0 || dom >= b->ndom) return bfail(FV_EINVAL, "fv_batch_get_state: bad arguments");
+  if (!b->has_state[dom]) return bfail(FV_EINVAL, "fv_batch_get_state: no state");
+  const BatchDomainDesc& d = b->desc[dom];
+  const size_t N = (size_t)d.p.nx * d.p.ny;
+  cudaStream_t st = b->inner;
+  BV_CUDA(cudaEventRecord(b->ev_in, b->user));
+  BV_CUDA(cudaStreamWaitEvent(st, b->ev_in, 0));
+  const double* src = (const double*)d.q[b->cur];
+  if (b->prec == FV_FP32_DEV) {
+    Tables tb{d.rhoE_d, d.rhoE_f};
+    launch_from_dev(d.p, (const float*)d.q[b->cur], d.solid, d.Kref, tb, b->d_stage, st);
+    src = b->d_stage;
+  }
+  BV_CUDA(cudaMemcpyAsync(q, src, 4 * N * sizeof(double),
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  BV_CUDA(cudaStreamSynchronize(st));
+  return FV_OK;
+}
+
+fv_status fv_batch_get_diag(fv_batch* b, int32_t dom, fv_diag* out) {
+  if (!b || !out || dom < 0 || dom >= b->ndom) return bfail(FV_EINVAL, "fv_batch_get_diag: bad arguments");
+  if (!b->has_state[dom]) return bfail(FV_EINVAL, "fv_batch_get_diag: no state");
+  const BatchDomainDesc& d = b->desc[dom];
+  cudaStream_t st = b->inner;
+  BV_CUDA(cudaEventRecord(b->ev_in, b->user));
+  BV_CUDA(cudaStreamWaitEvent(st, b->ev_in, 0));
+  const double* src = (const double*)d.q[b->cur];
+  if (b->prec == FV_FP32_DEV) {
+    Tables tb{d.rhoE_d, d.rhoE_f};
+    launch_from_dev(d.p, (const float*)d.q[b->cur], d.solid, d.Kref, tb, b->d_stage, st);
+    src = b->d_stage;
+  }
+  launch_mass(d.p, src, d.solid, b->d_partial, 1024, b->d_mass, st);
+  BV_CUDA(cudaGetLastError());
+  DevScalars sc;
+  double mass = 0.0;
+  BV_CUDA(cudaMemcpyAsync(&sc, d.sc, sizeof(sc), cudaMemcpyDeviceToHost, st));
+  BV_CUDA(cudaMemcpyAsync(&mass, b->d_mass, sizeof(double), cudaMemcpyDeviceToHost, st));
+  BV_CUDA(cudaStreamSynchronize(st));
+  out->t = sc.t;
+  out->steps = sc.steps;
+  out->dt_next = sc.dt_cur;
+  out->mass = mass;
+  out->status = sc.status ? FV_ENONFINITE : FV_OK;
+  return FV_OK;
+}
+
+int32_t fv_batch_size(const fv_batch* b) { return b ? b->ndom : 0; }
+
+void fv_batch_destroy(fv_batch* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->inner);
+  batch_release(b);
+}
+
+}  // extern "C"

@@ -109,17 +109,19 @@ __device__ __forceinline__ T tab(const T* rt, int h, int ny) {
 
 enum { R_AE = 0, R_MEC = 1, R_MES = 2, R_MEN = 3, R_FW = 4, R_FE = 8, R_FS = 12, R_FN = 16 };
 
+// One tile (bx, by) of one domain; called by the whole CTA.
 template <typename T, bool DEV>
-__global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? 2 : 4))
-    step_kernel(StepParams p, KConsts<T> kc, const T* __restrict__ qin, T* __restrict__ qout,
-                const uint8_t* __restrict__ solid, const int32_t* __restrict__ Kref,
-                const int32_t* __restrict__ Kcur, unsigned long long* __restrict__ colsum,
-                DevScalars* __restrict__ sc, const double* __restrict__ rhoE_d,
-                const T* __restrict__ rt) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem<T>& S = *reinterpret_cast<Smem<T>*>(smem_raw);
+__device__ __forceinline__ void step_tile(const StepParams& p, const KConsts<T>& kc,
+                                          const T* __restrict__ qin, T* __restrict__ qout,
+                                          const uint8_t* __restrict__ solid,
+                                          const int32_t* __restrict__ Kref,
+                                          const int32_t* __restrict__ Kcur,
+                                          unsigned long long* __restrict__ colsum,
+                                          DevScalars* __restrict__ sc,
+                                          const double* __restrict__ rhoE_d,
+                                          const T* __restrict__ rt, int bx, int by, Smem<T>& S) {
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int i0 = bx * TX, j0 = by * TY;
   const int nx = p.nx, ny = p.ny;
   const size_t N = (size_t)nx * ny;
 
@@ -492,6 +494,85 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? 2 : 4))
   }
 }
 
+template <typename T, bool DEV>
+__global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? 2 : 4))
+    step_kernel(StepParams p, KConsts<T> kc, const T* __restrict__ qin, T* __restrict__ qout,
+                const uint8_t* __restrict__ solid, const int32_t* __restrict__ Kref,
+                const int32_t* __restrict__ Kcur, unsigned long long* __restrict__ colsum,
+                DevScalars* __restrict__ sc, const double* __restrict__ rhoE_d,
+                const T* __restrict__ rt) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem<T>& S = *reinterpret_cast<Smem<T>*>(smem_raw);
+  step_tile<T, DEV>(p, kc, qin, qout, solid, Kref, Kcur, colsum, sc, rhoE_d, rt, blockIdx.x,
+                    blockIdx.y, S);
+}
+
+// Batched step: every tile of every domain of an ensemble, distributed
+// round-robin over a persistent grid (one or a few CTAs per SM); each domain
+// uses its own dt, levels and accumulators.  parity selects which of the two
+// state buffers is read.
+template <typename T>
+struct BatchDomain {
+  StepParams p;
+  KConsts<T> kc;
+  T* q[2];
+  const uint8_t* solid;
+  int32_t* Kref;
+  int32_t* Kcur;
+  unsigned long long* colsum;
+  DevScalars* sc;
+  const double* rhoE_d;
+  const T* rt;
+};
+
+template <typename T, bool DEV>
+__global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? 2 : 4))
+    batch_step_kernel(const BatchDomain<T>* __restrict__ doms, const int4* __restrict__ tiles,
+                      int ntiles, int parity) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem<T>& S = *reinterpret_cast<Smem<T>*>(smem_raw);
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int4 td = tiles[t];
+    const BatchDomain<T>& d = doms[td.x];
+    step_tile<T, DEV>(d.p, d.kc, d.q[parity], d.q[1 - parity], d.solid, d.Kref, d.Kcur, d.colsum,
+                      d.sc, d.rhoE_d, d.rt, td.y, td.z, S);
+    __syncthreads();  // shared memory is reused by the next tile
+  }
+}
+
+// Per-domain finalize for a batch: one CTA per domain.
+template <typename T>
+__global__ void batch_finalize_kernel(const BatchDomain<T>* __restrict__ doms, double cfl,
+                                      int count_step) {
+  const BatchDomain<T>& d = doms[blockIdx.x];
+  for (int i = threadIdx.x; i < d.p.nx; i += blockDim.x) {
+    d.Kref[i] = d.Kcur[i];
+    d.Kcur[i] = (int32_t)((d.colsum[i] + (1ull << 31)) >> 32);
+    d.colsum[i] = 0ull;
+  }
+  if (threadIdx.x == 0) {
+    DevScalars* sc = d.sc;
+    if (count_step) {
+      sc->t += sc->dt_cur;
+      sc->dt_last = sc->dt_cur;
+      sc->steps += 1;
+    }
+    sc->rate_cur = __longlong_as_double((long long)sc->rate_acc);
+    sc->rate_acc = 0ull;
+    sc->dt_cur = sc->rate_cur > 0.0 ? cfl / sc->rate_cur : 0.0;
+    sc->dt_cur_f = (float)sc->dt_cur;
+  }
+}
+
+template <typename T>
+__global__ void batch_prepare_kernel(const BatchDomain<T>* __restrict__ doms, int ndom, double cfl) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ndom; k += gridDim.x * blockDim.x) {
+    DevScalars* sc = doms[k].sc;
+    sc->dt_cur = sc->rate_cur > 0.0 ? cfl / sc->rate_cur : 0.0;
+    sc->dt_cur_f = (float)sc->dt_cur;
+  }
+}
+
 // ----------------------------------------------------------------------------
 __global__ void finalize_kernel(StepParams p, int32_t* Kref, int32_t* Kcur,
                                 unsigned long long* colsum, DevScalars* sc, int count_step) {
@@ -654,6 +735,88 @@ void launch_step_t(const StepParams& p, const T* in, T* out, const uint8_t* soli
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------- batch helpers
+size_t batch_table_bytes(int ndom, bool f64) {
+  return (size_t)ndom * (f64 ? sizeof(BatchDomain<double>) : sizeof(BatchDomain<float>));
+}
+
+template <typename T>
+static void fill_table_t(const BatchDomainDesc* d, int ndom, void* dst) {
+  BatchDomain<T>* out = static_cast<BatchDomain<T>*>(dst);
+  for (int k = 0; k < ndom; ++k) {
+    BatchDomain<T> b;
+    b.p = d[k].p;
+    b.kc = make_consts<T>(d[k].p);
+    b.q[0] = static_cast<T*>(d[k].q[0]);
+    b.q[1] = static_cast<T*>(d[k].q[1]);
+    b.solid = d[k].solid;
+    b.Kref = d[k].Kref;
+    b.Kcur = d[k].Kcur;
+    b.colsum = d[k].colsum;
+    b.sc = d[k].sc;
+    b.rhoE_d = d[k].rhoE_d;
+    b.rt = sizeof(T) == 8 ? (const T*)d[k].rhoE_d : (const T*)d[k].rhoE_f;
+    out[k] = b;
+  }
+}
+
+void batch_fill_table(const BatchDomainDesc* d, int ndom, bool f64, void* host_dst) {
+  if (f64)
+    fill_table_t<double>(d, ndom, host_dst);
+  else
+    fill_table_t<float>(d, ndom, host_dst);
+}
+
+template <typename T, bool DEV>
+static int batch_grid_t() {
+  static int grid = 0;
+  if (!grid) {
+    const size_t smem = sizeof(Smem<T>);
+    cudaFuncSetAttribute(batch_step_kernel<T, DEV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_step_kernel<T, DEV>, NT, smem);
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    grid = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+  }
+  return grid;
+}
+
+int batch_grid_size(bool f64) { return f64 ? batch_grid_t<double, false>() : batch_grid_t<float, true>(); }
+
+void launch_batch_step(bool f64, const void* table, const int4* tiles, int ntiles, int parity,
+                       cudaStream_t st) {
+  dim3 block(TX, TY);
+  if (f64) {
+    const int grid = batch_grid_t<double, false>();
+    batch_step_kernel<double, false><<<grid < ntiles ? grid : ntiles, block, sizeof(Smem<double>), st>>>(
+        static_cast<const BatchDomain<double>*>(table), tiles, ntiles, parity);
+  } else {
+    const int grid = batch_grid_t<float, true>();
+    batch_step_kernel<float, true><<<grid < ntiles ? grid : ntiles, block, sizeof(Smem<float>), st>>>(
+        static_cast<const BatchDomain<float>*>(table), tiles, ntiles, parity);
+  }
+}
+
+void launch_batch_finalize(bool f64, const void* table, int ndom, double cfl, int count_step,
+                           cudaStream_t st) {
+  if (f64)
+    batch_finalize_kernel<double><<<ndom, 256, 0, st>>>(static_cast<const BatchDomain<double>*>(table),
+                                                        cfl, count_step);
+  else
+    batch_finalize_kernel<float><<<ndom, 256, 0, st>>>(static_cast<const BatchDomain<float>*>(table),
+                                                       cfl, count_step);
+}
+
+void launch_batch_prepare(bool f64, const void* table, int ndom, double cfl, cudaStream_t st) {
+  const int grid = (ndom + 255) / 256;
+  if (f64)
+    batch_prepare_kernel<double><<<grid, 256, 0, st>>>(static_cast<const BatchDomain<double>*>(table), ndom, cfl);
+  else
+    batch_prepare_kernel<float><<<grid, 256, 0, st>>>(static_cast<const BatchDomain<float>*>(table), ndom, cfl);
+}
 
 void launch_step_f64(const StepParams& p, const StateF64& s, const uint8_t* solid,
                      const int32_t* Kcur, unsigned long long* colsum, DevScalars* sc,

@@ -66,6 +66,30 @@ void launch_mass(const StepParams& p, const double* q, const uint8_t* solid, dou
                  int nblocks, double* out, cudaStream_t st);
 void launch_zero_solid(const StepParams& p, double* q, const uint8_t* solid, cudaStream_t st);
 
+// Host description of one domain of a batch (device pointers).
+struct BatchDomainDesc {
+  StepParams p;
+  void* q[2];
+  const uint8_t* solid;
+  int32_t* Kref;
+  int32_t* Kcur;
+  unsigned long long* colsum;
+  DevScalars* sc;
+  const double* rhoE_d;
+  const float* rhoE_f;
+};
+
+// Device table of a batch: batch_table_bytes bytes, filled on the host by
+// batch_fill_table and copied to the device by the caller.
+size_t batch_table_bytes(int ndom, bool f64);
+void batch_fill_table(const BatchDomainDesc* descs, int ndom, bool f64, void* host_dst);
+int batch_grid_size(bool f64);
+void launch_batch_step(bool f64, const void* table, const int4* tiles, int ntiles, int parity,
+                       cudaStream_t st);
+void launch_batch_finalize(bool f64, const void* table, int ndom, double cfl, int count_step,
+                           cudaStream_t st);
+void launch_batch_prepare(bool f64, const void* table, int ndom, double cfl, cudaStream_t st);
+
 // Message returned by fv_last_error() on this thread.
 void set_last_error(const char* msg);
 

@@ -75,13 +75,30 @@ _lib.fv_host_cell_ops.argtypes = [_D]
 _lib.fv_step_static.argtypes = [C.POINTER(fv_grid), C.POINTER(fv_eos), C.POINTER(C.c_int32),
                                 C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, _D]
 _lib.fv_step_static.restype = C.c_int
+_B = C.c_void_p
+_lib.fv_batch_create.argtypes = [C.c_int32, C.POINTER(fv_grid), C.POINTER(fv_eos), C.POINTER(fv_bc),
+                                 C.c_int, C.c_void_p, C.POINTER(_B)]
+_lib.fv_batch_set_state.argtypes = [_B, C.c_int32, C.c_void_p, C.c_int]
+_lib.fv_batch_step.argtypes = [_B, C.c_int32, C.c_double]
+_lib.fv_batch_step_timed.argtypes = [_B, C.c_int32, C.c_double, _D]
+_lib.fv_batch_get_state.argtypes = [_B, C.c_int32, C.c_void_p, C.c_int]
+_lib.fv_batch_get_diag.argtypes = [_B, C.c_int32, C.POINTER(fv_diag)]
+_lib.fv_batch_size.argtypes = [_B]
+_lib.fv_batch_size.restype = C.c_int32
+_lib.fv_batch_destroy.argtypes = [_B]
+_lib.fv_batch_destroy.restype = None
+for _f in ("fv_batch_create", "fv_batch_set_state", "fv_batch_step", "fv_batch_step_timed",
+           "fv_batch_get_state", "fv_batch_get_diag"):
+    getattr(_lib, _f).restype = C.c_int
 _lib.fv_host_cell_ops.restype = C.c_int
 _lib.fv_host_yface.restype = C.c_int
 
 ABI_SYMBOLS = ("fv_create", "fv_set_state", "fv_step", "fv_step_timed", "fv_get_state",
                "fv_get_levels",
                "fv_get_diag", "fv_destroy", "fv_last_error", "fv_version", "fv_host_xface",
-               "fv_host_yface", "fv_host_cell_ops", "fv_step_static")
+               "fv_host_yface", "fv_host_cell_ops", "fv_step_static", "fv_batch_create",
+               "fv_batch_set_state", "fv_batch_step", "fv_batch_step_timed", "fv_batch_get_state",
+               "fv_batch_get_diag", "fv_batch_size", "fv_batch_destroy")
 
 
 def _check(st):
@@ -240,6 +257,69 @@ class Solver:
         if self.h:
             fv_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Ensemble of independent cases advanced together (fv_batch_*)."""
+
+    def __init__(self, case_list, prec: int = FV_FP64, stream: int | None = None):
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+            except ImportError:  # pragma: no cover
+                stream = 0
+        self.cases = list(case_list)
+        n = len(self.cases)
+        self._solids = [np.ascontiguousarray(c.solid, dtype=np.uint8) for c in self.cases]
+        grids = (fv_grid * n)(*[fv_grid(c.nx, c.ny, c.x0, c.y0, c.dx, c.dy) for c in self.cases])
+        eos = (fv_eos * n)(*[fv_eos(c.rho0, c.k0, c.gamma, c.g, c.eps) for c in self.cases])
+        bcs = (fv_bc * n)(*[fv_bc((C.c_int32 * 4)(*c.sides), s.ctypes.data_as(C.POINTER(C.c_uint8)))
+                            for c, s in zip(self.cases, self._solids)])
+        self.b = _B()
+        _check(_lib.fv_batch_create(n, grids, eos, bcs, int(prec), C.c_void_p(stream),
+                                    C.byref(self.b)))
+
+    def set_state(self, dom: int, q) -> None:
+        if isinstance(q, np.ndarray):
+            q = np.ascontiguousarray(q, dtype=np.float64)
+        p, dev = _ptr(q)
+        _check(_lib.fv_batch_set_state(self.b, int(dom), C.c_void_p(p), dev))
+
+    def step(self, n: int, cfl: float) -> None:
+        _check(_lib.fv_batch_step(self.b, int(n), float(cfl)))
+
+    def step_timed(self, n: int, cfl: float) -> float:
+        t = C.c_double(0.0)
+        _check(_lib.fv_batch_step_timed(self.b, int(n), float(cfl), C.byref(t)))
+        return t.value
+
+    def get_state(self, dom: int, out=None):
+        c = self.cases[dom]
+        if out is None:
+            out = np.empty((4, c.ny, c.nx), dtype=np.float64)
+        p, dev = _ptr(out)
+        _check(_lib.fv_batch_get_state(self.b, int(dom), C.c_void_p(p), dev))
+        return out
+
+    def diag(self, dom: int) -> fv_diag:
+        d = fv_diag()
+        _check(_lib.fv_batch_get_diag(self.b, int(dom), C.byref(d)))
+        return d
+
+    def size(self) -> int:
+        return int(_lib.fv_batch_size(self.b))
+
+    def close(self) -> None:
+        if self.b:
+            _lib.fv_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:

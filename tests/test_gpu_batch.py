@@ -1,0 +1,85 @@
+"""Batched ensemble (fv_batch_*) against the single-domain path and the oracle.
+
+Each domain of an ensemble runs the same per-tile arithmetic with its own dt;
+the batched and single-domain kernels are separate instantiations whose
+roundoff may differ, so the comparison is at CFL 0.45 (where roundoff is not
+amplified) with the parity tolerances: 1e-12 relative (FP64), 1e-5 (FP32)."""
+import numpy as np
+import pytest
+
+from paper_1806_04960_gb300 import cases
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fv():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1806_04960_gb300 import build
+    build.build()
+    from paper_1806_04960_gb300 import fv as mod
+    return mod
+
+
+def small_ensemble():
+    doms = cases.weir_domains(count=5, seed=77, nmin=40, nmax=150)
+    doms.append(cases.c1())
+    doms.append(cases.perturbed(cases.dambreak(33, 17, lx=1.0, ly=0.5, x_col=0.3), 5))
+    return doms
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batch_equals_single_domain_runs(fv, prec):
+    doms = small_ensemble()
+    b = fv.Batch(doms, prec)
+    for k, c in enumerate(doms):
+        b.set_state(k, c.q)
+    b.step(7, 0.45)
+    b.step(6, 0.45)
+    tol = 1e-12 if prec == 0 else 1e-5
+    for k, c in enumerate(doms):
+        s = fv.Solver(c, prec)
+        s.set_state(c.q)
+        s.step(13, 0.45)
+        ref = s.get_state()
+        dref = s.diag()
+        s.close()
+        got = b.get_state(k)
+        dg = b.diag(k)
+        for v in range(4):
+            scale = np.abs(ref[v]).max() or 1.0
+            assert np.abs(got[v] - ref[v]).max() <= tol * scale, (k, v)
+        assert abs(dg.t - dref.t) <= tol * dref.t and dg.steps == 13 and dg.status == 0
+    ts = {b.diag(k).t for k in range(len(doms))}
+    assert len(ts) > 1          # per-domain dt
+    b.close()
+
+
+def test_batch_domain_matches_oracle(fv):
+    doms = small_ensemble()
+    b = fv.Batch(doms, fv.FV_FP64)
+    for k, c in enumerate(doms):
+        b.set_state(k, c.q)
+    b.step(20, 0.45)
+    for k in (0, 5):
+        qo, to, _, _ = O.run(doms[k], 20, cfl=0.45)
+        got = b.get_state(k)
+        for v in range(4):
+            scale = np.abs(qo[v]).max() or 1.0
+            assert np.abs(got[v] - qo[v]).max() <= 1e-10 * scale
+        assert abs(b.diag(k).t - to) <= 1e-12 * to
+    b.close()
+
+
+def test_batch_rejects_bad_input(fv):
+    doms = small_ensemble()[:2]
+    b = fv.Batch(doms, fv.FV_FP64)
+    b.set_state(0, doms[0].q)
+    with pytest.raises(fv.FvError):
+        b.step(1, 0.9)            # domain 1 has no state
+    with pytest.raises(fv.FvError):
+        b.set_state(5, doms[0].q)
+    b.close()
