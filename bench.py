@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--only", choices=("f32", "f64"), default=None,
                     help="time one path only (profiling runs)")
+    ap.add_argument("--workload", choices=("dambreak", "drop"), default="dambreak",
+                    help="drop: the 2048^2 elliptical drop, FP32 vs FP64 semi-axis histories")
     return ap.parse_args()
 
 
@@ -397,8 +399,62 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def drop_axes(case, q):
+    """Semi-axes from the alpha = 0.5 crossings on the positive x and y axes."""
+    import numpy as np
+    n = case.nx
+    col = 0.5 * (q[3][:, n // 2 - 1] + q[3][:, n // 2])
+    row = 0.5 * (q[3][n // 2 - 1, :] + q[3][n // 2, :])
+    y, x = case.yc(), case.xc()
+    up = np.flatnonzero((y[:-1] > 0) & (col[:-1] >= 0.5) & (col[1:] < 0.5))
+    rt = np.flatnonzero((x[:-1] > 0) & (row[:-1] >= 0.5) & (row[1:] < 0.5))
+    if len(up) == 0 or len(rt) == 0:
+        return float("nan"), float("nan")
+    u, r = up[0], rt[0]
+    return (float(x[r] + (row[r] - 0.5) / (row[r] - row[r + 1]) * case.dx),
+            float(y[u] + (col[u] - 0.5) / (col[u] - col[u + 1]) * case.dy))
+
+
+def run_drop(args):
+    """Config 3: oscillating elliptical drop (g = 0) on [-2,2]^2 at 2048^2, 2000
+    steps at CFL 0.9; semi-axis histories of the FP32 and FP64 paths and their
+    difference.  The exact-solution values come from the drop ODE of the tests
+    only for reporting, not as an input."""
+    import torch
+    from paper_1806_04960_gb300 import build, cases
+    build.build()
+    from paper_1806_04960_gb300 import fv
+    case = cases.drop(2048)
+    hist = {}
+    rates = {}
+    for name, prec in (("f64", fv.FV_FP64), ("f32", fv.FV_FP32_DEV)):
+        s = fv.Solver(case, prec)
+        s.set_state(case.q)
+        h = []
+        ms = 0.0
+        for k in range(20):
+            _, tot = s.step_timed(100, case.cfl)
+            ms += tot
+            d = s.diag()
+            a, b = drop_axes(case, s.get_state())
+            h.append({"step": (k + 1) * 100, "t": d.t, "a": a, "b": b, "status": d.status})
+        s.close()
+        hist[name] = h
+        rates[name] = case.nx * case.ny * 2000 / (ms * 1e-3) / 1e6
+    torch.cuda.synchronize()
+    db = max(abs(p["b"] - q["b"]) / q["b"] for p, q in zip(hist["f32"], hist["f64"]))
+    da = max(abs(p["a"] - q["a"]) / q["a"] for p, q in zip(hist["f32"], hist["f64"]))
+    print(json.dumps({"workload": "drop_2048x2048", "steps": 2000, "cfl": case.cfl,
+                      "mcups": rates, "max_rel_diff_f32_vs_f64": {"a": da, "b": db},
+                      "final": {"f64": hist["f64"][-1], "f32": hist["f32"][-1]},
+                      "history": hist}), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "drop":
+        run_drop(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

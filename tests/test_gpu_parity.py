@@ -281,3 +281,22 @@ def test_fp32_mass_conservation(fv):
     m1 = s.diag().mass
     s.close()
     assert abs(m1 - m0) <= 1e-5 * m0
+
+
+def test_drop_fp32_follows_fp64_and_exact_solution(fv):
+    """Config 3 at 512^2 (2000 steps, t = 4.4e-3): the FP32 and FP64 semi-axes
+    agree to 1e-3 and follow the exact elliptical-drop solution within 2 %."""
+    from oracle_refs import drop_semi_axes
+    from test_oracle_pins import drop_axes
+    c = cases.drop(512)
+    res = {}
+    for prec in (fv.FV_FP64, fv.FV_FP32_DEV):
+        s = fv.Solver(c, prec)
+        s.set_state(c.q)
+        t = s.step(2000, c.cfl, want_time=True)
+        res[prec] = (t, drop_axes(c, s.get_state()))
+        s.close()
+    (t64, (a64, b64)), (t32, (a32, b32)) = res[fv.FV_FP64], res[fv.FV_FP32_DEV]
+    assert abs(b32 - b64) <= 1e-3 * b64 and abs(a32 - a64) <= 1e-3 * a64
+    a_ex, b_ex = drop_semi_axes(t64, nsub=4000)
+    assert abs(b64 - b_ex) <= 0.02 * b_ex and abs(a64 - a_ex) <= 0.02 * a_ex
