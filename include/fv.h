@@ -131,6 +131,51 @@ fv_status fv_get_diag(fv_handle* h, fv_diag* d);
 /* Release the handle and its device memory (synchronises; NULL is a no-op). */
 void fv_destroy(fv_handle* h);
 
+/* ---- Discrete adjoint (reverse mode) of n time steps.
+ *
+ * Loss of a gauge record: L = sum_{n=1..N} dt_n sum_g (m_g^n - T_g^n)^2, m =
+ * alpha rho at gauge cell g after step n, dt_n the step's dt.  fv_adjoint runs
+ * the N steps from the handle's current state Q^0 (like fv_step(h, N, cfl);
+ * the handle holds Q^N afterwards) and returns dL/dQ^0.  The paper computes
+ * no gradients; the derivative is that of the scheme of Eq. (Scheme) with the
+ * quantities that are piecewise constant in the state held at their forward
+ * values: dt_n, the detected levels K_i^n (Eq. (Free_surf_detector)), and each
+ * branch of the step (the Barth-Jespersen factor's active face and stencil
+ * extremum, |u|, sign(v) with sign(0) = 0, the order switch alpha <= 10 eps,
+ * the first-order fallback).  It is evaluated in the handle's arithmetic type
+ * (FP64, or FP32 deviation form) and accumulated in double.  States at every
+ * checkpoint_every-th step are kept on the device and each segment is
+ * replayed once before it is reversed (ceil(sqrt(N)) when 0: about 2 sqrt(N)
+ * stored states, one extra forward pass). */
+typedef struct {
+  int32_t nsteps;           /* N >= 1 */
+  double cfl;               /* (0, 1] */
+  int32_t ngauges;          /* >= 1 */
+  const int64_t* gauges;    /* host, ngauges fluid cell indices j*nx + i (repeats allowed) */
+  const double* target;     /* host, N*ngauges: T_g^n at [(n-1)*ngauges + g] */
+  int32_t checkpoint_every; /* >= 0; 0 = ceil(sqrt(N)) */
+  double* m_series;         /* nullable host, N*ngauges: receives m_g^n */
+} fv_adjoint_spec;
+
+typedef struct {
+  double loss;              /* L */
+  double t;                 /* simulated time after the N steps */
+  int32_t checkpoints;      /* stored states */
+  int32_t recomputed_steps; /* forward steps replayed by the reverse sweep */
+  double forward_ms;        /* device time of the forward sweep (CUDA events) */
+  double reverse_ms;        /* device time of the reverse sweep, replays included */
+} fv_adjoint_info;
+
+/* dL_dq0: 4 planes (alpha rho, alpha rho u, alpha rho v, alpha) of nx*ny
+ * doubles, layout of fv_set_state, zero in solid cells; host (on_device = 0)
+ * or device memory (1).  info: nullable.  Synchronises.  FV_EINVAL on bad
+ * arguments (a gauge outside the grid or in a solid cell, a non-finite
+ * target), FV_ENONFINITE if a forward step produced a non-admissible state,
+ * FV_ENOMEM if the workspace (about (2 sqrt(N) + 20) state-sized buffers)
+ * cannot be allocated. */
+fv_status fv_adjoint(fv_handle* h, const fv_adjoint_spec* spec, double* dL_dq0, int on_device,
+                     fv_adjoint_info* info);
+
 /* ---- Batched ensemble of independent domains (configs of uneven sizes,
  * parameter sweeps).  Each domain has its own grid, equation of state,
  * boundaries, free-surface levels, dt (its own CFL condition) and time; one

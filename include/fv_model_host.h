@@ -19,6 +19,10 @@
 #ifndef FV_MODEL_HOST_H
 #define FV_MODEL_HOST_H
 
+#include <stdint.h>
+
+#include "fv.h"
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -33,6 +37,33 @@ int fv_host_yface(const double* model, const double* qm, const double* qp, doubl
  * out[0..4] = additions, multiplications, divisions, square roots,
  * comparisons.  Returns 0, or 1 on a null pointer. */
 int fv_host_cell_ops(double* out);
+
+/* Forward value and reverse-mode derivative of one per-face or per-cell
+ * function of the kernels (the building blocks of fv_adjoint), on the host.
+ * which = 0: x face, in = qm[4], qp[4], out = D-[4], D+[4];
+ *         1: y face (dap = c2 (dq0 - rho0 dq3)), same layout;
+ *         2: reconstruction of Section 3.4 (limiter, order switch, predictor,
+ *            face states, admissibility fallback): in = Qf[4], fW[4], fE[4],
+ *            fS[4], fN[4], mx[4], mn[4], alpha^E (29); out = face states
+ *            W, E, S, N [16], centre [4], limited alpha slopes [2];
+ *         3: interior integral: in = fW[4], fE[4], fS[4], fN[4], centre[4],
+ *            alpha^E, dax, day (23); out = Ix[4], Iy[4].
+ * k (which 2, 3) = {dx, dy, dt, rhoE_c, rhoE_S, rhoE_N}; the equilibrium
+ * masses are alpha^E rhoE.  If lout is not null, lin receives d<lout, out>/d in
+ * with every branch held as at `in`.  Returns 0, or 1 on a bad argument. */
+int fv_host_adj_check(int which, const double* model, const double* k, const double* in,
+                      const double* lout, double* out, double* lin);
+
+/* One reverse step of fv_adjoint on the host: lam_out = lam + (dQ^{n+1}/dQ^n)^T
+ * lam for the step with levels K (nx int32) and time step dt held fixed,
+ * through the same per-cell and per-face code as the adjoint kernels, in the
+ * arithmetic of prec (FV_FP64: full state in double; FV_FP32_DEV: q rounded
+ * to the float deviation form relative to K, float arithmetic).  grid, eos,
+ * side, solid (ny*nx) as for fv_create; q (full state), lam, lam_out: 4 planes
+ * of ny*nx doubles (host).  Returns 0, or 1 on a bad argument. */
+int fv_host_adjoint_step(const fv_grid* grid, const fv_eos* eos, const int32_t side[4],
+                         const uint8_t* solid, const double* q, const int32_t* K, double dt,
+                         const double* lam, double* lam_out, int prec);
 
 #ifdef __cplusplus
 }

@@ -678,13 +678,18 @@ bool admissible(const double q[4]) {
   return q[0] > 0.0 && q[3] > 0.0;
 }
 
-// One time step Q^n -> Q^{n+1}.  Returns 0, or 2 if a non-admissible state appears.
-int full_step(Ctx& C, double cfl, double* q_out) {
-  const Grid& G = C.G;
-  const size_t n = (size_t)G.nx * G.ny;
+// Levels (reading R-det) and dt (reading R-cfl) of the step from the state C.Q.
+void levels_and_dt(Ctx& C, double cfl) {
   detect_levels(C);
   const double rate = max_rate(C);
   C.dt = rate > 0.0 ? cfl / rate : 0.0;
+}
+
+// One time step Q^n -> Q^{n+1} with the levels C.K and the step C.dt.
+// Returns 0, or 2 if a non-admissible state appears.
+int advance(Ctx& C, double* q_out) {
+  const Grid& G = C.G;
+  const size_t n = (size_t)G.nx * G.ny;
   std::vector<Rec> rec(n);
   std::vector<uint8_t> fl(n);
   for (size_t c = 0; c < n; ++c) fl[c] = C.solid[c] == 0;
@@ -728,6 +733,12 @@ int full_step(Ctx& C, double cfl, double* q_out) {
       for (int v = 0; v < 4; ++v) q_out[v * n + c] = out[v];
     }
   return bad ? 2 : 0;
+}
+
+// One time step Q^n -> Q^{n+1}.  Returns 0, or 2 if a non-admissible state appears.
+int full_step(Ctx& C, double cfl, double* q_out) {
+  levels_and_dt(C, cfl);
+  return advance(C, q_out);
 }
 
 Ctx make_ctx(const int32_t* gi, const double* gd, const double* eos, const int32_t* sides,
@@ -812,6 +823,44 @@ int orc_run(const int32_t* gi, const double* gd, const double* eos, const int32_
   }
   std::memcpy(q_out, a.data(), n4 * sizeof(double));
   if (t_out) *t_out = t;
+  return rc;
+}
+
+// n time steps recording, for each step, its levels (K_hist, nsteps*nx,
+// nullable), its dt (dt_hist, nullable) and alpha rho at the gauge cells after
+// it (m_hist, nsteps*ngauges, nullable).  With dt_fix and K_fix (both given),
+// step s uses dt_fix[s] and the levels K_fix[s*nx ..] instead of those of its
+// state: the map whose derivative the gradient checks take by finite
+// differences.
+int orc_run_record(const int32_t* gi, const double* gd, const double* eos, const int32_t* sides,
+                   const uint8_t* solid, const double* q_in, double* q_out, int nsteps,
+                   double cfl, const double* dt_fix, const int32_t* K_fix, double* dt_hist,
+                   int32_t* K_hist, const int64_t* gauges, int ngauges, double* m_hist) {
+  Ctx C = make_ctx(gi, gd, eos, sides, solid, q_in);
+  if (!valid(C) || nsteps < 0 || !(cfl > 0.0) || (!dt_fix) != (!K_fix)) return 1;
+  const size_t n1 = (size_t)C.G.nx * C.G.ny, n4 = 4 * n1;
+  for (int g = 0; g < ngauges; ++g)
+    if (gauges[g] < 0 || gauges[g] >= (int64_t)n1) return 1;
+  std::vector<double> a(q_in, q_in + n4), b(n4);
+  int rc = 0;
+  for (int s = 0; s < nsteps; ++s) {
+    C.Q = a.data();
+    if (dt_fix) {
+      C.K.assign(K_fix + (size_t)s * C.G.nx, K_fix + (size_t)(s + 1) * C.G.nx);
+      C.dt = dt_fix[s];
+    } else {
+      levels_and_dt(C, cfl);
+    }
+    if (dt_hist) dt_hist[s] = C.dt;
+    if (K_hist)
+      for (int i = 0; i < C.G.nx; ++i) K_hist[(size_t)s * C.G.nx + i] = C.K[i];
+    rc = advance(C, b.data());
+    a.swap(b);
+    if (m_hist)
+      for (int g = 0; g < ngauges; ++g) m_hist[(size_t)s * ngauges + g] = a[gauges[g]];
+    if (rc) break;
+  }
+  std::memcpy(q_out, a.data(), n4 * sizeof(double));
   return rc;
 }
 

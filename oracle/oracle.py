@@ -51,6 +51,9 @@ def lib():
             L.orc_step_cells.argtypes = [_I32, _D, _D, _I32, _U8, _D, C.c_double, _I64, C.c_int,
                                          _D, _D]
             L.orc_step_cells.restype = C.c_int
+            L.orc_run_record.argtypes = [_I32, _D, _D, _I32, _U8, _D, _D, C.c_int, C.c_double,
+                                         _D, _I32, _D, _I32, _I64, C.c_int, _D]
+            L.orc_run_record.restype = C.c_int
             L.orc_set_threads.argtypes = [C.c_int]
             L.orc_max_threads.restype = C.c_int
             L.orc_flux.argtypes = [_D, _D, _D, _D]
@@ -108,6 +111,37 @@ def run(case, nsteps: int, q=None, cfl: float | None = None):
     if rc == 2:
         raise OracleError("non-admissible state (non-finite, alpha <= 0 or alpha*rho <= 0)")
     return qout, float(t[0]), dts[:nsteps], K
+
+
+def run_record(case, nsteps: int, gauges, q=None, cfl: float | None = None, dt_fix=None,
+               K_fix=None):
+    """Advance ``nsteps`` steps recording each step's dt, levels and the alpha
+    rho at the flat gauge cells after it.  With ``dt_fix`` (nsteps) and
+    ``K_fix`` (nsteps, nx) the steps use those instead of their own.
+    Returns (q_out, dt (nsteps), K (nsteps, nx), m (nsteps, ngauges))."""
+    L = lib()
+    gi, gd, eos, sides, solid = _case_args(case)
+    qin = np.ascontiguousarray(case.q if q is None else q, dtype=np.float64)
+    qout = np.empty_like(qin)
+    g = np.ascontiguousarray(gauges, dtype=np.int64)
+    n = max(nsteps, 1)
+    dts = np.zeros(n)
+    Ks = np.zeros((n, case.nx), dtype=np.int32)
+    ms = np.zeros((n, max(g.size, 1)))
+    if (dt_fix is None) != (K_fix is None):
+        raise ValueError("give both dt_fix and K_fix or neither")
+    dfix = None if dt_fix is None else np.ascontiguousarray(dt_fix, dtype=np.float64)
+    kfix = None if K_fix is None else np.ascontiguousarray(K_fix, dtype=np.int32)
+    rc = L.orc_run_record(_p(gi, _I32), _p(gd), _p(eos), _p(sides, _I32), _p(solid, _U8),
+                          _p(qin), _p(qout), int(nsteps), float(case.cfl if cfl is None else cfl),
+                          None if dfix is None else _p(dfix),
+                          None if kfix is None else _p(kfix, _I32), _p(dts), _p(Ks, _I32),
+                          _p(g, _I64), int(g.size), _p(ms))
+    if rc == 1:
+        raise OracleError("invalid input")
+    if rc == 2:
+        raise OracleError("non-admissible state (non-finite, alpha <= 0 or alpha*rho <= 0)")
+    return qout, dts[:nsteps], Ks[:nsteps], ms[:nsteps, :g.size]
 
 
 def dt_levels(case, q=None, cfl: float | None = None):

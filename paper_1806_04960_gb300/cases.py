@@ -154,6 +154,75 @@ def c1_lake(nx: int = 128, ny: int = 64) -> Case:
     return dambreak(nx, ny, rects=[C1_RECT], lake_level=1.0, name=f"lake_{nx}x{ny}", steps=200)
 
 
+C5_TARGET_RECT = (2.5, 2.7, 0.0, 0.25)
+
+
+def c5(nx: int = 512, ny: int = 256, steps: int = 2000, cfl: float = 0.45) -> Case:
+    """Gradient workload: the dam break of c1 (k0 = 4.36e5) at nx x ny."""
+    return dambreak(nx, ny, rects=[C1_RECT], k0=4.36e5, cfl=cfl, name=f"adjoint_{nx}x{ny}",
+                    steps=steps)
+
+
+def c5_target(nx: int = 512, ny: int = 256, seed: int = 5, cfl: float = 0.45) -> Case:
+    """Initial state whose gauge record is the loss's target: column height
+    0.95, obstacle height 0.25, density and velocity perturbed (seed 5)."""
+    c = dambreak(nx, ny, h_col=0.95, rects=[C5_TARGET_RECT], k0=4.36e5, cfl=cfl,
+                 name=f"adjoint_target_{nx}x{ny}")
+    return perturbed(c, seed)
+
+
+def c5_gauges(c: Case, count: int = 16, seed: int = 5, region=(0.0, 2.0, 0.0, 1.2)):
+    """``count`` distinct flat cell indices j*nx + i drawn (PCG64, seed) from the
+    fluid cells whose centre lies in region = (x_left, x_right, y_bottom, y_top),
+    where the dam-break wave passes; sorted."""
+    xl, xr, yb, yt = region
+    X, Y = np.meshgrid(c.xc(), c.yc())
+    ok = (c.solid == 0) & (X >= xl) & (X <= xr) & (Y >= yb) & (Y <= yt)
+    pool = np.flatnonzero(ok.ravel())
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.sort(rng.choice(pool, size=count, replace=False)).astype(np.int64)
+
+
+def c5_directions(c: Case, count: int = 32, seed: int = 32) -> np.ndarray:
+    """``count`` seeded perturbation directions of the initial state (count, 4,
+    ny, nx): standard normal factors times alpha rho and alpha on fluid cells
+    (relative perturbations of the two fields the gradient is taken for), zero
+    in the momenta and in solid cells."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    d = np.zeros((count, 4, c.ny, c.nx))
+    fluid = c.solid == 0
+    for k in range(count):
+        d[k, 0] = rng.standard_normal((c.ny, c.nx)) * c.q[0]
+        d[k, 3] = rng.standard_normal((c.ny, c.nx)) * c.q[3]
+        d[k][:, ~fluid] = 0.0
+    return d
+
+
+def generic(c: Case, seed: int, scale: float = 1e-3) -> Case:
+    """``perturbed`` plus a seeded perturbation of the volume fraction
+    (liquid alpha = 1 - scale U(0,1), gas alpha = eps (1 + 0.1 N(0,1)) clipped
+    to [eps/2, 2 eps]), alpha rho rescaled to keep the density: a state with no
+    two cells exactly equal in any component."""
+    p = perturbed(c, seed, scale)
+    rng = np.random.Generator(np.random.PCG64(seed + 1))
+    q = p.q.copy()
+    fluid = c.solid == 0
+    a = q[3]
+    liquid = a > 0.5
+    rho = np.where(fluid, q[0] / np.where(a > 0, a, 1.0), 0.0)
+    a_new = np.where(liquid, 1.0 - scale * rng.uniform(size=a.shape),
+                     np.clip(c.eps * (1.0 + 0.1 * rng.standard_normal(a.shape)), 0.5 * c.eps,
+                             2.0 * c.eps))
+    u = np.where(fluid, q[1] / np.where(q[0] > 0, q[0], 1.0), 0.0)
+    v = np.where(fluid, q[2] / np.where(q[0] > 0, q[0], 1.0), 0.0)
+    q[3] = a_new
+    q[0] = a_new * rho
+    q[1] = q[0] * u
+    q[2] = q[0] * v
+    q[:, ~fluid] = 0.0
+    return replace(c, q=q, name=c.name + f"_g{seed}")
+
+
 def c2(nx: int = 4096, ny: int = 2048, steps: int = 1000) -> Case:
     """Throughput workload: the dam break at 4096 x 2048 with 8 seeded obstacles."""
     return dambreak(nx, ny, rects=c2_rects(), name=f"dambreak8_{nx}x{ny}", steps=steps)

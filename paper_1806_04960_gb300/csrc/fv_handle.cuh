@@ -1,0 +1,53 @@
+// Handle of libfv (opaque to callers: include/fv.h declares it incomplete).
+// Internal header shared by the C ABI translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "fv.h"
+#include "fv_kernels.cuh"
+
+struct fv_handle {
+  fv_grid grid;
+  fv_eos eos;
+  int side[4];
+  fv_prec prec;
+  cudaStream_t stream;
+  size_t ncell;
+  uint8_t* d_solid = nullptr;
+  int32_t* d_Kref = nullptr;
+  int32_t* d_Kcur = nullptr;
+  unsigned long long* d_colsum = nullptr;
+  fv::DevScalars* d_sc = nullptr;
+  double* d_rhoE = nullptr;
+  float* d_rhoE_f = nullptr;
+  void* d_q[2] = {nullptr, nullptr};
+  int cur = 0;
+  double* d_stage = nullptr;    // FP32 path: double staging buffer
+  double* d_partial = nullptr;  // mass partials
+  double* d_mass = nullptr;
+  int mass_blocks = 0;
+  bool has_state = false;
+  double cfl = 0.9;
+};
+
+inline fv::StepParams params_of(const fv_handle* h, double cfl) {
+  fv::StepParams p;
+  p.nx = h->grid.nx;
+  p.ny = h->grid.ny;
+  p.dx = h->grid.dx;
+  p.dy = h->grid.dy;
+  p.rho0 = h->eos.rho0;
+  p.k0 = h->eos.k0;
+  p.g = h->eos.g;
+  p.eps = h->eos.eps_gas;
+  p.c2 = h->eos.k0 / h->eos.rho0;
+  p.c = std::sqrt(p.c2);
+  p.kappa = h->eos.g * h->eos.rho0 / h->eos.k0;
+  for (int s = 0; s < 4; ++s) p.side[s] = h->side[s];
+  p.cfl = cfl;
+  return p;
+}
+

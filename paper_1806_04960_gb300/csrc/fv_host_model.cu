@@ -1,6 +1,7 @@
 // Host instantiation of the device face solvers (include/fv_model_host.h).
 #include <cmath>
 
+#include "fv_adjoint.cuh"
 #include "fv_model.cuh"
 #include "fv_model_host.h"
 
@@ -33,6 +34,100 @@ extern "C" int fv_host_yface(const double* model, const double* qm, const double
   const fv::Phys<double> P = phys(model);
   fv::yface<double>(qm, qp, dq, P.c2 * (dq[0] - P.rho0 * dq[3]), P, Dm, Dp);
   return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Forward value and reverse-mode derivative of one per-face or per-cell
+// function of the kernels, for finite-difference checks on the host.
+// ---------------------------------------------------------------------------
+namespace {
+
+fv::ReconConsts<double> recon_consts(const double* model, const double* k) {
+  const fv::Phys<double> P = phys(model);
+  fv::ReconConsts<double> R;
+  R.half_dx = 0.5 * k[0];
+  R.half_dy = 0.5 * k[1];
+  R.inv_2dx = 1.0 / (2.0 * k[0]);
+  R.inv_2dy = 1.0 / (2.0 * k[1]);
+  R.half_dt = 0.5 * k[2];
+  R.ten_eps = 10.0 * model[4];
+  const double eta[4] = {std::ldexp(P.rho0, -20), std::ldexp(P.rho0 * P.c, -10),
+                         std::ldexp(P.rho0 * P.c, -10), std::ldexp(1.0, -20)};
+  for (int v = 0; v < 4; ++v) {
+    R.eta[v] = eta[v];
+    R.inv_eta[v] = 1.0 / eta[v];
+  }
+  return R;
+}
+
+}  // namespace
+
+extern "C" int fv_host_adj_check(int which, const double* model, const double* k, const double* in,
+                                 const double* lout, double* out, double* lin) {
+  if (!model || !in || !out || (lout && !lin)) return 1;
+  const fv::Phys<double> P = phys(model);
+  if (which == 0 || which == 1) {
+    const double* qm = in;
+    const double* qp = in + 4;
+    const double dq[4] = {qp[0] - qm[0], qp[1] - qm[1], qp[2] - qm[2], qp[3] - qm[3]};
+    const double dap = P.c2 * (dq[0] - P.rho0 * dq[3]);
+    if (which == 0) fv::xface<double>(qm, qp, dq, P, out, out + 4);
+    else fv::yface<double>(qm, qp, dq, dap, P, out, out + 4);
+    if (!lout) return 0;
+    double lqm[4] = {0, 0, 0, 0}, lqp[4] = {0, 0, 0, 0}, ldq[4] = {0, 0, 0, 0}, ldap = 0.0;
+    if (which == 0) fv::xface_adj<double>(qm, qp, dq, P, lout, lout + 4, lqm, lqp, ldq);
+    else fv::yface_adj<double>(qm, qp, dq, dap, P, lout, lout + 4, lqm, lqp, ldq, ldap);
+    ldq[0] += P.c2 * ldap;
+    ldq[3] -= P.c2 * P.rho0 * ldap;
+    for (int c = 0; c < 4; ++c) {
+      lin[c] = lqm[c] - ldq[c];
+      lin[4 + c] = lqp[c] + ldq[c];
+    }
+    return 0;
+  }
+  if (!k) return 1;
+  if (which == 2) {
+    // in: Qf[4], fW[4], fE[4], fS[4], fN[4], mx[4], mn[4], aE; k: dx, dy, dt, rEc, rES, rEN
+    // out: fW'[4], fE'[4], fS'[4], fN'[4], base[4], gxa[2]
+    const fv::ReconConsts<double> R = recon_consts(model, k);
+    const double rEc = k[3], rES = k[4], rEN = k[5];
+    const double aE = in[28];
+    const double mEc = aE * rEc, mES = aE * rES, mEN = aE * rEN;
+    double f[4][4];
+    for (int s = 0; s < 4; ++s)
+      for (int c = 0; c < 4; ++c) f[s][c] = in[4 + 4 * s + c];
+    fv::recon_core<double>(in, f[0], f[1], f[2], f[3], in + 20, in + 24, aE, mEc, mES, mEN, rEc, P,
+                           R, out + 16, out + 20);
+    for (int s = 0; s < 4; ++s)
+      for (int c = 0; c < 4; ++c) out[4 * s + c] = f[s][c];
+    if (!lout) return 0;
+    for (int x = 0; x < 29; ++x) lin[x] = 0.0;
+    double laE = 0.0, lmEc = 0.0;
+    fv::recon_core_adj<double>(in, in + 4, in + 8, in + 12, in + 16, in + 20, in + 24, aE, mEc, mES,
+                               mEN, rEc, P, R, lout, lout + 4, lout + 8, lout + 12, lout + 16,
+                               lout + 20, lin, lin + 4, lin + 8, lin + 12, lin + 16, lin + 20,
+                               lin + 24, laE, lmEc);
+    lin[28] = laE + rEc * lmEc;
+    return 0;
+  }
+  if (which == 3) {
+    // in: fW[4], fE[4], fS[4], fN[4], base[4], aE, dax, day; k: dx, dy, dt, rEc, rES, rEN
+    // out: Ix[4], Iy[4]
+    const double rEc = k[3], rES = k[4], rEN = k[5];
+    const double aE = in[20];
+    fv::interior_terms<double>(in, in + 4, in + 8, in + 12, in + 16, aE * rEc, aE * rES, aE * rEN,
+                               in[21], in[22], k[0], k[1], P, out, out + 4);
+    if (!lout) return 0;
+    for (int x = 0; x < 23; ++x) lin[x] = 0.0;
+    double lmEc = 0.0, lmES = 0.0, lmEN = 0.0;
+    fv::interior_terms_adj<double>(in, in + 4, in + 8, in + 12, in + 16, aE * rEc, aE * rES,
+                                   aE * rEN, in[21], in[22], k[0], k[1], P, lout, lout + 4, lin,
+                                   lin + 4, lin + 8, lin + 12, lin + 16, lmEc, lmES, lmEN, lin[21],
+                                   lin[22]);
+    lin[20] = rEc * lmEc + rES * lmES + rEN * lmEN;
+    return 0;
+  }
+  return 1;
 }
 
 // ---------------------------------------------------------------------------

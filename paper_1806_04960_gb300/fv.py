@@ -41,6 +41,18 @@ class fv_diag(C.Structure):
                 ("mass", C.c_double), ("status", C.c_int32)]
 
 
+class fv_adjoint_spec(C.Structure):
+    _fields_ = [("nsteps", C.c_int32), ("cfl", C.c_double), ("ngauges", C.c_int32),
+                ("gauges", C.POINTER(C.c_int64)), ("target", C.POINTER(C.c_double)),
+                ("checkpoint_every", C.c_int32), ("m_series", C.POINTER(C.c_double))]
+
+
+class fv_adjoint_info(C.Structure):
+    _fields_ = [("loss", C.c_double), ("t", C.c_double), ("checkpoints", C.c_int32),
+                ("recomputed_steps", C.c_int32), ("forward_ms", C.c_double),
+                ("reverse_ms", C.c_double)]
+
+
 class FvError(RuntimeError):
     def __init__(self, status, message):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
@@ -92,13 +104,18 @@ for _f in ("fv_batch_create", "fv_batch_set_state", "fv_batch_step", "fv_batch_s
     getattr(_lib, _f).restype = C.c_int
 _lib.fv_host_cell_ops.restype = C.c_int
 _lib.fv_host_yface.restype = C.c_int
+_lib.fv_adjoint.argtypes = [_H, C.POINTER(fv_adjoint_spec), C.c_void_p, C.c_int,
+                            C.POINTER(fv_adjoint_info)]
+_lib.fv_adjoint.restype = C.c_int
+_lib.fv_host_adj_check.argtypes = [C.c_int, _D, _D, _D, _D, _D, _D]
+_lib.fv_host_adj_check.restype = C.c_int
 
 ABI_SYMBOLS = ("fv_create", "fv_set_state", "fv_step", "fv_step_timed", "fv_get_state",
                "fv_get_levels",
                "fv_get_diag", "fv_destroy", "fv_last_error", "fv_version", "fv_host_xface",
-               "fv_host_yface", "fv_host_cell_ops", "fv_step_static", "fv_batch_create",
+               "fv_host_yface", "fv_host_cell_ops", "fv_host_adj_check", "fv_step_static", "fv_batch_create",
                "fv_batch_set_state", "fv_batch_step", "fv_batch_step_timed", "fv_batch_get_state",
-               "fv_batch_get_diag", "fv_batch_size", "fv_batch_destroy")
+               "fv_batch_get_diag", "fv_batch_size", "fv_batch_destroy", "fv_adjoint")
 
 
 def _check(st):
@@ -149,6 +166,29 @@ def fv_host_xface(qm, qp, model):
 def fv_host_yface(qm, qp, model):
     """Host evaluation of the kernels' y-face fluctuations (D-, D+)."""
     return _host_face(_lib.fv_host_yface, qm, qp, model)
+
+
+HOST_ADJ_SIZES = {0: (8, 8), 1: (8, 8), 2: (29, 22), 3: (23, 8)}
+
+
+def fv_host_adj_check(which: int, model, k, x, lout=None):
+    """Host value (and, with lout, reverse derivative d<lout, out>/dx) of one
+    per-face or per-cell building block of the kernels (see fv_model_host.h)."""
+    nin, nout = HOST_ADJ_SIZES[which]
+    m = np.ascontiguousarray(model, dtype=np.float64)
+    kk = np.ascontiguousarray(np.zeros(6) if k is None else k, dtype=np.float64)
+    xi = np.ascontiguousarray(x, dtype=np.float64)
+    assert xi.size == nin
+    out = np.zeros(nout)
+    P = lambda a: a.ctypes.data_as(_D)
+    if lout is None:
+        _check(_lib.fv_host_adj_check(which, P(m), P(kk), P(xi), None, P(out), None) and FV_EINVAL)
+        return out
+    lo = np.ascontiguousarray(lout, dtype=np.float64)
+    assert lo.size == nout
+    lin = np.zeros(nin)
+    _check(_lib.fv_host_adj_check(which, P(m), P(kk), P(xi), P(lo), P(out), P(lin)) and FV_EINVAL)
+    return out, lin
 
 
 def fv_host_cell_ops() -> dict:
@@ -206,6 +246,27 @@ def fv_get_diag(h) -> fv_diag:
     return d
 
 
+def fv_adjoint(h, nsteps: int, cfl: float, gauges, target, grad_out, checkpoint_every: int = 0,
+               want_series: bool = False):
+    """Gradient of the gauge loss (see fv.h) after ``nsteps`` steps with respect
+    to the handle's current state, written to ``grad_out`` (4, ny, nx) float64
+    (numpy or CUDA tensor).  Returns (fv_adjoint_info, m series (nsteps,
+    ngauges) or None)."""
+    g = np.ascontiguousarray(gauges, dtype=np.int64)
+    t = np.ascontiguousarray(target, dtype=np.float64)
+    if t.size != int(nsteps) * g.size:
+        raise ValueError("target must hold nsteps x ngauges values")
+    series = np.zeros((int(nsteps), g.size)) if want_series else None
+    spec = fv_adjoint_spec(int(nsteps), float(cfl), int(g.size),
+                           g.ctypes.data_as(C.POINTER(C.c_int64)), t.ctypes.data_as(_D),
+                           int(checkpoint_every),
+                           series.ctypes.data_as(_D) if want_series else None)
+    info = fv_adjoint_info()
+    p, dev = _ptr(grad_out)
+    _check(_lib.fv_adjoint(h, C.byref(spec), C.c_void_p(p), dev, C.byref(info)))
+    return info, series
+
+
 def fv_destroy(h) -> None:
     _lib.fv_destroy(h)
 
@@ -249,6 +310,16 @@ class Solver:
 
     def levels(self) -> np.ndarray:
         return fv_get_levels(self.h, self.case.nx)
+
+    def adjoint(self, nsteps: int, gauges, target, cfl: float | None = None,
+                checkpoint_every: int = 0, grad=None, want_series: bool = False):
+        """Gauge-loss gradient with respect to the current state (fv_adjoint);
+        the handle advances by ``nsteps``.  Returns (grad, info, series)."""
+        if grad is None:
+            grad = np.empty((4, self.case.ny, self.case.nx), dtype=np.float64)
+        info, series = fv_adjoint(self.h, nsteps, self.case.cfl if cfl is None else cfl, gauges,
+                                  target, grad, checkpoint_every, want_series)
+        return grad, info, series
 
     def diag(self) -> fv_diag:
         return fv_get_diag(self.h)
@@ -326,3 +397,31 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def gauge_loss_function():
+    """torch.autograd.Function computing the gauge loss of fv_adjoint from an
+    initial state tensor; backward returns grad_output * dL/dQ0.
+
+    Usage: L = gauge_loss_function().apply(q0, solver, nsteps, cfl, gauges,
+    target) with q0 a (4, ny, nx) float64 CUDA tensor.  The forward call runs
+    the steps and the reverse sweep together (fv_adjoint) and keeps the
+    gradient; the solver's state is advanced by nsteps."""
+    import torch
+
+    class GaugeLoss(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, q0, solver, nsteps, cfl, gauges, target):
+            q0c = q0.detach().contiguous()
+            solver.set_state(q0c)
+            grad = torch.empty_like(q0c)
+            info, _ = fv_adjoint(solver.h, nsteps, cfl, gauges, target, grad)
+            ctx.save_for_backward(grad)
+            return torch.tensor(info.loss, dtype=q0.dtype, device=q0.device)
+
+        @staticmethod
+        def backward(ctx, gout):
+            (grad,) = ctx.saved_tensors
+            return gout * grad, None, None, None, None, None
+
+    return GaugeLoss

@@ -387,3 +387,20 @@ def test_drop_semi_axis_follows_exact_solution():
     a_ode, b_ode = drop_semi_axes(t_end)
     assert abs(b - b_ode) <= 0.01 * b_ode, (b, b_ode)
     assert abs(a - a_ode) <= 0.01 * a_ode, (a, a_ode)
+
+
+def test_frozen_replay_reproduces_free_run():
+    """orc_run_record with each step's own dt and levels held fixed repeats the
+    free run bitwise (the map the gradient checks difference), and its free run
+    is orc_run's."""
+    c = cases.c1(48, 24)
+    g = np.array([c.nx * 5 + 7, c.nx * 12 + 30], dtype=np.int64)
+    q1, _, dts, K_last = O.run(c, 25, cfl=0.45)
+    q2, dt, K, m = O.run_record(c, 25, g, cfl=0.45)
+    assert np.array_equal(q1, q2) and np.array_equal(dts, dt) and np.array_equal(K[-1], K_last)
+    assert np.array_equal(m[-1], q2[0].ravel()[g])
+    q3, dt3, K3, m3 = O.run_record(c, 25, g, cfl=0.45, dt_fix=dt, K_fix=K)
+    assert np.array_equal(q3, q2) and np.array_equal(m3, m)
+    # a different dt changes the result: the fixed values are used
+    q4, _, _, _ = O.run_record(c, 25, g, cfl=0.45, dt_fix=dt * 0.5, K_fix=K)
+    assert not np.array_equal(q4, q2)
