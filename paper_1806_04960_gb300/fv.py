@@ -107,6 +107,10 @@ _lib.fv_host_yface.restype = C.c_int
 _lib.fv_adjoint.argtypes = [_H, C.POINTER(fv_adjoint_spec), C.c_void_p, C.c_int,
                             C.POINTER(fv_adjoint_info)]
 _lib.fv_adjoint.restype = C.c_int
+_lib.fv_host_adjoint_step.argtypes = [C.POINTER(fv_grid), C.POINTER(fv_eos), C.POINTER(C.c_int32),
+                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p,
+                                      C.c_void_p, C.c_int]
+_lib.fv_host_adjoint_step.restype = C.c_int
 _lib.fv_host_adj_check.argtypes = [C.c_int, _D, _D, _D, _D, _D, _D]
 _lib.fv_host_adj_check.restype = C.c_int
 
@@ -115,7 +119,8 @@ ABI_SYMBOLS = ("fv_create", "fv_set_state", "fv_step", "fv_step_timed", "fv_get_
                "fv_get_diag", "fv_destroy", "fv_last_error", "fv_version", "fv_host_xface",
                "fv_host_yface", "fv_host_cell_ops", "fv_host_adj_check", "fv_step_static", "fv_batch_create",
                "fv_batch_set_state", "fv_batch_step", "fv_batch_step_timed", "fv_batch_get_state",
-               "fv_batch_get_diag", "fv_batch_size", "fv_batch_destroy", "fv_adjoint")
+               "fv_batch_get_diag", "fv_batch_size", "fv_batch_destroy", "fv_adjoint",
+               "fv_host_adjoint_step")
 
 
 def _check(st):
