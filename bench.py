@@ -19,6 +19,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -44,10 +45,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--only", choices=("f32", "f64"), default=None,
                     help="time one path only (profiling runs)")
-    ap.add_argument("--workload", choices=("dambreak", "drop"), default="dambreak",
-                    help="drop: the 2048^2 elliptical drop, FP32 vs FP64 semi-axis histories")
+    ap.add_argument("--workload", choices=("dambreak", "drop", "adjoint"), default="dambreak",
+                    help="drop: the 2048^2 elliptical drop, FP32 vs FP64 semi-axis histories; "
+                         "adjoint: the 512x256 gradient workload only")
+    ap.add_argument("--adjoint-steps", type=int, default=2000)
     return ap.parse_args()
 
 
@@ -288,6 +292,65 @@ def measure_e2e(fv, case, prec, steps):
             "d2h_bytes_per_step": (nbytes + 8 * steps) / steps}
 
 
+def measure_adjoint(fv, cases_mod, prec, nsteps, stream_sync):
+    """Config 5: the dam break of config 1 at 512 x 256 (k0 = 4.36e5, CFL 0.45),
+    gauge loss over `nsteps` steps at 16 seeded gauges, gradient with respect to
+    the initial state by fv_adjoint (sqrt(N) checkpoints, one replay of the
+    forward sweep).  The target record is the gauges' initial alpha rho held
+    constant (the cost does not depend on it).  Cost ratio = device time of
+    fv_adjoint (forward sweep + reverse sweep) / device time of fv_step over
+    the same steps."""
+    import numpy as np
+    c = cases_mod.c5(512, 256)
+    g = cases_mod.c5_gauges(c)
+    target = np.repeat(c.q[0].ravel()[g][None, :], nsteps, axis=0)
+    s = fv.Solver(c, prec)
+    s.set_state(c.q)
+    s.step(3, c.cfl)
+    s.set_state(c.q)
+    _, fwd_ms = s.step_timed(nsteps, c.cfl)
+    s.set_state(c.q)
+    s.adjoint(min(nsteps, 20), g, target[:min(nsteps, 20)], cfl=c.cfl)   # warm the path
+    s.set_state(c.q)
+    stream_sync()
+    t0 = time.perf_counter()
+    grad, info, _ = s.adjoint(nsteps, g, target, cfl=c.cfl)
+    wall = time.perf_counter() - t0
+    s.close()
+    adj_ms = info.forward_ms + info.reverse_ms
+    cells = c.nx * c.ny
+    return {"forward_ms": fwd_ms, "adjoint_ms": adj_ms, "ratio": adj_ms / fwd_ms,
+            "adjoint_forward_sweep_ms": info.forward_ms, "adjoint_reverse_sweep_ms": info.reverse_ms,
+            "wall_s": wall, "checkpoints": info.checkpoints,
+            "replayed_steps": info.recomputed_steps,
+            "mcups_forward": cells * nsteps / (fwd_ms * 1e-3) / 1e6,
+            "mcups_gradient": cells * nsteps / (adj_ms * 1e-3) / 1e6,
+            "finite_fraction": float(np.isfinite(grad).mean()), "loss": info.loss}
+
+
+def adjoint_block(fv, cases_mod, na, stream_sync):
+    return {"workload": "adjoint_dambreak_512x256", "steps": na, "cfl": 0.45, "gauges": 16,
+            "checkpoint_every": int(math.ceil(math.sqrt(na))),
+            "f32": measure_adjoint(fv, cases_mod, fv.FV_FP32_DEV, na, stream_sync),
+            "f64": measure_adjoint(fv, cases_mod, fv.FV_FP64, na, stream_sync),
+            "note": "timing of the configured horizon; beyond about step 600 the bed toe of the "
+                    "wave amplifies perturbations, so gradient values there exceed 1e25 (float: "
+                    "overflow); parity is tested on 80-400 steps"}
+
+
+def run_adjoint(args):
+    """--workload adjoint: the gradient workload alone (one JSON line)."""
+    import torch
+    from paper_1806_04960_gb300 import build
+    build.build()
+    from paper_1806_04960_gb300 import cases, fv
+    blk = adjoint_block(fv, cases, max(1, args.adjoint_steps), torch.cuda.synchronize)
+    print(json.dumps({"metric": "adjoint/forward cost ratio", "value": blk["f32"]["ratio"],
+                      "unit": "ratio", "n_gpus": 1, "higher_is_better": False, "dtype": "f32",
+                      "data": "synthetic", "config": {"workload": blk["workload"]},
+                      "adjoint": blk}), flush=True)
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -353,6 +416,9 @@ def run_ours(args):
     batch = None
     if not args.only and not args.no_batch:
         batch = measure_batch(fv, cases, min(steps, 100), warmup, torch.cuda.synchronize, barrier)
+    adjoint = None
+    if not args.only and not args.no_adjoint:
+        adjoint = adjoint_block(fv, cases, args.adjoint_steps, torch.cuda.synchronize)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
@@ -391,6 +457,7 @@ def run_ours(args):
                      "steps": f64["steps"], "dtype": "f64", "roofline": f64["roofline"],
                      "clocks": f64["clocks"]},
             "batch": batch,
+            "adjoint": adjoint,
             "status": {"f32": f32["status"], "f64": f64["status"]},
         }
         print(json.dumps(line), flush=True)
@@ -454,6 +521,9 @@ def main():
     args = parse()
     if args.workload == "drop":
         run_drop(args)
+        return
+    if args.workload == "adjoint" and args.impl == "ours":
+        run_adjoint(args)
         return
     if args.impl == "reference":
         run_reference(args)

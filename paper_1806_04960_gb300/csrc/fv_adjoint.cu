@@ -71,6 +71,15 @@ struct AdjArgs {
   T* slot;                  // NSLOT planes
   T* contrib;               // NCONTRIB planes
   double* lam_out;          // adjoint of Q^{n-1}
+  // loss source of Q^{n-1}, added by the gather (src_dt = 0: none): gauges
+  // sorted by cell (gord), gmark[c] = first position of cell c in that order or -1
+  const int32_t* gmark;
+  const int32_t* gord;
+  const int64_t* gauges;
+  int ng;
+  const double* src_m;      // alpha rho at the gauges after step n-1
+  const double* src_t;      // their targets
+  double src_dt;            // dt of step n-1
 };
 
 template <typename T>
@@ -522,6 +531,12 @@ __host__ __device__ void gather_body(const AdjArgs<T>& A, int i, int j) {
 #pragma unroll
       for (int v = 0; v < 4; ++v) acc[v] += (double)A.contrib[(size_t)(4 * p + v) * N + s];
     }
+  if (A.src_dt != 0.0) {
+    const int k0 = A.gmark[c];
+    if (k0 >= 0)
+      for (int k = k0; k < A.ng && A.gauges[A.gord[k]] == (int64_t)c; ++k)
+        acc[0] += 2.0 * A.src_dt * (A.src_m[A.gord[k]] - A.src_t[A.gord[k]]);
+  }
 #pragma unroll
   for (int v = 0; v < 4; ++v) A.lam_out[v * N + c] = acc[v];
 }
@@ -631,7 +646,8 @@ fv_status run_adjoint(fv_handle* h, const fv_adjoint_spec* spec, double* grad, i
   const Tables tb{h->d_rhoE, h->d_rhoE_f};
   const T* rt = DEV ? (const T*)h->d_rhoE_f : (const T*)h->d_rhoE;
 
-  DevBuf Khist, dthist, gidx, gval, tgt, ckpt, seg, lamA, lamB, rec, slot, contrib, rsc, rcol;
+  DevBuf Khist, dthist, gidx, gval, tgt, ckpt, seg, lamA, lamB, rec, slot, contrib, rsc, rcol,
+      gmark, gord;
   const bool ok =
       Khist.alloc(sizeof(int32_t) * (size_t)nx * (Nst + 1)) &&
       dthist.alloc(sizeof(double) * (Nst + 1)) && gidx.alloc(sizeof(int64_t) * ng) &&
@@ -640,7 +656,8 @@ fv_status run_adjoint(fv_handle* h, const fv_adjoint_spec* spec, double* grad, i
       lamA.alloc(sizeof(double) * 4 * N) && lamB.alloc(sizeof(double) * 4 * N) &&
       rec.alloc(sizeof(T) * NREC * N) && slot.alloc(sizeof(T) * NSLOT * N) &&
       contrib.alloc(sizeof(T) * NCONTRIB * N) && rsc.alloc(sizeof(DevScalars)) &&
-      rcol.alloc(sizeof(unsigned long long) * nx);
+      rcol.alloc(sizeof(unsigned long long) * nx) && gmark.alloc(sizeof(int32_t) * N) &&
+      gord.alloc(sizeof(int32_t) * ng);
   if (!ok) {
     set_last_error("fv_adjoint: device allocation failed");
     return FV_ENOMEM;
@@ -657,6 +674,14 @@ fv_status run_adjoint(fv_handle* h, const fv_adjoint_spec* spec, double* grad, i
   ADJ_CUDA(cudaMemcpyAsync(gidx.p, spec->gauges, sizeof(int64_t) * ng, cudaMemcpyHostToDevice, st));
   ADJ_CUDA(cudaMemcpyAsync(tgt.p, spec->target, sizeof(double) * (size_t)Nst * ng,
                            cudaMemcpyHostToDevice, st));
+  // gauges in cell order (stable), and each gauge cell's first position in it
+  std::vector<int32_t> ord_h(ng), mark_h(N, -1);
+  for (int g = 0; g < ng; ++g) ord_h[g] = g;
+  std::stable_sort(ord_h.begin(), ord_h.end(),
+                   [&](int32_t a, int32_t b) { return spec->gauges[a] < spec->gauges[b]; });
+  for (int k = ng - 1; k >= 0; --k) mark_h[spec->gauges[ord_h[k]]] = k;
+  ADJ_CUDA(cudaMemcpyAsync(gord.p, ord_h.data(), sizeof(int32_t) * ng, cudaMemcpyHostToDevice, st));
+  ADJ_CUDA(cudaMemcpyAsync(gmark.p, mark_h.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, st));
   ADJ_CUDA(cudaMemsetAsync(rsc.p, 0, sizeof(DevScalars), st));
   ADJ_CUDA(cudaMemsetAsync(rcol.p, 0, sizeof(unsigned long long) * nx, st));
   int32_t* Kh = Khist.as<int32_t>();
@@ -725,6 +750,10 @@ fv_status run_adjoint(fv_handle* h, const fv_adjoint_spec* spec, double* grad, i
   A.rec = rec.as<T>();
   A.slot = slot.as<T>();
   A.contrib = contrib.as<T>();
+  A.gmark = gmark.as<int32_t>();
+  A.gord = gord.as<int32_t>();
+  A.gauges = gidx.as<int64_t>();
+  A.ng = ng;
   long long replayed = 0;
   for (int k = nck - 1; k >= 0; --k) {
     const int n0 = k * s, n1 = std::min(Nst, n0 + s);
@@ -739,9 +768,14 @@ fv_status run_adjoint(fv_handle* h, const fv_adjoint_spec* spec, double* grad, i
       ++replayed;
     }
     for (int n = n1; n > n0; --n) {
-      adj_source_kernel<<<1, 1, 0, st>>>(lam, gidx.as<int64_t>(), ng,
-                                         gval.as<double>() + (size_t)(n - 1) * ng,
-                                         tgt.as<double>() + (size_t)(n - 1) * ng, dt_h[n]);
+      if (n == Nst)  // the source of Q^N; later sources are added by the gather
+        adj_source_kernel<<<1, 1, 0, st>>>(lam, gidx.as<int64_t>(), ng,
+                                           gval.as<double>() + (size_t)(n - 1) * ng,
+                                           tgt.as<double>() + (size_t)(n - 1) * ng, dt_h[n]);
+      // the gather of this step adds the source of Q^{n-1} (none for Q^0)
+      A.src_dt = n >= 2 ? dt_h[n - 1] : 0.0;
+      A.src_m = gval.as<double>() + (size_t)(n >= 2 ? n - 2 : 0) * ng;
+      A.src_t = tgt.as<double>() + (size_t)(n >= 2 ? n - 2 : 0) * ng;
       A.dt = (T)dt_h[n];
       A.kc.R.half_dt = T(0.5) * A.dt;
       A.q = state(n - 1);
@@ -815,6 +849,12 @@ void host_reverse_step(const StepParams& p, const int32_t* side, const uint8_t* 
   A.slot = slot.data();
   A.contrib = contrib.data();
   A.lam_out = lam_out;
+  A.gmark = nullptr;
+  A.gord = nullptr;
+  A.gauges = nullptr;
+  A.ng = 0;
+  A.src_m = A.src_t = nullptr;
+  A.src_dt = 0.0;
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < nx; ++i) rec_body<T, DEV>(A, i, j);
   const long long nf = (long long)(nx + 1) * ny + (long long)nx * (ny + 1);

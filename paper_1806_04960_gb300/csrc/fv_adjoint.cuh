@@ -31,7 +31,7 @@ __host__ __device__ __forceinline__ T sgn_frozen(T x) {
 // (the caller formed dq from qm, qp and their equilibrium parts; the dq
 // adjoint is returned separately in ldq).
 template <typename T>
-__host__ __device__ void xface_adj(const T qm[4], const T qp[4], const T dq[4], const Phys<T>& P,
+__host__ __device__ __forceinline__ void xface_adj(const T qm[4], const T qp[4], const T dq[4], const Phys<T>& P,
                                    const T lDm[4], const T lDp[4], T lqm[4], T lqp[4], T ldq[4]) {
   const T s_gl[3] = {T(0.5 - 0.38729833462074168852), T(0.5), T(0.5 + 0.38729833462074168852)};
   const T w_gl[3] = {T(5.0 / 18.0), T(8.0 / 18.0), T(5.0 / 18.0)};
@@ -153,7 +153,7 @@ __host__ __device__ __forceinline__ void sign_A2_adj(T u, T v, const T r[4], con
 
 // Adjoint of yface(qm, qp, dq, dap): adds to lqm, lqp, ldq, ldap.
 template <typename T>
-__host__ __device__ void yface_adj(const T qm[4], const T qp[4], const T dq[4], T dap,
+__host__ __device__ __forceinline__ void yface_adj(const T qm[4], const T qp[4], const T dq[4], T dap,
                                    const Phys<T>& P, const T lDm[4], const T lDp[4], T lqm[4],
                                    T lqp[4], T ldq[4], T& ldap) {
   // forward values
@@ -240,7 +240,7 @@ __host__ __device__ void yface_adj(const T qm[4], const T qp[4], const T dq[4], 
 // fluctuation states, the centre state, the equilibrium masses and the limited
 // alpha slopes.
 template <typename T>
-__host__ __device__ void interior_terms_adj(const T fW[4], const T fE[4], const T fS[4],
+__host__ __device__ __forceinline__ void interior_terms_adj(const T fW[4], const T fE[4], const T fS[4],
                                             const T fN[4], const T base[4], T mEc, T mES, T mEN,
                                             T dax, T day, T dx, T dy, const Phys<T>& P,
                                             const T lIx[4], const T lIy[4], T lfW[4], T lfE[4],
@@ -323,7 +323,7 @@ __host__ __device__ void interior_terms_adj(const T fW[4], const T fE[4], const 
 // active factor (the first candidate attaining the minimum), the order switch
 // and the admissibility fallback are taken as in the forward evaluation.
 template <typename T>
-__host__ __device__ void recon_core_adj(const T Qf[4], const T fWi[4], const T fEi[4],
+__host__ __device__ __forceinline__ void recon_core_adj(const T Qf[4], const T fWi[4], const T fEi[4],
                                         const T fSi[4], const T fNi[4], const T mx[4],
                                         const T mn[4], T aE, T mEc, T mES, T mEN, T rEc,
                                         const Phys<T>& P, const ReconConsts<T>& R,
@@ -465,9 +465,11 @@ __host__ __device__ void recon_core_adj(const T Qf[4], const T fWi[4], const T f
       lgx[c] += psi * lsx[c];
       lgy[c] += psi * lsy[c];
     }
-    // limiter: psi = 1 - ramp (1 - phi) of the active candidate
-    if (act_v >= 0) {
-      const int w = act_v;
+    // limiter: psi = 1 - ramp (1 - phi) of the active candidate (the loop
+    // keeps every array index a compile-time constant)
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      if (w != act_v) continue;
       const T up = mx[w] - Qf[w], dn = mn[w] - Qf[w];
       const T d = act_dir == 0 ? R.half_dx * gx[w] : R.half_dy * gy[w];
       const T ad = tabs(d);
