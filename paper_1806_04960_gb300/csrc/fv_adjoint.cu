@@ -517,20 +517,31 @@ __host__ __device__ void gather_body(const AdjArgs<T>& A, int i, int j) {
     for (int v = 0; v < 4; ++v) A.lam_out[v * N + c] = 0.0;
     return;
   }
+  // every load is issued before any is used (no branch between them); a source
+  // outside the fluid contributes nothing but is read at the cell's own index
+  bool ok[9];
+  size_t src[9];
+#pragma unroll
+  for (int p = 0; p < 9; ++p) {
+    const int di = p % 3 - 1, dj = p / 3 - 1;
+    const int si = i - di, sj = j - dj;
+    ok[p] = fluid_at(A, si, sj);
+    src[p] = ok[p] ? (size_t)sj * A.nx + si : c;
+  }
+  T val[9][4];
+#pragma unroll
+  for (int p = 0; p < 9; ++p)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) val[p][v] = A.contrib[(size_t)(4 * p + v) * N + src[p]];
   double acc[4];
 #pragma unroll
   for (int v = 0; v < 4; ++v) acc[v] = A.lam[v * N + c];
+  // fixed order: dj = -1..1, di = -1..1 (p = (dj+1)*3 + (di+1))
 #pragma unroll
-  for (int dj = -1; dj <= 1; ++dj)
+  for (int p = 0; p < 9; ++p)
+    if (ok[p])
 #pragma unroll
-    for (int di = -1; di <= 1; ++di) {
-      const int si = i - di, sj = j - dj;
-      if (!fluid_at(A, si, sj)) continue;
-      const size_t s = (size_t)sj * A.nx + si;
-      const int p = (dj + 1) * 3 + (di + 1);
-#pragma unroll
-      for (int v = 0; v < 4; ++v) acc[v] += (double)A.contrib[(size_t)(4 * p + v) * N + s];
-    }
+      for (int v = 0; v < 4; ++v) acc[v] += (double)val[p][v];
   if (A.src_dt != 0.0) {
     const int k0 = A.gmark[c];
     if (k0 >= 0)
@@ -600,6 +611,20 @@ struct DevBuf {
   U* as() const { return (U*)p; }
 };
 
+struct OwnedStream {
+  cudaStream_t s = nullptr;
+  ~OwnedStream() {
+    if (s) cudaStreamDestroy(s);
+  }
+};
+
+struct OwnedEvent {
+  cudaEvent_t e = nullptr;
+  ~OwnedEvent() {
+    if (e) cudaEventDestroy(e);
+  }
+};
+
 struct EventPair {
   cudaEvent_t a = nullptr, b = nullptr;
   ~EventPair() {
@@ -641,6 +666,7 @@ fv_status run_adjoint(fv_handle* h, const fv_adjoint_spec* spec, double* grad, i
   const int s = spec->checkpoint_every > 0 ? std::min(spec->checkpoint_every, Nst)
                                            : (int)std::ceil(std::sqrt((double)Nst));
   const int nck = (Nst + s - 1) / s;
+  const size_t segs = (size_t)std::max(1, s - 1);  // replayed states per segment
   cudaStream_t st = h->stream;
   const StepParams p = params_of(h, spec->cfl);
   const Tables tb{h->d_rhoE, h->d_rhoE_f};
@@ -652,7 +678,7 @@ fv_status run_adjoint(fv_handle* h, const fv_adjoint_spec* spec, double* grad, i
       Khist.alloc(sizeof(int32_t) * (size_t)nx * (Nst + 1)) &&
       dthist.alloc(sizeof(double) * (Nst + 1)) && gidx.alloc(sizeof(int64_t) * ng) &&
       gval.alloc(sizeof(double) * (size_t)Nst * ng) && tgt.alloc(sizeof(double) * (size_t)Nst * ng) &&
-      ckpt.alloc(qbytes * nck) && seg.alloc(qbytes * (size_t)std::max(1, s - 1)) &&
+      ckpt.alloc(qbytes * nck) && seg.alloc(qbytes * 2 * segs) &&
       lamA.alloc(sizeof(double) * 4 * N) && lamB.alloc(sizeof(double) * 4 * N) &&
       rec.alloc(sizeof(T) * NREC * N) && slot.alloc(sizeof(T) * NSLOT * N) &&
       contrib.alloc(sizeof(T) * NCONTRIB * N) && rsc.alloc(sizeof(DevScalars)) &&
@@ -687,6 +713,14 @@ fv_status run_adjoint(fv_handle* h, const fv_adjoint_spec* spec, double* grad, i
   int32_t* Kh = Khist.as<int32_t>();
   double* dth = dthist.as<double>();
   EventPair evf, evr;
+  OwnedStream st2;
+  OwnedEvent ev_start, ev_rep[2], ev_rev[2];
+  ADJ_CUDA(cudaStreamCreateWithFlags(&st2.s, cudaStreamNonBlocking));
+  ADJ_CUDA(cudaEventCreateWithFlags(&ev_start.e, cudaEventDisableTiming));
+  for (int k = 0; k < 2; ++k) {
+    ADJ_CUDA(cudaEventCreateWithFlags(&ev_rep[k].e, cudaEventDisableTiming));
+    ADJ_CUDA(cudaEventCreateWithFlags(&ev_rev[k].e, cudaEventDisableTiming));
+  }
   ADJ_CUDA(cudaEventCreate(&evf.a));
   ADJ_CUDA(cudaEventCreate(&evf.b));
   ADJ_CUDA(cudaEventCreate(&evr.a));
@@ -754,18 +788,36 @@ fv_status run_adjoint(fv_handle* h, const fv_adjoint_spec* spec, double* grad, i
   A.gord = gord.as<int32_t>();
   A.gauges = gidx.as<int64_t>();
   A.ng = ng;
+  // Segment k is replayed into seg set k % 2 on the second stream while the
+  // reverse of segment k + 1 runs on the handle's stream.
   long long replayed = 0;
+  auto state = [&](int k, int n) -> T* {  // Q^n of segment k (k s <= n < min(N, k s + s))
+    const int n0 = k * s;
+    if (n == n0) return (T*)(ckpt.as<char>() + qbytes * k);
+    return (T*)(seg.as<char>() + qbytes * ((size_t)(k % 2) * segs + (n - n0 - 1)));
+  };
+  auto replay = [&](int k) {
+    const int n0 = k * s, n1 = std::min(Nst, n0 + s);
+    for (int n = n0 + 1; n < n1; ++n) {
+      adj_set_dt_kernel<<<1, 1, 0, st2.s>>>(rsc.as<DevScalars>(), dt_h[n]);
+      launch_replay_step<T, DEV>(p, state(k, n - 1), state(k, n), h->d_solid,
+                                 Kh + (size_t)(n - 1) * nx, Kh + (size_t)n * nx,
+                                 rcol.as<unsigned long long>(), rsc.as<DevScalars>(), tb, st2.s);
+      ++replayed;
+    }
+  };
+  ADJ_CUDA(cudaEventRecord(ev_start.e, st));
+  ADJ_CUDA(cudaStreamWaitEvent(st2.s, ev_start.e, 0));
+  replay(nck - 1);
+  ADJ_CUDA(cudaEventRecord(ev_rep[(nck - 1) % 2].e, st2.s));
   for (int k = nck - 1; k >= 0; --k) {
     const int n0 = k * s, n1 = std::min(Nst, n0 + s);
-    auto state = [&](int n) -> T* {  // Q^n for n0 <= n < n1
-      return n == n0 ? (T*)(ckpt.as<char>() + qbytes * k) : (T*)(seg.as<char>() + qbytes * (n - n0 - 1));
-    };
-    for (int n = n0 + 1; n < n1; ++n) {
-      adj_set_dt_kernel<<<1, 1, 0, st>>>(rsc.as<DevScalars>(), dt_h[n]);
-      launch_replay_step<T, DEV>(p, state(n - 1), state(n), h->d_solid, Kh + (size_t)(n - 1) * nx,
-                                 Kh + (size_t)n * nx, rcol.as<unsigned long long>(),
-                                 rsc.as<DevScalars>(), tb, st);
-      ++replayed;
+    ADJ_CUDA(cudaStreamWaitEvent(st, ev_rep[k % 2].e, 0));
+    if (k >= 1) {
+      // seg set (k - 1) % 2 was last read by the reverse of segment k + 1
+      if (k + 1 < nck) ADJ_CUDA(cudaStreamWaitEvent(st2.s, ev_rev[(k + 1) % 2].e, 0));
+      replay(k - 1);
+      ADJ_CUDA(cudaEventRecord(ev_rep[(k - 1) % 2].e, st2.s));
     }
     for (int n = n1; n > n0; --n) {
       if (n == Nst)  // the source of Q^N; later sources are added by the gather
@@ -778,7 +830,7 @@ fv_status run_adjoint(fv_handle* h, const fv_adjoint_spec* spec, double* grad, i
       A.src_t = tgt.as<double>() + (size_t)(n >= 2 ? n - 2 : 0) * ng;
       A.dt = (T)dt_h[n];
       A.kc.R.half_dt = T(0.5) * A.dt;
-      A.q = state(n - 1);
+      A.q = state(k, n - 1);
       A.Kref = Kh + (size_t)(n - 1) * nx;
       A.Kcur = Kh + (size_t)n * nx;
       A.lam = lam;
@@ -786,6 +838,7 @@ fv_status run_adjoint(fv_handle* h, const fv_adjoint_spec* spec, double* grad, i
       launch_reverse_step<T, DEV>(A, st);
       std::swap(lam, lam2);
     }
+    ADJ_CUDA(cudaEventRecord(ev_rev[k % 2].e, st));
   }
   ADJ_CUDA(cudaGetLastError());
   ADJ_CUDA(cudaEventRecord(evr.b, st));
