@@ -151,7 +151,7 @@ def recorded_traffic():
     import hashlib
     rec = os.path.join(ROOT, "profiles", "step_kernel_dram.txt")
     srcs = [os.path.join(ROOT, "paper_1806_04960_gb300", "csrc", f)
-            for f in ("fv_kernels.cu", "fv_model.cuh")]
+            for f in ("fv_kernels.cu", "fv_model.cuh", "fv_consts.cuh")]
     if not os.path.exists(rec) or not all(os.path.exists(f) for f in srcs):
         return {}
     h = hashlib.sha256(b"".join(open(f, "rb").read() for f in srcs)).hexdigest()
