@@ -69,7 +69,13 @@
 //           outside diagonal neighbours are left out of the min/max;
 //   R-cfl   dt = CFL / max over fluid cells of (|u|+c)/dx + (|v|+c)/dy;
 //   R-sw    a cell with alpha <= 10 eps gets Psi = 0 and dQ/dt = 0;
-//   R-sign  sign(0) = 0.
+//   R-sign  sign(0) = 0;
+//   R-o1    first-order scheme (Sections 3.2-3.3): face states are cell
+//           averages; a y face joins the cell centres y_j -> y_{j+1} along
+//           Eq. (path) with alpha^E linear in s and rho^E at the height y(s);
+//           b3 = pressure part of R-b3 + g Delta y (printed averages) +
+//           Delta alpha^E p^E(face); walls mirror the cell state at the
+//           cell's height.
 //
 // Parity-pinned by the tests listed next to each C entry point.
 
@@ -741,6 +747,186 @@ int full_step(Ctx& C, double cfl, double* q_out) {
   return advance(C, q_out);
 }
 
+// ---------------------------------------------------------------------------
+// First-order scheme, Sections 3.2 and 3.3 (Eq. (SemidiscreteScheme_2)): the
+// face states are the cell averages, a y face joins the two cell centres
+// y_j -> y_{j+1} along the well-balanced path of Eq. (path), and there is no
+// interior term.  Reading R-o1: the equilibrium part Phi^E(s) has alpha^E
+// linear in s (as at second order) and rho^E evaluated at the height y(s);
+// b3 of a segment A -> B is the fluctuation part of Eq. (b^y_3_final) with the
+// pressure part read as in R-b3 and the gravity part g (y_B - y_A) times the
+// printed averages, plus the alpha^E contact part Delta alpha^E p^E(y_face)
+// of reading R-eq (zero at the level face and for equal alpha^E).  A wall or
+// solid neighbour is the mirror of the cell state at the cell's own height
+// (no gravity across the wall face), as in reading R-wall.
+// ---------------------------------------------------------------------------
+struct O1Node {
+  double q[4];   // full conserved state
+  double f[4];   // fluctuation
+  double aE;     // alpha^E on the path
+  double rhoE;   // rho^E at the node's height
+  double y;      // height above the level y0
+};
+
+O1Node o1_node(const Model& M, const double fa[4], double aEa, const double fb[4], double aEb,
+               double ya, double dy, double s) {
+  O1Node n;
+  n.aE = aEa + s * (aEb - aEa);
+  n.y = ya + s * dy;
+  n.rhoE = M.rho0 * std::exp(-kappa(M) * n.y);
+  for (int v = 0; v < 4; ++v) n.f[v] = fa[v] + s * (fb[v] - fa[v]);
+  n.q[0] = n.aE * n.rhoE + n.f[0];
+  n.q[1] = n.f[1];
+  n.q[2] = n.f[2];
+  n.q[3] = n.aE + n.f[3];
+  return n;
+}
+
+// Primitive fluctuations at a node (reading G24 of the survey): rho^f, alpha^f.
+double o1_rhof(const O1Node& n) { return (n.f[0] - n.rhoE * n.f[3]) / n.q[3]; }
+
+// B_Phi (b - a) on the segment a -> b: (0, 0, b3, b4, 0).
+void o1_bterm(const Model& M, const O1Node& a, const O1Node& b, double vbar, double pE_face,
+              double out[5]) {
+  YNode na, nb;
+  for (int v = 0; v < 4; ++v) {
+    na.q[v] = a.q[v]; na.f[v] = a.f[v];
+    nb.q[v] = b.q[v]; nb.f[v] = b.f[v];
+  }
+  na.aE = a.aE;
+  nb.aE = b.aE;
+  const double pressure_part = ap_fluct(M, nb, b.rhoE) - ap_fluct(M, na, a.rhoE);
+  const double aEbar = 0.5 * (a.aE + b.aE), afbar = 0.5 * (a.f[3] + b.f[3]);
+  const double rEbar = 0.5 * (a.rhoE + b.rhoE), rfbar = 0.5 * (o1_rhof(a) + o1_rhof(b));
+  const double gravity_part = (aEbar * rfbar + afbar * rEbar + afbar * rfbar) * M.g * (b.y - a.y);
+  out[0] = 0.0;
+  out[1] = 0.0;
+  out[2] = pressure_part + gravity_part + (b.aE - a.aE) * pE_face;
+  out[3] = vbar * (b.q[3] - a.q[3]);
+  out[4] = 0.0;
+}
+
+// D-+ of Eq. (FIrstOrderDgeneric_y) between two cell centres: fluctuations fa,
+// fb, volume fractions aEa, aEb, lower centre at height ya above the level,
+// spacing dy; pE_face = p^E at the face between them.
+void dfluct_y_o1(const Model& M, const double fa[4], double aEa, const double fb[4], double aEb,
+                 double ya, double dy, double pE_face, double Dm[4], double Dp[4]) {
+  const double sk[3] = {0.25, 0.75, 0.5};
+  const double wk[3] = {2.0 / 3.0, 2.0 / 3.0, -1.0 / 3.0};
+  const double ek[3] = {0.25, 0.25, 0.5};
+  auto node = [&](double s) { return o1_node(M, fa, aEa, fb, aEb, ya, dy, s); };
+  O1Node n0 = node(0.0), n1 = node(1.0);
+  double g0[5], g1[5], B01[5];
+  flux_g(M, n0.q, g0);
+  flux_g(M, n1.q, g1);
+  double vbar01 = 0.0;
+  for (int k = 0; k < 3; ++k) vbar01 += wk[k] * prim(M, node(sk[k]).q).v;
+  o1_bterm(M, n0, n1, vbar01, pE_face, B01);
+  double V[5] = {0, 0, 0, 0, 0};
+  for (int k = 0; k < 3; ++k) {
+    O1Node na = node(sk[k] - ek[k]), nb = node(sk[k] + ek[k]), nc = node(sk[k]);
+    double ga[5], gb[5], Bab[5], Rk[5], t[5];
+    flux_g(M, na.q, ga);
+    flux_g(M, nb.q, gb);
+    o1_bterm(M, na, nb, prim(M, nc.q).v, pE_face, Bab);
+    for (int v = 0; v < 5; ++v) Rk[v] = gb[v] - ga[v] + Bab[v];
+    sign_A2_apply(M, nc.q, Rk, t);
+    for (int v = 0; v < 5; ++v) V[v] += wk[k] * t[v] / (2.0 * ek[k]);
+  }
+  for (int v = 0; v < 4; ++v) {
+    Dm[v] = 0.5 * (g1[v] - g0[v] + B01[v] - V[v]);
+    Dp[v] = 0.5 * (g1[v] - g0[v] + B01[v] + V[v]);
+  }
+}
+
+// One first-order time step with the levels C.K and the step C.dt.
+int advance_o1(Ctx& C, double* q_out) {
+  const Grid& G = C.G;
+  const Model& M = C.M;
+  const size_t n = (size_t)G.nx * G.ny;
+  auto cell = [&](int i, int j, double q[4]) {
+    for (int v = 0; v < 4; ++v) q[v] = C.Q[v * n + at(G, i, j)];
+  };
+  // fluctuation of cell (i, j) w.r.t. its own equilibrium (alpha^E = alpha_ij,
+  // reading R-eq; column level K_i)
+  auto fluct = [&](int i, int j, double f[4], double& aE) {
+    double q[4];
+    cell(i, j, q);
+    aE = q[3];
+    f[0] = q[0] - aE * rhoE_centre(C, j, C.K[i]);
+    f[1] = q[1];
+    f[2] = q[2];
+    f[3] = 0.0;
+  };
+  int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
+  for (int j = 0; j < G.ny; ++j)
+    for (int i = 0; i < G.nx; ++i) {
+      const size_t c = at(G, i, j);
+      double out[4] = {0, 0, 0, 0};
+      if (is_fluid(C, i, j)) {
+        double qc[4];
+        cell(i, j, qc);
+        double Dx[2][4], Dy[2][4];  // D+ of the west/south face, D- of the east/north face
+        for (int side = 0; side < 2; ++side) {
+          // x face: west (side 0) or east (side 1)
+          const int ii = side == 0 ? i - 1 : i + 1;
+          double qn[4], Dm[4], Dp[4];
+          if (is_fluid(C, ii, j)) {
+            cell(ii, j, qn);
+          } else {
+            const bool outside = ii < 0 || ii >= G.nx;
+            std::memcpy(qn, qc, sizeof qn);
+            if (!(outside && C.sides[side] == 1)) mirror(qn, 1);
+          }
+          if (side == 0) {
+            dfluct_x(M, qn, qc, Dm, Dp);
+            std::memcpy(Dx[0], Dp, sizeof Dp);
+          } else {
+            dfluct_x(M, qc, qn, Dm, Dp);
+            std::memcpy(Dx[1], Dm, sizeof Dm);
+          }
+          // y face: south (side 0) or north (side 1)
+          const int jj = side == 0 ? j - 1 : j + 1;
+          double fc[4], aEc;
+          fluct(i, j, fc, aEc);
+          if (is_fluid(C, i, jj)) {
+            double fn[4], aEn;
+            fluct(i, jj, fn, aEn);
+            const int jl = side == 0 ? jj : j;  // lower cell
+            const double ya = (jl + 0.5 - C.K[i]) * G.dy;
+            const double pE_face = pressure(M, rhoE_face(C, jl + 1, C.K[i]));
+            if (side == 0) {
+              dfluct_y_o1(M, fn, aEn, fc, aEc, ya, G.dy, pE_face, Dm, Dp);
+              std::memcpy(Dy[0], Dp, sizeof Dp);
+            } else {
+              dfluct_y_o1(M, fc, aEc, fn, aEn, ya, G.dy, pE_face, Dm, Dp);
+              std::memcpy(Dy[1], Dm, sizeof Dm);
+            }
+          } else {
+            const bool outside = jj < 0 || jj >= G.ny;
+            double fg[4];
+            std::memcpy(fg, fc, sizeof fg);
+            if (!(outside && C.sides[2 + side] == 1)) mirror(fg, 2);
+            const double rE = rhoE_centre(C, j, C.K[i]);
+            if (side == 0) {
+              dfluct_y(M, fg, aEc, fc, aEc, rE, Dm, Dp);
+              std::memcpy(Dy[0], Dp, sizeof Dp);
+            } else {
+              dfluct_y(M, fc, aEc, fg, aEc, rE, Dm, Dp);
+              std::memcpy(Dy[1], Dm, sizeof Dm);
+            }
+          }
+        }
+        for (int v = 0; v < 4; ++v)
+          out[v] = qc[v] - C.dt / G.dx * (Dx[0][v] + Dx[1][v]) - C.dt / G.dy * (Dy[0][v] + Dy[1][v]);
+        if (!admissible(out)) bad = 1;
+      }
+      for (int v = 0; v < 4; ++v) q_out[v * n + c] = out[v];
+    }
+  return bad ? 2 : 0;
+}
+
 Ctx make_ctx(const int32_t* gi, const double* gd, const double* eos, const int32_t* sides,
              const uint8_t* solid, const double* q) {
   Ctx C;
@@ -826,7 +1012,9 @@ int orc_run(const int32_t* gi, const double* gd, const double* eos, const int32_
   return rc;
 }
 
-// n time steps recording, for each step, its levels (K_hist, nsteps*nx,
+// n time steps of the scheme of the given order (2: Eq. (Scheme) with the
+// reconstruction of Section 3.4; 1: the first-order scheme of Sections 3.2-3.3,
+// reading R-o1) recording, for each step, its levels (K_hist, nsteps*nx,
 // nullable), its dt (dt_hist, nullable) and alpha rho at the gauge cells after
 // it (m_hist, nsteps*ngauges, nullable).  With dt_fix and K_fix (both given),
 // step s uses dt_fix[s] and the levels K_fix[s*nx ..] instead of those of its
@@ -835,9 +1023,11 @@ int orc_run(const int32_t* gi, const double* gd, const double* eos, const int32_
 int orc_run_record(const int32_t* gi, const double* gd, const double* eos, const int32_t* sides,
                    const uint8_t* solid, const double* q_in, double* q_out, int nsteps,
                    double cfl, const double* dt_fix, const int32_t* K_fix, double* dt_hist,
-                   int32_t* K_hist, const int64_t* gauges, int ngauges, double* m_hist) {
+                   int32_t* K_hist, const int64_t* gauges, int ngauges, double* m_hist,
+                   int order) {
   Ctx C = make_ctx(gi, gd, eos, sides, solid, q_in);
   if (!valid(C) || nsteps < 0 || !(cfl > 0.0) || (!dt_fix) != (!K_fix)) return 1;
+  if (order != 1 && order != 2) return 1;
   const size_t n1 = (size_t)C.G.nx * C.G.ny, n4 = 4 * n1;
   for (int g = 0; g < ngauges; ++g)
     if (gauges[g] < 0 || gauges[g] >= (int64_t)n1) return 1;
@@ -854,7 +1044,7 @@ int orc_run_record(const int32_t* gi, const double* gd, const double* eos, const
     if (dt_hist) dt_hist[s] = C.dt;
     if (K_hist)
       for (int i = 0; i < C.G.nx; ++i) K_hist[(size_t)s * C.G.nx + i] = C.K[i];
-    rc = advance(C, b.data());
+    rc = order == 2 ? advance(C, b.data()) : advance_o1(C, b.data());
     a.swap(b);
     if (m_hist)
       for (int g = 0; g < ngauges; ++g) m_hist[(size_t)s * ngauges + g] = a[gauges[g]];
@@ -954,6 +1144,12 @@ void orc_dfluct_x(const double* model, const double qm[4], const double qp[4], d
                   double Dp[4]) {
   Model M{model[0], model[1], model[2], model[3], model[4]};
   dfluct_x(M, qm, qp, Dm, Dp);
+}
+
+void orc_dfluct_y_o1(const double* model, const double fa[4], double aEa, const double fb[4],
+                     double aEb, double ya, double dy, double pE_face, double Dm[4], double Dp[4]) {
+  Model M{model[0], model[1], model[2], model[3], model[4]};
+  dfluct_y_o1(M, fa, aEa, fb, aEb, ya, dy, pE_face, Dm, Dp);
 }
 
 void orc_dfluct_y(const double* model, const double fm[4], double aEm, const double fp[4],

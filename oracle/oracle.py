@@ -52,7 +52,9 @@ def lib():
                                          _D, _D]
             L.orc_step_cells.restype = C.c_int
             L.orc_run_record.argtypes = [_I32, _D, _D, _I32, _U8, _D, _D, C.c_int, C.c_double,
-                                         _D, _I32, _D, _I32, _I64, C.c_int, _D]
+                                         _D, _I32, _D, _I32, _I64, C.c_int, _D, C.c_int]
+            L.orc_dfluct_y_o1.argtypes = [_D, _D, C.c_double, _D, C.c_double, C.c_double,
+                                          C.c_double, C.c_double, _D, _D]
             L.orc_run_record.restype = C.c_int
             L.orc_set_threads.argtypes = [C.c_int]
             L.orc_max_threads.restype = C.c_int
@@ -114,11 +116,13 @@ def run(case, nsteps: int, q=None, cfl: float | None = None):
 
 
 def run_record(case, nsteps: int, gauges, q=None, cfl: float | None = None, dt_fix=None,
-               K_fix=None):
-    """Advance ``nsteps`` steps recording each step's dt, levels and the alpha
-    rho at the flat gauge cells after it.  With ``dt_fix`` (nsteps) and
-    ``K_fix`` (nsteps, nx) the steps use those instead of their own.
-    Returns (q_out, dt (nsteps), K (nsteps, nx), m (nsteps, ngauges))."""
+               K_fix=None, order: int = 2):
+    """Advance ``nsteps`` steps of the scheme of ``order`` (2: Eq. (Scheme);
+    1: the first-order scheme of Sections 3.2-3.3) recording each step's dt,
+    levels and the alpha rho at the flat gauge cells after it.  With
+    ``dt_fix`` (nsteps) and ``K_fix`` (nsteps, nx) the steps use those instead
+    of their own.  Returns (q_out, dt (nsteps), K (nsteps, nx), m (nsteps,
+    ngauges))."""
     L = lib()
     gi, gd, eos, sides, solid = _case_args(case)
     qin = np.ascontiguousarray(case.q if q is None else q, dtype=np.float64)
@@ -136,7 +140,7 @@ def run_record(case, nsteps: int, gauges, q=None, cfl: float | None = None, dt_f
                           _p(qin), _p(qout), int(nsteps), float(case.cfl if cfl is None else cfl),
                           None if dfix is None else _p(dfix),
                           None if kfix is None else _p(kfix, _I32), _p(dts), _p(Ks, _I32),
-                          _p(g, _I64), int(g.size), _p(ms))
+                          _p(g, _I64), int(g.size), _p(ms), int(order))
     if rc == 1:
         raise OracleError("invalid input")
     if rc == 2:
@@ -232,6 +236,15 @@ def dfluct_x(qm, qp, **m):
     Dm, Dp = np.zeros(4), np.zeros(4)
     lib().orc_dfluct_x(_p(_model(**m)), _p(np.ascontiguousarray(qm, dtype=np.float64)),
                        _p(np.ascontiguousarray(qp, dtype=np.float64)), _p(Dm), _p(Dp))
+    return Dm, Dp
+
+
+def dfluct_y_o1(fa, aEa, fb, aEb, ya, dy, pE_face, **m):
+    """First-order y-face fluctuations between two cell centres (reading R-o1)."""
+    Dm, Dp = np.zeros(4), np.zeros(4)
+    lib().orc_dfluct_y_o1(_p(_model(**m)), _p(np.ascontiguousarray(fa, dtype=np.float64)),
+                          float(aEa), _p(np.ascontiguousarray(fb, dtype=np.float64)), float(aEb),
+                          float(ya), float(dy), float(pE_face), _p(Dm), _p(Dp))
     return Dm, Dp
 
 

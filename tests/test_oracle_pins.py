@@ -404,3 +404,123 @@ def test_frozen_replay_reproduces_free_run():
     # a different dt changes the result: the fixed values are used
     q4, _, _, _ = O.run_record(c, 25, g, cfl=0.45, dt_fix=dt * 0.5, K_fix=K)
     assert not np.array_equal(q4, q2)
+
+
+# ---------------------------------------------------------------- first-order scheme (R-o1)
+
+def run_to_o1(c, t_end):
+    q = c.q
+    t = 0.0
+    while t < t_end * (1 - 1e-12):
+        dt, _ = O.dt_levels(c, q)
+        cfl = c.cfl if t + dt <= t_end else c.cfl * (t_end - t) / dt
+        q, dts, _, _ = O.run_record(c, 1, [0], q=q, cfl=cfl, order=1)
+        t += float(dts[0])
+    return q
+
+
+def test_first_order_y_face_reduces_to_second_order_face_at_equal_heights():
+    """With dy = 0 the path joins two states at one height: the first-order
+    face (reading R-o1) is the same-height face of Section 3.3."""
+    rng = np.random.default_rng(21)
+    kap = G * RHO0 / K0
+    for _ in range(8):
+        ya = rng.uniform(-0.5, 0.5)
+        rhoE = RHO0 * math.exp(-kap * ya)
+        pE = K0 * (rhoE / RHO0 - 1.0)
+        aEa, aEb = rng.uniform(0.3, 1.0), rng.uniform(0.3, 1.0)
+        fa = np.array([rng.normal() * 5, rng.normal() * 300, rng.normal() * 300, rng.normal() * 0.02])
+        fb = np.array([rng.normal() * 5, rng.normal() * 300, rng.normal() * 300, rng.normal() * 0.02])
+        a = O.dfluct_y_o1(fa, aEa, fb, aEb, ya, 0.0, pE, rho0=RHO0, k0=K0, g=G)
+        b = O.dfluct_y(fa, aEa, fb, aEb, rhoE, rho0=RHO0, k0=K0, g=G)
+        for x, y in zip(a, b):
+            assert np.allclose(x, y, rtol=1e-13, atol=1e-9)
+
+
+def test_first_order_y_face_is_zero_on_a_rest_profile_across_heights():
+    """Two cell centres of one water-at-rest profile (zero fluctuations,
+    one volume fraction, or the level between them with alpha^E jumping from
+    1 to eps): D+- = 0 exactly, and a fluctuation gives a non-zero face."""
+    kap = G * RHO0 / K0
+    dy = 1.0 / 32
+    z = np.zeros(4)
+    for ya, aEa, aEb in ((-0.4, 1.0, 1.0), (0.3, 1e-3, 1e-3), (-0.5 * dy, 1.0, 1e-3)):
+        pE = K0 * (math.exp(-kap * (ya + 0.5 * dy)) - 1.0)
+        if aEa != aEb:
+            assert pE == 0.0     # the level face
+        Dm, Dp = O.dfluct_y_o1(z, aEa, z, aEb, ya, dy, pE, rho0=RHO0, k0=K0, g=G)
+        assert np.all(Dm == 0.0) and np.all(Dp == 0.0)
+    Dm, Dp = O.dfluct_y_o1(np.array([1.0, 0, 0, 0]), 1.0, z, 1.0, -0.4, dy,
+                           K0 * (math.exp(kap * (0.4 - 0.5 * dy)) - 1.0), rho0=RHO0, k0=K0, g=G)
+    assert np.abs(Dm).max() > 0.0
+
+
+def test_first_order_lakes_stay_at_rest():
+    c = cases.c1_lake()
+    q, _, K, _ = O.run_record(c, 200, [0], order=1)
+    fl = c.solid == 0
+    assert np.all(K[-1] == 32)
+    assert np.abs(q[1]).max() < 1e-12 and np.abs(q[2]).max() < 1e-12
+    assert np.abs(q[0] - c.q[0])[fl].max() < 1e-11 * RHO0
+    assert np.array_equal(q[3], c.q[3])
+    for obstacle in (False, True):
+        lb = cases.lake_box(40, obstacle=obstacle)
+        q, _, _, _ = O.run_record(lb, 100, [0], order=1)
+        assert np.abs(q[1]).max() < 1e-12 and np.abs(q[2]).max() < 1e-12
+
+
+def test_first_order_mass_conserved_and_bounded():
+    c = cases.c1()
+    q, dts, _, _ = O.run_record(c, 200, [0], order=1)
+    fl = c.solid == 0
+    m0 = c.q[0].sum()
+    assert abs(q[0].sum() - m0) <= 1e-13 * m0
+    assert np.all(q[3][fl] > 0) and np.all(q[0][fl] > 0) and np.all(q[3][fl] <= 1.0 + 1e-12)
+    assert dts.sum() > 0.1
+
+
+def test_first_order_mirror_symmetry():
+    c = cases.dambreak(64, 32, x_col=10.0, h_col=1.0, lx=4.0, ly=2.0)
+    X = np.meshgrid(c.xc(), c.yc())[0]
+    q = c.q.copy()
+    liquid = (np.abs(X - 2.0) < 0.5) & (q[3] == 1.0)
+    q[3] = np.where(liquid, 1.0, c.eps)
+    q[0] = np.where(liquid, c.q[0], c.eps * RHO0)
+    c = c.with_state(q)
+    qa, _, _, _ = O.run_record(c, 60, [0], order=1)
+    qb, _, _, _ = O.run_record(cases.mirror_x(c), 60, [0], order=1)
+    mb = qb[:, :, ::-1].copy()
+    mb[1] = -mb[1]
+    for v in range(4):
+        scale = np.abs(qa[v]).max() + 1e-300
+        assert np.abs(qa[v] - mb[v]).max() <= 1e-10 * scale
+
+
+def test_first_order_self_convergence_on_smooth_bump():
+    """Self-convergence of the first-order scheme: the observed rate rises
+    towards 1 with refinement (0.66 at 32/64/128, 0.81 at 64/128/256)."""
+    res = {n: run_to_o1(cases.smooth_bump(n), 0.006) for n in (32, 64, 128, 256)}
+
+    def coarsen(q):
+        return 0.25 * (q[:, 0::2, 0::2] + q[:, 1::2, 0::2] + q[:, 0::2, 1::2] + q[:, 1::2, 1::2])
+
+    e = [np.abs(res[n][0] - coarsen(res[2 * n])[0]).mean() for n in (32, 64, 128)]
+    r1, r2 = math.log2(e[0] / e[1]), math.log2(e[1] / e[2])
+    assert r1 < r2 and 0.75 <= r2 <= 1.3
+
+
+def test_first_order_riemann_problem_converges_and_is_more_diffusive():
+    c_s = math.sqrt(K0 / RHO0)
+    errs = []
+    for n in (100, 200, 400):
+        c = cases.riemann_x(n, rho_l=1010.0, rho_r=1000.0, u_l=0.5, u_r=-0.5)
+        t_end = 0.25 / c_s
+        q = run_to_o1(c, t_end)
+        xi = (c.xc() - 0.5) / t_end
+        rho_ex, _ = isothermal_riemann(1010.0, 0.5, 1000.0, -0.5, c_s, xi)
+        errs.append(np.abs(q[0][1] / q[3][1] - rho_ex).mean())
+        if n == 200:
+            q2 = run_to(c, t_end)
+            assert errs[-1] > np.abs(q2[0][1] / q2[3][1] - rho_ex).mean()
+    assert errs[2] < errs[1] < errs[0]
+    assert math.log2(errs[0] / errs[2]) / 2 > 0.4
