@@ -110,6 +110,15 @@ fv_status fv_set_state(fv_handle* h, const double* q, int on_device);
  * device status is checked (FV_ENONFINITE if a step produced a bad state). */
 fv_status fv_step(fv_handle* h, int32_t n, double cfl, double* t_out);
 
+/* Scheme used by the following fv_step / fv_step_timed calls: 2 (default) =
+ * Eq. (Scheme) with the second-order well-balanced reconstruction of Section
+ * 3.4; 1 = the first-order scheme of Sections 3.2-3.3 (Eq.
+ * (SemidiscreteScheme_2)): cell averages as face states, y faces along the
+ * well-balanced path between the two cell centres, no interior term.  Both
+ * precisions.  fv_adjoint, the batch and fv_step_static are second order
+ * only.  FV_EINVAL for another value. */
+fv_status fv_set_order(fv_handle* h, int32_t order);
+
 /* fv_step plus timing: CUDA events recorded on the handle's stream around
  * every launch of the fused step kernel give *kernel_ms, the summed device
  * time of those launches, and *total_ms, the device time of the whole call

@@ -30,6 +30,15 @@ extern "C" {
 int fv_host_xface(const double* model, const double* qm, const double* qp, double* Dm, double* Dp);
 int fv_host_yface(const double* model, const double* qm, const double* qp, double* Dm, double* Dp);
 
+/* fv_host_yface_o1: D-, D+ of the first-order y face (Sections 3.2-3.3)
+ * between the centre of a lower cell at height ya above the level and an upper
+ * one dy higher: fa, fb = fluctuations (alpha rho - alpha^E rho^E, alpha rho u,
+ * alpha rho v, alpha - alpha^E), aEa, aEb = alpha^E; rho^E and p^E at the
+ * quarter heights as the kernels' tables hold them.  Returns 0, or 1 on a null
+ * pointer. */
+int fv_host_yface_o1(const double* model, const double* fa, double aEa, const double* fb,
+                     double aEb, double ya, double dy, double* Dm, double* Dp);
+
 /* Algorithmic operation count of one cell-update of the kernels (one
  * second-order reconstruction with predictor, one x face, one y face, the
  * interior integral of Eq. (Scheme), the update and the epilogue), obtained by

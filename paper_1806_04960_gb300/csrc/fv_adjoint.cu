@@ -960,6 +960,10 @@ extern "C" fv_status fv_adjoint(fv_handle* h, const fv_adjoint_spec* spec, doubl
     set_last_error("fv_adjoint: no state (call fv_set_state first)");
     return FV_EINVAL;
   }
+  if (h->order != 2) {
+    set_last_error("fv_adjoint: the adjoint is of the second-order scheme (fv_set_order(h, 2))");
+    return FV_EINVAL;
+  }
   if (spec->nsteps < 1 || !(spec->cfl > 0.0) || !(spec->cfl <= 1.0) || spec->ngauges < 1 ||
       !spec->gauges || !spec->target || spec->checkpoint_every < 0) {
     set_last_error("fv_adjoint: need nsteps >= 1, 0 < cfl <= 1, ngauges >= 1, gauges, target, "

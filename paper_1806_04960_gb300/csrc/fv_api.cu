@@ -48,12 +48,36 @@ static void release(fv_handle* h) {
   cudaFree(h->d_sc);
   cudaFree(h->d_rhoE);
   cudaFree(h->d_rhoE_f);
+  cudaFree(h->d_rq);
+  cudaFree(h->d_pq);
+  cudaFree(h->d_rq_f);
+  cudaFree(h->d_pq_f);
   cudaFree(h->d_q[0]);
   cudaFree(h->d_q[1]);
   cudaFree(h->d_stage);
   cudaFree(h->d_partial);
   cudaFree(h->d_mass);
   delete h;
+}
+
+// One step of the handle's scheme from d_q[a] to d_q[b] (no finalize).
+static void launch_one_step(fv_handle* h, const StepParams& p, int a, int b) {
+  Tables tb{h->d_rhoE, h->d_rhoE_f};
+  QuarterTables tq{h->d_rq, h->d_pq, h->d_rq_f, h->d_pq_f};
+  if (h->prec == FV_FP64) {
+    StateF64 s{(const double*)h->d_q[a], (double*)h->d_q[b]};
+    if (h->order == 1)
+      launch_step_o1_f64(p, s, h->d_solid, h->d_Kcur, h->d_colsum, h->d_sc, tb, tq, h->stream);
+    else
+      launch_step_f64(p, s, h->d_solid, h->d_Kcur, h->d_colsum, h->d_sc, tb, h->stream);
+  } else {
+    StateF32 s{(const float*)h->d_q[a], (float*)h->d_q[b]};
+    if (h->order == 1)
+      launch_step_o1_f32(p, s, h->d_solid, h->d_Kref, h->d_Kcur, h->d_colsum, h->d_sc, tb, tq,
+                         h->stream);
+    else
+      launch_step_f32(p, s, h->d_solid, h->d_Kref, h->d_Kcur, h->d_colsum, h->d_sc, tb, h->stream);
+  }
 }
 
 extern "C" {
@@ -104,6 +128,10 @@ fv_status fv_create(const fv_grid* grid, const fv_eos* eos, const fv_bc* bc, fv_
             alloc((void**)&h->d_sc, sizeof(DevScalars)) &&
             alloc((void**)&h->d_rhoE, (4 * (size_t)ny + 1) * sizeof(double)) &&
             alloc((void**)&h->d_rhoE_f, (4 * (size_t)ny + 1) * sizeof(float)) &&
+            alloc((void**)&h->d_rq, (8 * (size_t)ny + 1) * sizeof(double)) &&
+            alloc((void**)&h->d_pq, (8 * (size_t)ny + 1) * sizeof(double)) &&
+            alloc((void**)&h->d_rq_f, (8 * (size_t)ny + 1) * sizeof(float)) &&
+            alloc((void**)&h->d_pq_f, (8 * (size_t)ny + 1) * sizeof(float)) &&
             alloc(&h->d_q[0], 4 * N * elem) && alloc(&h->d_q[1], 4 * N * elem) &&
             alloc((void**)&h->d_partial, h->mass_blocks * sizeof(double)) &&
             alloc((void**)&h->d_mass, sizeof(double));
@@ -125,7 +153,26 @@ fv_status fv_create(const fv_grid* grid, const fv_eos* eos, const fv_bc* bc, fv_
     rt[h2 + 2L * ny] = val;
     rtf[h2 + 2L * ny] = (float)val;
   }
+  // the same at quarter-cell heights, with p^E = k0 (rho^E / rho0 - 1)
+  std::vector<double> rq(8 * (size_t)ny + 1), pq(rq.size());
+  std::vector<float> rqf(rq.size()), pqf(rq.size());
+  for (long q4 = -4L * ny; q4 <= 4L * ny; ++q4) {
+    const double r = eos->rho0 * std::exp(-kappa * (0.25 * (double)q4) * grid->dy);
+    const size_t k = (size_t)(q4 + 4L * ny);
+    rq[k] = r;
+    pq[k] = eos->k0 * (r / eos->rho0 - 1.0);
+    rqf[k] = (float)r;
+    pqf[k] = (float)pq[k];
+  }
   cudaError_t e = cudaMemcpyAsync(h->d_solid, solid.data(), N, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->d_rq, rq.data(), rq.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->d_pq, pq.data(), pq.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->d_rq_f, rqf.data(), rqf.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->d_pq_f, pqf.data(), pqf.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->d_rhoE, rt.data(), rt.size() * sizeof(double), cudaMemcpyHostToDevice,
                         h->stream);
@@ -184,17 +231,10 @@ fv_status fv_step(fv_handle* h, int32_t n, double cfl, double* t_out) {
   if (!h->has_state) return fail(FV_EINVAL, "fv_step: no state (call fv_set_state first)");
   h->cfl = cfl;
   const StepParams p = params_of(h, cfl);
-  Tables tb{h->d_rhoE, h->d_rhoE_f};
   if (n > 0) launch_prepare(cfl, h->d_sc, h->stream);
   for (int32_t k = 0; k < n; ++k) {
     const int a = h->cur, b = 1 - h->cur;
-    if (h->prec == FV_FP64) {
-      StateF64 s{(const double*)h->d_q[a], (double*)h->d_q[b]};
-      launch_step_f64(p, s, h->d_solid, h->d_Kcur, h->d_colsum, h->d_sc, tb, h->stream);
-    } else {
-      StateF32 s{(const float*)h->d_q[a], (float*)h->d_q[b]};
-      launch_step_f32(p, s, h->d_solid, h->d_Kref, h->d_Kcur, h->d_colsum, h->d_sc, tb, h->stream);
-    }
+    launch_one_step(h, p, a, b);
     launch_finalize(p, h->d_Kref, h->d_Kcur, h->d_colsum, h->d_sc, 1, h->stream);
     h->cur = b;
   }
@@ -217,7 +257,6 @@ fv_status fv_step_timed(fv_handle* h, int32_t n, double cfl, double* kernel_ms,
   if (!h->has_state) return fail(FV_EINVAL, "fv_step_timed: no state (call fv_set_state first)");
   h->cfl = cfl;
   const StepParams p = params_of(h, cfl);
-  Tables tb{h->d_rhoE, h->d_rhoE_f};
   std::vector<cudaEvent_t> ev(2 * (size_t)n + 2);
   for (auto& e : ev) FV_CUDA(cudaEventCreate(&e));
   fv_status st = FV_OK;
@@ -226,13 +265,7 @@ fv_status fv_step_timed(fv_handle* h, int32_t n, double cfl, double* kernel_ms,
   for (int32_t k = 0; k < n && err == cudaSuccess; ++k) {
     const int a = h->cur, b = 1 - h->cur;
     err = cudaEventRecord(ev[2 * k], h->stream);
-    if (h->prec == FV_FP64) {
-      StateF64 s{(const double*)h->d_q[a], (double*)h->d_q[b]};
-      launch_step_f64(p, s, h->d_solid, h->d_Kcur, h->d_colsum, h->d_sc, tb, h->stream);
-    } else {
-      StateF32 s{(const float*)h->d_q[a], (float*)h->d_q[b]};
-      launch_step_f32(p, s, h->d_solid, h->d_Kref, h->d_Kcur, h->d_colsum, h->d_sc, tb, h->stream);
-    }
+    launch_one_step(h, p, a, b);
     if (err == cudaSuccess) err = cudaEventRecord(ev[2 * k + 1], h->stream);
     launch_finalize(p, h->d_Kref, h->d_Kcur, h->d_colsum, h->d_sc, 1, h->stream);
     h->cur = b;
@@ -259,6 +292,13 @@ fv_status fv_step_timed(fv_handle* h, int32_t n, double cfl, double* kernel_ms,
   FV_CUDA(cudaMemcpy(&sc, h->d_sc, sizeof(sc), cudaMemcpyDeviceToHost));
   if (sc.status) st = fail(FV_ENONFINITE, "fv_step_timed: a step produced a non-admissible state");
   return st;
+}
+
+fv_status fv_set_order(fv_handle* h, int32_t order) {
+  if (!h) return fail(FV_EINVAL, "fv_set_order: null handle");
+  if (order != 1 && order != 2) return fail(FV_EINVAL, "fv_set_order: order must be 1 or 2");
+  h->order = order;
+  return FV_OK;
 }
 
 fv_status fv_get_state(fv_handle* h, double* q, int on_device) {

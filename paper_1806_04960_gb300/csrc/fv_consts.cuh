@@ -1,6 +1,6 @@
-// Per-precision constants of one step, built on the host from StepParams, and
-// the equilibrium-density table lookup.  Internal header shared by the step
-// and adjoint kernels.
+// Per-precision constants of one step, built on the host from StepParams, the
+// equilibrium-density table lookup and the epilogue every step kernel ends
+// with.  Internal header shared by the step, first-order and adjoint kernels.
 #pragma once
 
 #include <cmath>
@@ -53,6 +53,87 @@ inline KConsts<T> make_consts(const StepParams& p) {
 template <typename T>
 __host__ __device__ __forceinline__ T tab(const T* rt, int h, int ny) {
   return rt[h + 2 * ny];
+}
+
+// Product rounded on its own (never fused into an FMA): a difference of two
+// such products of equal factors is then exactly zero, which keeps equal
+// neighbouring rest states exactly balanced when both products are formed in
+// the same expression.
+template <typename T>
+__device__ __forceinline__ T mul_rn(T a, T b);
+template <>
+__device__ __forceinline__ float mul_rn<float>(float a, float b) {
+  return __fmul_rn(a, b);
+}
+template <>
+__device__ __forceinline__ double mul_rn<double>(double a, double b) {
+  return __dmul_rn(a, b);
+}
+
+// Per-cell epilogue of a step on the new state qn (stored form) with full
+// alpha rho m_full: admissibility, the signal rate of the next dt (reading
+// R-cfl) and the detector weight of Eq. (Free_surf_detector) on the common
+// 2^-32 fixed-point scale.
+template <typename T, bool DEV>
+__device__ __forceinline__ void cell_epilogue(const StepParams& p, const KConsts<T>& kc,
+                                              const T qn[4], T m_full, T& my_rate,
+                                              unsigned long long& my_w, bool& bad) {
+  if (DEV) {
+    // float path: in float; the max is taken in double by the reduction
+    const T r = rcp(m_full);
+    const T u = qn[1] * r, v = qn[2] * r;
+    if (!(m_full > T(0)) || !(qn[3] > T(0)) || !isfinite(u) || !isfinite(v) || !isfinite(qn[3]))
+      bad = true;
+    const T rt_ = (tabs(u) + kc.P.c) * kc.inv_dx + (tabs(v) + kc.P.c) * kc.inv_dy;
+    my_rate = rt_ >= T(0) ? rt_ : T(0);
+    T w = (qn[3] - kc.eps) * kc.inv_1meps;
+    w = w < T(0) ? T(0) : (w > T(1) ? T(1) : w);
+    // 2^-24 resolution in float, placed on the common 2^-32 fixed-point scale
+    my_w = (unsigned long long)__float2uint_rn((float)w * 16777216.0f) << 8;
+  } else {
+    // double path: same expressions as the definition (IEEE division), so dt
+    // and the detected levels are reproducible
+    const double md = (double)m_full, ad = (double)qn[3];
+    const double ud = (double)qn[1] / md, vd = (double)qn[2] / md;
+    if (!(md > 0.0) || !(ad > 0.0) || !isfinite(ud) || !isfinite(vd) || !isfinite(ad)) bad = true;
+    const double rd = (fabs(ud) + p.c) / p.dx + (fabs(vd) + p.c) / p.dy;
+    my_rate = rd >= 0.0 ? (T)rd : T(0);
+    double w = (ad - p.eps) / (1.0 - p.eps);
+    w = w < 0.0 ? 0.0 : (w > 1.0 ? 1.0 : w);
+    my_w = (unsigned long long)__double2ll_rn(w * 4294967296.0);
+  }
+}
+
+// Block part of the epilogue for a CTA of TX x TY threads (called by all of
+// them): the status flag, one 64-bit atomicAdd per column of the tile into the
+// detector's column sums and one atomicMax of the tile's largest rate.  col
+// and wmax are shared scratch of TY x TX and TX*TY/32 entries.
+template <typename T, int TX, int TY>
+__device__ __forceinline__ void block_epilogue(T my_rate, unsigned long long my_w, bool bad,
+                                               bool inside, int gi, unsigned long long (*col)[TX],
+                                               double* wmax, unsigned long long* colsum,
+                                               DevScalars* sc) {
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+  if (bad) atomicOr(&sc->status, 1);
+  col[ty][tx] = my_w;
+  // rate max (in T; one double per warp)
+  T r_t = my_rate;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) r_t = fmax(r_t, __shfl_xor_sync(0xffffffffu, r_t, o));
+  if ((tid & 31) == 0) wmax[tid >> 5] = (double)r_t;
+  __syncthreads();
+  if (ty == 0 && inside) {
+    unsigned long long s = 0;
+#pragma unroll
+    for (int r = 0; r < TY; ++r) s += col[r][tx];
+    if (s) atomicAdd(&colsum[gi], s);
+  }
+  if (tid == 0) {
+    double mrate = 0.0;
+#pragma unroll
+    for (int k = 0; k < TX * TY / 32; ++k) mrate = fmax(mrate, wmax[k]);
+    if (mrate > 0.0) atomicMax(&sc->rate_acc, (unsigned long long)__double_as_longlong(mrate));
+  }
 }
 
 }  // namespace fv

@@ -23,6 +23,11 @@ struct fv_handle {
   fv::DevScalars* d_sc = nullptr;
   double* d_rhoE = nullptr;
   float* d_rhoE_f = nullptr;
+  double* d_rq = nullptr;       // quarter-cell rho^E and p^E (first-order y faces)
+  double* d_pq = nullptr;
+  float* d_rq_f = nullptr;
+  float* d_pq_f = nullptr;
+  int order = 2;                // scheme of fv_step: 2 (Eq. (Scheme)) or 1 (Sections 3.2-3.3)
   void* d_q[2] = {nullptr, nullptr};
   int cur = 0;
   double* d_stage = nullptr;    // FP32 path: double staging buffer

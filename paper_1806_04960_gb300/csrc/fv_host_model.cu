@@ -4,6 +4,7 @@
 #include "fv_adjoint.cuh"
 #include "fv_model.cuh"
 #include "fv_model_host.h"
+#include "fv_order1.cuh"
 
 namespace {
 fv::Phys<double> phys(const double* model) {
@@ -33,6 +34,20 @@ extern "C" int fv_host_yface(const double* model, const double* qm, const double
   const double dq[4] = {qp[0] - qm[0], qp[1] - qm[1], qp[2] - qm[2], qp[3] - qm[3]};
   const fv::Phys<double> P = phys(model);
   fv::yface<double>(qm, qp, dq, P.c2 * (dq[0] - P.rho0 * dq[3]), P, Dm, Dp);
+  return 0;
+}
+
+extern "C" int fv_host_yface_o1(const double* model, const double* fa, double aEa,
+                                const double* fb, double aEb, double ya, double dy, double* Dm,
+                                double* Dp) {
+  if (!model || !fa || !fb || !Dm || !Dp) return 1;
+  const fv::Phys<double> P = phys(model);
+  double rq[5], pq[5];
+  for (int k = 0; k < 5; ++k) {
+    rq[k] = P.rho0 * std::exp(-P.kappa * (ya + 0.25 * k * dy));
+    pq[k] = P.k0 * (rq[k] / P.rho0 - 1.0);
+  }
+  fv::yface_o1<double>(fa, aEa, fb, aEb, rq, pq, dy, P, Dm, Dp);
   return 0;
 }
 

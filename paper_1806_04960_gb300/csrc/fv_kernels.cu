@@ -397,57 +397,14 @@ __device__ __forceinline__ void step_tile(const StepParams& p, const KConsts<T>&
 #pragma unroll
     for (int v = 0; v < 4; ++v) qout[v * N + c] = qn[v];
     // epilogue: admissibility, signal rate, detector weight
-    if (DEV) {
-      // float path: in float; the max is taken in double by the reduction
-      const T r = rcp(m_full);
-      const T u = qn[1] * r, v = qn[2] * r;
-      if (!(m_full > T(0)) || !(qn[3] > T(0)) || !isfinite(u) || !isfinite(v) || !isfinite(qn[3]))
-        bad = true;
-      const T rt_ = (tabs(u) + P.c) * inv_dx + (tabs(v) + P.c) * inv_dy;
-      my_rate = rt_ >= T(0) ? rt_ : T(0);
-      T w = (qn[3] - eps) * inv_1meps;
-      w = w < T(0) ? T(0) : (w > T(1) ? T(1) : w);
-      // 2^-24 resolution in float, placed on the common 2^-32 fixed-point scale
-      my_w = (unsigned long long)__float2uint_rn((float)w * 16777216.0f) << 8;
-    } else {
-      // double path: same expressions as the definition (IEEE division), so dt
-      // and the detected levels are reproducible
-      const double md = (double)m_full, ad = (double)qn[3];
-      const double ud = (double)qn[1] / md, vd = (double)qn[2] / md;
-      if (!(md > 0.0) || !(ad > 0.0) || !isfinite(ud) || !isfinite(vd) || !isfinite(ad)) bad = true;
-      const double rd = (fabs(ud) + p.c) / p.dx + (fabs(vd) + p.c) / p.dy;
-      my_rate = rd >= 0.0 ? (T)rd : T(0);
-      double w = (ad - p.eps) / (1.0 - p.eps);
-      w = w < 0.0 ? 0.0 : (w > 1.0 ? 1.0 : w);
-      my_w = (unsigned long long)__double2ll_rn(w * 4294967296.0);
-    }
+    cell_epilogue<T, DEV>(p, kc, qn, m_full, my_rate, my_w, bad);
   } else if (inside) {
     const size_t c = (size_t)gj_me * nx + gi_me;
 #pragma unroll
     for (int v = 0; v < 4; ++v) qout[v * N + c] = T(0);
     if (flag_me == F_SOLID) my_w = ONE_FIXED;
   }
-  if (bad) atomicOr(&sc->status, 1);
-  // column sums
-  S.col[ty][tx] = my_w;
-  // rate max (in T; one double per warp)
-  T r_t = my_rate;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) r_t = fmax(r_t, __shfl_xor_sync(0xffffffffu, r_t, o));
-  if ((tid & 31) == 0) S.wmax[tid >> 5] = (double)r_t;
-  __syncthreads();
-  if (ty == 0 && inside) {
-    unsigned long long s = 0;
-#pragma unroll
-    for (int r = 0; r < TY; ++r) s += S.col[r][tx];
-    if (s) atomicAdd(&colsum[gi_me], s);
-  }
-  if (tid == 0) {
-    double mrate = 0.0;
-#pragma unroll
-    for (int k = 0; k < NT / 32; ++k) mrate = fmax(mrate, S.wmax[k]);
-    if (mrate > 0.0) atomicMax(&sc->rate_acc, (unsigned long long)__double_as_longlong(mrate));
-  }
+  block_epilogue<T, TX, TY>(my_rate, my_w, bad, inside, gi_me, S.col, S.wmax, colsum, sc);
 }
 
 template <typename T, bool DEV>

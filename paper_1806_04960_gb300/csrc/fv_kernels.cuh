@@ -36,6 +36,16 @@ struct Tables {
   const float* rhoE_f;    // same, rounded to float
 };
 
+// rho^E and p^E = k0 (rho^E / rho0 - 1) at quarter-cell heights: entry
+// q + 4 ny holds the value q dy / 4 above the level, q in [-4 ny, 4 ny]
+// (first-order y faces evaluate the path at s = 0, 1/4, ..., 1).
+struct QuarterTables {
+  const double* rhoE_d;
+  const double* pE_d;
+  const float* rhoE_f;
+  const float* pE_f;
+};
+
 struct StateF64 {
   const double* in;       // 4 planes of nx*ny, full conserved state
   double* out;
@@ -52,6 +62,14 @@ void launch_step_f64(const StepParams& p, const StateF64& s, const uint8_t* soli
 void launch_step_f32(const StepParams& p, const StateF32& s, const uint8_t* solid,
                      const int32_t* Kref, const int32_t* Kcur, unsigned long long* colsum,
                      DevScalars* sc, const Tables& tb, cudaStream_t st);
+// First-order scheme of Sections 3.2-3.3 (csrc/fv_order1.cu).
+void launch_step_o1_f64(const StepParams& p, const StateF64& s, const uint8_t* solid,
+                        const int32_t* Kcur, unsigned long long* colsum, DevScalars* sc,
+                        const Tables& tb, const QuarterTables& tq, cudaStream_t st);
+void launch_step_o1_f32(const StepParams& p, const StateF32& s, const uint8_t* solid,
+                        const int32_t* Kref, const int32_t* Kcur, unsigned long long* colsum,
+                        DevScalars* sc, const Tables& tb, const QuarterTables& tq,
+                        cudaStream_t st);
 void launch_finalize(const StepParams& p, int32_t* Kref, int32_t* Kcur,
                      unsigned long long* colsum, DevScalars* sc, int count_step,
                      cudaStream_t st);

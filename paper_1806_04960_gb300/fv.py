@@ -107,6 +107,11 @@ _lib.fv_host_yface.restype = C.c_int
 _lib.fv_adjoint.argtypes = [_H, C.POINTER(fv_adjoint_spec), C.c_void_p, C.c_int,
                             C.POINTER(fv_adjoint_info)]
 _lib.fv_adjoint.restype = C.c_int
+_lib.fv_set_order.argtypes = [_H, C.c_int32]
+_lib.fv_set_order.restype = C.c_int
+_lib.fv_host_yface_o1.argtypes = [_D, _D, C.c_double, _D, C.c_double, C.c_double, C.c_double,
+                                  _D, _D]
+_lib.fv_host_yface_o1.restype = C.c_int
 _lib.fv_host_adjoint_step.argtypes = [C.POINTER(fv_grid), C.POINTER(fv_eos), C.POINTER(C.c_int32),
                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p,
                                       C.c_void_p, C.c_int]
@@ -120,7 +125,7 @@ ABI_SYMBOLS = ("fv_create", "fv_set_state", "fv_step", "fv_step_timed", "fv_get_
                "fv_host_yface", "fv_host_cell_ops", "fv_host_adj_check", "fv_step_static", "fv_batch_create",
                "fv_batch_set_state", "fv_batch_step", "fv_batch_step_timed", "fv_batch_get_state",
                "fv_batch_get_diag", "fv_batch_size", "fv_batch_destroy", "fv_adjoint",
-               "fv_host_adjoint_step")
+               "fv_host_adjoint_step", "fv_set_order", "fv_host_yface_o1")
 
 
 def _check(st):
@@ -194,6 +199,22 @@ def fv_host_adj_check(which: int, model, k, x, lout=None):
     lin = np.zeros(nin)
     _check(_lib.fv_host_adj_check(which, P(m), P(kk), P(xi), P(lo), P(out), P(lin)) and FV_EINVAL)
     return out, lin
+
+
+def fv_host_yface_o1(fa, aEa, fb, aEb, ya, dy, model):
+    """Host evaluation of the kernels' first-order y face (D-, D+)."""
+    m = np.ascontiguousarray(model, dtype=np.float64)
+    a = np.ascontiguousarray(fa, dtype=np.float64)
+    b = np.ascontiguousarray(fb, dtype=np.float64)
+    Dm, Dp = np.zeros(4), np.zeros(4)
+    P = lambda x: x.ctypes.data_as(_D)
+    _check(_lib.fv_host_yface_o1(P(m), P(a), float(aEa), P(b), float(aEb), float(ya), float(dy),
+                                 P(Dm), P(Dp)) and FV_EINVAL)
+    return Dm, Dp
+
+
+def fv_set_order(h, order: int) -> None:
+    _check(_lib.fv_set_order(h, int(order)))
 
 
 def fv_host_cell_ops() -> dict:
@@ -300,6 +321,10 @@ class Solver:
         if isinstance(q, np.ndarray):
             q = np.ascontiguousarray(q, dtype=np.float64)
         fv_set_state(self.h, q)
+
+    def set_order(self, order: int) -> None:
+        """Scheme of the following steps: 2 (default) or 1 (fv_set_order)."""
+        fv_set_order(self.h, order)
 
     def step(self, n: int, cfl: float | None = None, want_time: bool = False):
         return fv_step(self.h, n, self.case.cfl if cfl is None else cfl, want_time)

@@ -9,6 +9,8 @@ the finite difference sees one smooth piece; each branch of the
 reconstruction (limiter active, limiter ramp, order switch, first-order
 fallback) is exercised and identified from the outputs.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -218,3 +220,26 @@ def test_host_reverse_sweep_matches_oracle_differences():
     for v, tol in ((0, 1e-5), (1, 1e-5), (2, 1e-5), (3, 1e-3)):
         a, b = sweeps[fv.FV_FP32_DEV][v], sweeps[fv.FV_FP64][v]
         assert np.sum(np.abs(a - b)) / np.sum(np.abs(b)) < tol, v
+
+
+def test_host_first_order_y_face_matches_oracle():
+    """The kernels' first-order y face (yface_o1, host instantiation) against
+    the oracle's (reading R-o1): random fluctuations, volume fractions,
+    heights, including the level face."""
+    from oracle import oracle as O
+    rng = np.random.default_rng(31)
+    kap = MODEL[3] * MODEL[0] / MODEL[1]
+    for k in range(12):
+        dy = 1.0 / 32
+        ya = -0.5 * dy if k == 0 else rng.uniform(-0.6, 0.6)
+        aEa, aEb = (1.0, 1e-3) if k == 0 else (rng.uniform(0.2, 1.0), rng.uniform(0.2, 1.0))
+        fa = np.array([rng.normal() * 5, rng.normal() * 300, rng.normal() * 300, 0.0])
+        fb = np.array([rng.normal() * 5, rng.normal() * 300, rng.normal() * 300, 0.0])
+        if k % 3 == 1:
+            fa[3], fb[3] = rng.normal() * 0.01, rng.normal() * 0.01
+        pE_face = MODEL[1] * (math.exp(-kap * (ya + 0.5 * dy)) - 1.0)
+        got = fv.fv_host_yface_o1(fa, aEa, fb, aEb, ya, dy, MODEL)
+        ref = O.dfluct_y_o1(fa, aEa, fb, aEb, ya, dy, pE_face, rho0=MODEL[0], k0=MODEL[1],
+                            g=MODEL[3])
+        for a, b in zip(got, ref):
+            assert np.allclose(a, b, rtol=1e-11, atol=1e-9 * np.abs(b).max()), (k, a, b)
