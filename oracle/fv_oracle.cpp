@@ -75,7 +75,10 @@
 //           Eq. (path) with alpha^E linear in s and rho^E at the height y(s);
 //           b3 = pressure part of R-b3 + g Delta y (printed averages) +
 //           Delta alpha^E p^E(face); walls mirror the cell state at the
-//           cell's height.
+//           cell's height;
+//   R-orx   the conservative Osher-Romberg x faces (Eq. (OR_cons)) complete
+//           each sub-segment's flux difference with b4x = u(Psi(s_k)) Delta
+//           alpha and use the Romberg average of u for the face's b4x.
 //
 // Parity-pinned by the tests listed next to each C entry point.
 
@@ -238,6 +241,14 @@ void sign_A2_apply(const Model& M, const double q[4], const double x[5], double 
   apply_eig(R, d, Ri, x, out);
 }
 
+// sign(A1(q)) x = R1 sign(Lambda1) R1^-1 x.
+void sign_A1_apply(const Model& M, const double q[4], const double x[5], double out[5]) {
+  double R[5][5], Ri[5][5], L[5], d[5];
+  eigen_x(M, q, R, L, Ri);
+  for (int k = 0; k < 5; ++k) d[k] = sgn(L[k]);
+  apply_eig(R, d, Ri, x, out);
+}
+
 // ---------------------------------------------------------------------------
 // x direction: path-conservative Osher scheme, Section 3.2.
 // ---------------------------------------------------------------------------
@@ -259,6 +270,46 @@ void dfluct_x(const Model& M, const double qm[4], const double qp[4], double Dm[
     ubar += w_gl[k] * prim(M, phi).u;
   }
   double B[5] = {0.0, 0.0, 0.0, ubar * dq[3], 0.0};
+  for (int v = 0; v < 4; ++v) {
+    Dm[v] = 0.5 * (fp[v] - fm[v] + B[v] - V[v]);
+    Dp[v] = 0.5 * (fp[v] - fm[v] + B[v] + V[v]);
+  }
+}
+
+// x direction with the conservative Osher-Romberg viscosity of Eq. (OR_cons)
+// (Section 3.1) in place of the Gauss-Legendre quadrature of |A1|: the
+// Romberg nodes and weights of Eq. (RombergWeights) on the segment path, each
+// sub-segment's flux difference completed by its non-conservative term
+// b4x = u(Psi(s_k)) Delta alpha, and the face's own b4x = u_bar Delta alpha
+// with u_bar the Romberg combination of the node velocities (reading R-vel).
+void dfluct_x_or(const Model& M, const double qm[4], const double qp[4], double Dm[4],
+                 double Dp[4]) {
+  const double sk[3] = {0.25, 0.75, 0.5};
+  const double wk[3] = {2.0 / 3.0, 2.0 / 3.0, -1.0 / 3.0};
+  const double ek[3] = {0.25, 0.25, 0.5};
+  const double dq[4] = {qp[0] - qm[0], qp[1] - qm[1], qp[2] - qm[2], qp[3] - qm[3]};
+  auto node = [&](double s, double out[4]) {
+    for (int v = 0; v < 4; ++v) out[v] = qm[v] + s * dq[v];
+  };
+  double fm[5], fp[5];
+  flux_f(M, qm, fm);
+  flux_f(M, qp, fp);
+  double ubar = 0.0, V[5] = {0, 0, 0, 0, 0};
+  for (int k = 0; k < 3; ++k) {
+    double na[4], nb[4], nc[4], fa[5], fb[5], Rk[5], t[5];
+    node(sk[k] - ek[k], na);
+    node(sk[k] + ek[k], nb);
+    node(sk[k], nc);
+    flux_f(M, na, fa);
+    flux_f(M, nb, fb);
+    const double uc = prim(M, nc).u;
+    ubar += wk[k] * uc;
+    for (int v = 0; v < 5; ++v) Rk[v] = fb[v] - fa[v];
+    Rk[3] += uc * (nb[3] - na[3]);
+    sign_A1_apply(M, nc, Rk, t);
+    for (int v = 0; v < 5; ++v) V[v] += wk[k] * t[v] / (2.0 * ek[k]);
+  }
+  const double B[5] = {0.0, 0.0, 0.0, ubar * dq[3], 0.0};
   for (int v = 0; v < 4; ++v) {
     Dm[v] = 0.5 * (fp[v] - fm[v] + B[v] - V[v]);
     Dp[v] = 0.5 * (fp[v] - fm[v] + B[v] + V[v]);
@@ -358,6 +409,8 @@ struct Ctx {
   const double* Q;           // 4 planes
   std::vector<int32_t> K;    // detected level per column
   double dt;
+  int xsolver = 0;           // x faces: 0 Gauss-Legendre Osher (Eq. (OsherMatrixFormal_approx)),
+                             // 1 conservative Osher-Romberg (Eq. (OR_cons))
 };
 
 inline size_t at(const Grid& G, int i, int j) { return (size_t)j * G.nx + i; }
@@ -609,7 +662,8 @@ void xface(const Ctx& C, const Rec* L, const Rec* R, int iface, double Dm[4], do
     const bool transmissive = iface == 0 && C.sides[0] == 1;
     if (!transmissive) mirror(qm, 1);
   }
-  dfluct_x(C.M, qm, qp, Dm, Dp);
+  if (C.xsolver == 1) dfluct_x_or(C.M, qm, qp, Dm, Dp);
+  else dfluct_x(C.M, qm, qp, Dm, Dp);
 }
 
 // y face between cells (i, jface-1) and (i, jface).
@@ -879,11 +933,15 @@ int advance_o1(Ctx& C, double* q_out) {
             std::memcpy(qn, qc, sizeof qn);
             if (!(outside && C.sides[side] == 1)) mirror(qn, 1);
           }
+          auto xsolve = [&](const double* a, const double* b) {
+            if (C.xsolver == 1) dfluct_x_or(M, a, b, Dm, Dp);
+            else dfluct_x(M, a, b, Dm, Dp);
+          };
           if (side == 0) {
-            dfluct_x(M, qn, qc, Dm, Dp);
+            xsolve(qn, qc);
             std::memcpy(Dx[0], Dp, sizeof Dp);
           } else {
-            dfluct_x(M, qc, qn, Dm, Dp);
+            xsolve(qc, qn);
             std::memcpy(Dx[1], Dm, sizeof Dm);
           }
           // y face: south (side 0) or north (side 1)
@@ -1012,9 +1070,10 @@ int orc_run(const int32_t* gi, const double* gd, const double* eos, const int32_
   return rc;
 }
 
-// n time steps of the scheme of the given order (2: Eq. (Scheme) with the
-// reconstruction of Section 3.4; 1: the first-order scheme of Sections 3.2-3.3,
-// reading R-o1) recording, for each step, its levels (K_hist, nsteps*nx,
+// n time steps of the scheme (bits 0-3: order 2 = Eq. (Scheme) with the
+// reconstruction of Section 3.4, order 1 = the first-order scheme of Sections
+// 3.2-3.3, reading R-o1; bit 4: x faces by the conservative Osher-Romberg
+// viscosity of Eq. (OR_cons) instead of Gauss-Legendre) recording, for each step, its levels (K_hist, nsteps*nx,
 // nullable), its dt (dt_hist, nullable) and alpha rho at the gauge cells after
 // it (m_hist, nsteps*ngauges, nullable).  With dt_fix and K_fix (both given),
 // step s uses dt_fix[s] and the levels K_fix[s*nx ..] instead of those of its
@@ -1024,10 +1083,12 @@ int orc_run_record(const int32_t* gi, const double* gd, const double* eos, const
                    const uint8_t* solid, const double* q_in, double* q_out, int nsteps,
                    double cfl, const double* dt_fix, const int32_t* K_fix, double* dt_hist,
                    int32_t* K_hist, const int64_t* gauges, int ngauges, double* m_hist,
-                   int order) {
+                   int scheme) {
   Ctx C = make_ctx(gi, gd, eos, sides, solid, q_in);
   if (!valid(C) || nsteps < 0 || !(cfl > 0.0) || (!dt_fix) != (!K_fix)) return 1;
-  if (order != 1 && order != 2) return 1;
+  const int order = scheme & 15;
+  C.xsolver = (scheme >> 4) & 1;
+  if ((order != 1 && order != 2) || (scheme >> 5) != 0) return 1;
   const size_t n1 = (size_t)C.G.nx * C.G.ny, n4 = 4 * n1;
   for (int g = 0; g < ngauges; ++g)
     if (gauges[g] < 0 || gauges[g] >= (int64_t)n1) return 1;
@@ -1144,6 +1205,17 @@ void orc_dfluct_x(const double* model, const double qm[4], const double qp[4], d
                   double Dp[4]) {
   Model M{model[0], model[1], model[2], model[3], model[4]};
   dfluct_x(M, qm, qp, Dm, Dp);
+}
+
+void orc_dfluct_x_or(const double* model, const double qm[4], const double qp[4], double Dm[4],
+                     double Dp[4]) {
+  Model M{model[0], model[1], model[2], model[3], model[4]};
+  dfluct_x_or(M, qm, qp, Dm, Dp);
+}
+
+void orc_sign_A1_apply(const double* model, const double q[4], const double x[5], double out[5]) {
+  Model M{model[0], model[1], model[2], model[3], model[4]};
+  sign_A1_apply(M, q, x, out);
 }
 
 void orc_dfluct_y_o1(const double* model, const double fa[4], double aEa, const double fb[4],

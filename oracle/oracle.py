@@ -53,6 +53,8 @@ def lib():
             L.orc_step_cells.restype = C.c_int
             L.orc_run_record.argtypes = [_I32, _D, _D, _I32, _U8, _D, _D, C.c_int, C.c_double,
                                          _D, _I32, _D, _I32, _I64, C.c_int, _D, C.c_int]
+            L.orc_dfluct_x_or.argtypes = [_D, _D, _D, _D, _D]
+            L.orc_sign_A1_apply.argtypes = [_D, _D, _D, _D]
             L.orc_dfluct_y_o1.argtypes = [_D, _D, C.c_double, _D, C.c_double, C.c_double,
                                           C.c_double, C.c_double, _D, _D]
             L.orc_run_record.restype = C.c_int
@@ -116,9 +118,11 @@ def run(case, nsteps: int, q=None, cfl: float | None = None):
 
 
 def run_record(case, nsteps: int, gauges, q=None, cfl: float | None = None, dt_fix=None,
-               K_fix=None, order: int = 2):
+               K_fix=None, order: int = 2, xsolver: int = 0):
     """Advance ``nsteps`` steps of the scheme of ``order`` (2: Eq. (Scheme);
-    1: the first-order scheme of Sections 3.2-3.3) recording each step's dt,
+    1: the first-order scheme of Sections 3.2-3.3) with x faces by
+    ``xsolver`` (0: Gauss-Legendre Osher; 1: conservative Osher-Romberg,
+    Eq. (OR_cons)), recording each step's dt,
     levels and the alpha rho at the flat gauge cells after it.  With
     ``dt_fix`` (nsteps) and ``K_fix`` (nsteps, nx) the steps use those instead
     of their own.  Returns (q_out, dt (nsteps), K (nsteps, nx), m (nsteps,
@@ -140,7 +144,7 @@ def run_record(case, nsteps: int, gauges, q=None, cfl: float | None = None, dt_f
                           _p(qin), _p(qout), int(nsteps), float(case.cfl if cfl is None else cfl),
                           None if dfix is None else _p(dfix),
                           None if kfix is None else _p(kfix, _I32), _p(dts), _p(Ks, _I32),
-                          _p(g, _I64), int(g.size), _p(ms), int(order))
+                          _p(g, _I64), int(g.size), _p(ms), int(order) | (int(xsolver) << 4))
     if rc == 1:
         raise OracleError("invalid input")
     if rc == 2:
@@ -237,6 +241,21 @@ def dfluct_x(qm, qp, **m):
     lib().orc_dfluct_x(_p(_model(**m)), _p(np.ascontiguousarray(qm, dtype=np.float64)),
                        _p(np.ascontiguousarray(qp, dtype=np.float64)), _p(Dm), _p(Dp))
     return Dm, Dp
+
+
+def dfluct_x_or(qm, qp, **m):
+    """x-face fluctuations with the conservative Osher-Romberg viscosity."""
+    Dm, Dp = np.zeros(4), np.zeros(4)
+    lib().orc_dfluct_x_or(_p(_model(**m)), _p(np.ascontiguousarray(qm, dtype=np.float64)),
+                          _p(np.ascontiguousarray(qp, dtype=np.float64)), _p(Dm), _p(Dp))
+    return Dm, Dp
+
+
+def sign_A1_apply(q, x, **m):
+    out = np.zeros(5)
+    lib().orc_sign_A1_apply(_p(_model(**m)), _p(np.ascontiguousarray(q, dtype=np.float64)),
+                            _p(np.ascontiguousarray(x, dtype=np.float64)), _p(out))
+    return out
 
 
 def dfluct_y_o1(fa, aEa, fb, aEb, ya, dy, pE_face, **m):

@@ -524,3 +524,69 @@ def test_first_order_riemann_problem_converges_and_is_more_diffusive():
             assert errs[-1] > np.abs(q2[0][1] / q2[3][1] - rho_ex).mean()
     assert errs[2] < errs[1] < errs[0]
     assert math.log2(errs[0] / errs[2]) / 2 > 0.4
+
+
+# ---------------------------------------------------------------- Osher-Romberg x faces (R-orx)
+
+def test_sign_A1_matches_numpy_eig():
+    for q in random_states(10, 17):
+        A1, _ = O.jacobians(q)
+        _, sgnA1 = np_abs_sign(A1)
+        x = np.array([3.0, -1.0, 2.0, 0.01, 0.0])
+        assert np.allclose(O.sign_A1_apply(q, x), sgnA1 @ x, rtol=1e-9, atol=1e-8)
+
+
+@pytest.mark.parametrize("scale", [0.8, 1.25])
+def test_osher_romberg_x_linear_case_equals_abs_matrix(scale):
+    """With A1 constant on the segment (q+ = lambda q-) the flux differences
+    are A1 times the sub-segment jumps, so the Romberg sum of sign(A1) R_k is
+    exactly |A1| dq (Eq. (OR_cons))."""
+    for q in random_states(8, 23):
+        qp = scale * q
+        dq = np.append(qp - q, 0.0)
+        A1, _ = O.jacobians(q)
+        absA, _ = np_abs_sign(A1)
+        Dm, Dp = O.dfluct_x_or(q, qp)
+        assert np.allclose(Dp - Dm, (absA @ dq)[:4], rtol=1e-9, atol=1e-7)
+        assert np.allclose(Dp + Dm, (A1 @ dq)[:4], rtol=1e-9, atol=1e-7)
+
+
+def test_osher_romberg_x_equal_states_and_flux_identity():
+    rng = np.random.default_rng(5)
+    for q in random_states(6, 29):
+        Dm, Dp = O.dfluct_x_or(q, q)
+        assert np.all(Dm == 0.0) and np.all(Dp == 0.0)
+        qp = q * (1.0 + 0.05 * rng.standard_normal(4))
+        fm, _ = O.flux(q)
+        fp, _ = O.flux(qp)
+        Dm, Dp = O.dfluct_x_or(q, qp)
+        # D+ + D- = f(q+) - f(q-) + (0, 0, 0, u_bar Delta alpha)
+        assert np.allclose((Dp + Dm)[:3], (fp - fm)[:3], rtol=1e-12, atol=1e-9)
+
+
+def test_osher_romberg_x_lake_mass_and_riemann():
+    c = cases.c1_lake()
+    q, _, _, _ = O.run_record(c, 100, [0], xsolver=1)
+    fl = c.solid == 0
+    assert np.abs(q[1]).max() < 1e-12 and np.abs(q[2]).max() < 1e-12
+    assert np.abs(q[0] - c.q[0])[fl].max() < 1e-11 * RHO0
+    c = cases.c1()
+    q, _, _, _ = O.run_record(c, 200, [0], cfl=0.45, xsolver=1)
+    m0 = c.q[0].sum()
+    assert abs(q[0].sum() - m0) <= 1e-13 * m0
+    c_s = math.sqrt(K0 / RHO0)
+    errs = []
+    for n in (100, 200, 400):
+        cr = cases.riemann_x(n, rho_l=1010.0, rho_r=1000.0, u_l=0.5, u_r=-0.5)
+        t_end = 0.25 / c_s
+        qq = cr.q
+        t = 0.0
+        while t < t_end * (1 - 1e-12):
+            dt, _ = O.dt_levels(cr, qq)
+            cfl = cr.cfl if t + dt <= t_end else cr.cfl * (t_end - t) / dt
+            qq, dts, _, _ = O.run_record(cr, 1, [0], q=qq, cfl=cfl, xsolver=1)
+            t += float(dts[0])
+        xi = (cr.xc() - 0.5) / t_end
+        rho_ex, _ = isothermal_riemann(1010.0, 0.5, 1000.0, -0.5, c_s, xi)
+        errs.append(np.abs(qq[0][1] / qq[3][1] - rho_ex).mean())
+    assert errs[2] < errs[1] < errs[0] and errs[2] < 0.3
