@@ -119,6 +119,17 @@ fv_status fv_step(fv_handle* h, int32_t n, double cfl, double* t_out);
  * only.  FV_EINVAL for another value. */
 fv_status fv_set_order(fv_handle* h, int32_t order);
 
+/* x-face viscosity used by the following fv_step / fv_step_timed calls:
+ * FV_XFACE_GL (default) = the Osher viscosity with 3-point Gauss-Legendre
+ * quadrature of |A1| (Eq. (OsherMatrixFormal_approx)); FV_XFACE_OR = the
+ * conservative Osher-Romberg viscosity of Section 3.1 (Eq. (OR_cons)) with the
+ * Romberg nodes of Eq. (RombergWeights), b4x = u Delta alpha on each
+ * sub-segment.  Both orders and precisions; fv_adjoint, the batch and
+ * fv_step_static use Gauss-Legendre.  FV_EINVAL for another value. */
+#define FV_XFACE_GL 0
+#define FV_XFACE_OR 1
+fv_status fv_set_xface(fv_handle* h, int32_t solver);
+
 /* fv_step plus timing: CUDA events recorded on the handle's stream around
  * every launch of the fused step kernel give *kernel_ms, the summed device
  * time of those launches, and *total_ms, the device time of the whole call

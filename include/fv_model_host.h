@@ -29,6 +29,12 @@ extern "C" {
 
 int fv_host_xface(const double* model, const double* qm, const double* qp, double* Dm, double* Dp);
 int fv_host_yface(const double* model, const double* qm, const double* qp, double* Dm, double* Dp);
+/* fv_host_xface_or: D-, D+ at an x face with the conservative Osher-Romberg
+ * viscosity of Eq. (OR_cons) (Romberg nodes on the segment path, b4x = u
+ * Delta alpha on each sub-segment, Romberg average of u on the face);
+ * arguments as fv_host_xface. */
+int fv_host_xface_or(const double* model, const double* qm, const double* qp, double* Dm,
+                     double* Dp);
 
 /* fv_host_yface_o1: D-, D+ of the first-order y face (Sections 3.2-3.3)
  * between the centre of a lower cell at height ya above the level and an upper

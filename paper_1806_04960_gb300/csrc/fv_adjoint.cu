@@ -960,8 +960,9 @@ extern "C" fv_status fv_adjoint(fv_handle* h, const fv_adjoint_spec* spec, doubl
     set_last_error("fv_adjoint: no state (call fv_set_state first)");
     return FV_EINVAL;
   }
-  if (h->order != 2) {
-    set_last_error("fv_adjoint: the adjoint is of the second-order scheme (fv_set_order(h, 2))");
+  if (h->order != 2 || h->xface != FV_XFACE_GL) {
+    set_last_error("fv_adjoint: the adjoint is of the second-order scheme with Gauss-Legendre x "
+                   "faces (fv_set_order(h, 2), fv_set_xface(h, FV_XFACE_GL))");
     return FV_EINVAL;
   }
   if (spec->nsteps < 1 || !(spec->cfl > 0.0) || !(spec->cfl <= 1.0) || spec->ngauges < 1 ||

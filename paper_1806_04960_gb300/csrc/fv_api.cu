@@ -64,19 +64,21 @@ static void release(fv_handle* h) {
 static void launch_one_step(fv_handle* h, const StepParams& p, int a, int b) {
   Tables tb{h->d_rhoE, h->d_rhoE_f};
   QuarterTables tq{h->d_rq, h->d_pq, h->d_rq_f, h->d_pq_f};
+  const bool orx = h->xface == FV_XFACE_OR;
   if (h->prec == FV_FP64) {
     StateF64 s{(const double*)h->d_q[a], (double*)h->d_q[b]};
     if (h->order == 1)
-      launch_step_o1_f64(p, s, h->d_solid, h->d_Kcur, h->d_colsum, h->d_sc, tb, tq, h->stream);
+      launch_step_o1_f64(p, s, h->d_solid, h->d_Kcur, h->d_colsum, h->d_sc, tb, tq, h->stream, orx);
     else
-      launch_step_f64(p, s, h->d_solid, h->d_Kcur, h->d_colsum, h->d_sc, tb, h->stream);
+      launch_step_f64(p, s, h->d_solid, h->d_Kcur, h->d_colsum, h->d_sc, tb, h->stream, orx);
   } else {
     StateF32 s{(const float*)h->d_q[a], (float*)h->d_q[b]};
     if (h->order == 1)
       launch_step_o1_f32(p, s, h->d_solid, h->d_Kref, h->d_Kcur, h->d_colsum, h->d_sc, tb, tq,
-                         h->stream);
+                         h->stream, orx);
     else
-      launch_step_f32(p, s, h->d_solid, h->d_Kref, h->d_Kcur, h->d_colsum, h->d_sc, tb, h->stream);
+      launch_step_f32(p, s, h->d_solid, h->d_Kref, h->d_Kcur, h->d_colsum, h->d_sc, tb, h->stream,
+                      orx);
   }
 }
 
@@ -298,6 +300,14 @@ fv_status fv_set_order(fv_handle* h, int32_t order) {
   if (!h) return fail(FV_EINVAL, "fv_set_order: null handle");
   if (order != 1 && order != 2) return fail(FV_EINVAL, "fv_set_order: order must be 1 or 2");
   h->order = order;
+  return FV_OK;
+}
+
+fv_status fv_set_xface(fv_handle* h, int32_t solver) {
+  if (!h) return fail(FV_EINVAL, "fv_set_xface: null handle");
+  if (solver != FV_XFACE_GL && solver != FV_XFACE_OR)
+    return fail(FV_EINVAL, "fv_set_xface: solver must be FV_XFACE_GL or FV_XFACE_OR");
+  h->xface = solver;
   return FV_OK;
 }
 

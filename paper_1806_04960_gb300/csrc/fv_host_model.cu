@@ -28,6 +28,14 @@ extern "C" int fv_host_xface(const double* model, const double* qm, const double
   return 0;
 }
 
+extern "C" int fv_host_xface_or(const double* model, const double* qm, const double* qp,
+                                double* Dm, double* Dp) {
+  if (!model || !qm || !qp || !Dm || !Dp) return 1;
+  const double dq[4] = {qp[0] - qm[0], qp[1] - qm[1], qp[2] - qm[2], qp[3] - qm[3]};
+  fv::xface_or<double>(qm, qp, dq, phys(model), Dm, Dp);
+  return 0;
+}
+
 extern "C" int fv_host_yface(const double* model, const double* qm, const double* qp, double* Dm,
                              double* Dp) {
   if (!model || !qm || !qp || !Dm || !Dp) return 1;

@@ -66,7 +66,9 @@ struct Smem {
 enum { R_AE = 0, R_MEC = 1, R_MES = 2, R_MEN = 3, R_FW = 4, R_FE = 8, R_FS = 12, R_FN = 16 };
 
 // One tile (bx, by) of one domain; called by the whole CTA.
-template <typename T, bool DEV>
+// XOR: x faces by the conservative Osher-Romberg viscosity of Eq. (OR_cons)
+// instead of the Gauss-Legendre quadrature of Eq. (OsherMatrixFormal_approx).
+template <typename T, bool DEV, bool XOR>
 __device__ __forceinline__ void step_tile(const StepParams& p, const KConsts<T>& kc,
                                           const T* __restrict__ qin, T* __restrict__ qout,
                                           const uint8_t* __restrict__ solid,
@@ -278,7 +280,8 @@ __device__ __forceinline__ void step_tile(const StepParams& p, const KConsts<T>&
           dq[2] = T(0);
           dq[3] = T(0);
         }
-        xface(qm, qp, dq, P, Dm, Dp);
+        if (XOR) xface_or(qm, qp, dq, P, Dm, Dp);
+        else xface(qm, qp, dq, P, Dm, Dp);
       }
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
@@ -407,7 +410,7 @@ __device__ __forceinline__ void step_tile(const StepParams& p, const KConsts<T>&
   block_epilogue<T, TX, TY>(my_rate, my_w, bad, inside, gi_me, S.col, S.wmax, colsum, sc);
 }
 
-template <typename T, bool DEV>
+template <typename T, bool DEV, bool XOR>
 __global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? 2 : 4))
     step_kernel(StepParams p, KConsts<T> kc, const T* __restrict__ qin, T* __restrict__ qout,
                 const uint8_t* __restrict__ solid, const int32_t* __restrict__ Kref,
@@ -416,8 +419,8 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? 2 : 4))
                 const T* __restrict__ rt) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<T>& S = *reinterpret_cast<Smem<T>*>(smem_raw);
-  step_tile<T, DEV>(p, kc, qin, qout, solid, Kref, Kcur, colsum, sc, rhoE_d, rt, blockIdx.x,
-                    blockIdx.y, S);
+  step_tile<T, DEV, XOR>(p, kc, qin, qout, solid, Kref, Kcur, colsum, sc, rhoE_d, rt, blockIdx.x,
+                         blockIdx.y, S);
 }
 
 // Batched step: every tile of every domain of an ensemble, distributed
@@ -447,7 +450,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? 2 : 4))
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int4 td = tiles[t];
     const BatchDomain<T>& d = doms[td.x];
-    step_tile<T, DEV>(d.p, d.kc, d.q[parity], d.q[1 - parity], d.solid, d.Kref, d.Kcur, d.colsum,
+    step_tile<T, DEV, false>(d.p, d.kc, d.q[parity], d.q[1 - parity], d.solid, d.Kref, d.Kcur, d.colsum,
                       d.sc, d.rhoE_d, d.rt, td.y, td.z, S);
     __syncthreads();  // shared memory is reused by the next tile
   }
@@ -630,21 +633,32 @@ int grid_1d(size_t n) {
   return (int)b;
 }
 
-template <typename T, bool DEV>
-void launch_step_t(const StepParams& p, const T* in, T* out, const uint8_t* solid,
-                   const int32_t* Kref, const int32_t* Kcur, unsigned long long* colsum,
-                   DevScalars* sc, const double* rhoE_d, const T* rt, cudaStream_t st) {
+template <typename T, bool DEV, bool XOR>
+void launch_step_xt(const StepParams& p, const T* in, T* out, const uint8_t* solid,
+                    const int32_t* Kref, const int32_t* Kcur, unsigned long long* colsum,
+                    DevScalars* sc, const double* rhoE_d, const T* rt, cudaStream_t st) {
   const size_t smem = sizeof(Smem<T>);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(step_kernel<T, DEV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(step_kernel<T, DEV, XOR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     attr_set = true;
   }
   dim3 block(TX, TY);
   dim3 grid((p.nx + TX - 1) / TX, (p.ny + TY - 1) / TY);
-  step_kernel<T, DEV><<<grid, block, smem, st>>>(p, make_consts<T>(p), in, out, solid, Kref, Kcur,
-                                                  colsum, sc, rhoE_d, rt);
+  step_kernel<T, DEV, XOR><<<grid, block, smem, st>>>(p, make_consts<T>(p), in, out, solid, Kref,
+                                                       Kcur, colsum, sc, rhoE_d, rt);
+}
+
+template <typename T, bool DEV>
+void launch_step_t(const StepParams& p, const T* in, T* out, const uint8_t* solid,
+                   const int32_t* Kref, const int32_t* Kcur, unsigned long long* colsum,
+                   DevScalars* sc, const double* rhoE_d, const T* rt, bool osher_romberg_x,
+                   cudaStream_t st) {
+  if (osher_romberg_x)
+    launch_step_xt<T, DEV, true>(p, in, out, solid, Kref, Kcur, colsum, sc, rhoE_d, rt, st);
+  else
+    launch_step_xt<T, DEV, false>(p, in, out, solid, Kref, Kcur, colsum, sc, rhoE_d, rt, st);
 }
 
 }  // namespace
@@ -733,16 +747,16 @@ void launch_batch_prepare(bool f64, const void* table, int ndom, double cfl, cud
 
 void launch_step_f64(const StepParams& p, const StateF64& s, const uint8_t* solid,
                      const int32_t* Kcur, unsigned long long* colsum, DevScalars* sc,
-                     const Tables& tb, cudaStream_t st) {
+                     const Tables& tb, cudaStream_t st, bool osher_romberg_x) {
   launch_step_t<double, false>(p, s.in, s.out, solid, Kcur, Kcur, colsum, sc, tb.rhoE_d,
-                               tb.rhoE_d, st);
+                               tb.rhoE_d, osher_romberg_x, st);
 }
 
 void launch_step_f32(const StepParams& p, const StateF32& s, const uint8_t* solid,
                      const int32_t* Kref, const int32_t* Kcur, unsigned long long* colsum,
-                     DevScalars* sc, const Tables& tb, cudaStream_t st) {
+                     DevScalars* sc, const Tables& tb, cudaStream_t st, bool osher_romberg_x) {
   launch_step_t<float, true>(p, s.in, s.out, solid, Kref, Kcur, colsum, sc, tb.rhoE_d,
-                             tb.rhoE_f, st);
+                             tb.rhoE_f, osher_romberg_x, st);
 }
 
 void launch_finalize(const StepParams& p, int32_t* Kref, int32_t* Kcur,

@@ -56,20 +56,24 @@ struct StateF32 {
   float* out;             // written relative to Kcur
 };
 
+// osher_romberg_x: x faces by the conservative Osher-Romberg viscosity of Eq.
+// (OR_cons) instead of the Gauss-Legendre Osher of Eq. (OsherMatrixFormal_approx).
 void launch_step_f64(const StepParams& p, const StateF64& s, const uint8_t* solid,
                      const int32_t* Kcur, unsigned long long* colsum, DevScalars* sc,
-                     const Tables& tb, cudaStream_t st);
+                     const Tables& tb, cudaStream_t st, bool osher_romberg_x = false);
 void launch_step_f32(const StepParams& p, const StateF32& s, const uint8_t* solid,
                      const int32_t* Kref, const int32_t* Kcur, unsigned long long* colsum,
-                     DevScalars* sc, const Tables& tb, cudaStream_t st);
+                     DevScalars* sc, const Tables& tb, cudaStream_t st,
+                     bool osher_romberg_x = false);
 // First-order scheme of Sections 3.2-3.3 (csrc/fv_order1.cu).
 void launch_step_o1_f64(const StepParams& p, const StateF64& s, const uint8_t* solid,
                         const int32_t* Kcur, unsigned long long* colsum, DevScalars* sc,
-                        const Tables& tb, const QuarterTables& tq, cudaStream_t st);
+                        const Tables& tb, const QuarterTables& tq, cudaStream_t st,
+                        bool osher_romberg_x = false);
 void launch_step_o1_f32(const StepParams& p, const StateF32& s, const uint8_t* solid,
                         const int32_t* Kref, const int32_t* Kcur, unsigned long long* colsum,
                         DevScalars* sc, const Tables& tb, const QuarterTables& tq,
-                        cudaStream_t st);
+                        cudaStream_t st, bool osher_romberg_x = false);
 void launch_finalize(const StepParams& p, int32_t* Kref, int32_t* Kcur,
                      unsigned long long* colsum, DevScalars* sc, int count_step,
                      cudaStream_t st);

@@ -109,6 +109,93 @@ __host__ __device__ __forceinline__ void xface(const T qm[4], const T qp[4], con
   Dp[3] = T(0.5) * (F3 + V3);
 }
 
+// sign(A1(q)) r = R1 sign(Lambda1) R1^-1 r for r with zero 5th entry: the
+// closed form of |A1| in xface with each |lambda| replaced by sign(lambda).
+template <typename T>
+__host__ __device__ __forceinline__ void sign_A1(T u, T v, const T r[4], const Phys<T>& P,
+                                                 T out[4]) {
+  const T uc = u * P.inv_c;
+  const T w1 = T(0.5) * ((T(1) + uc) * r[0] - r[1] * P.inv_c - P.rho0 * r[3]);
+  const T w5 = T(0.5) * ((T(1) - uc) * r[0] + r[1] * P.inv_c - P.rho0 * r[3]);
+  const T w2 = r[2] - v * (r[0] - P.rho0 * r[3]);
+  const T s1 = sgn(u - P.c), s5 = sgn(u + P.c), s3 = sgn(u);
+  const T a1 = s1 * w1, a5 = s5 * w5;
+  const T Pk = a1 + a5;
+  const T r0 = Pk + s3 * P.rho0 * r[3];
+  out[0] = r0;
+  out[1] = u * r0 + P.c * (a5 - a1);
+  out[2] = v * Pk + s3 * w2;
+  out[3] = s3 * r[3];
+}
+
+// x faces with the conservative Osher-Romberg viscosity of Eq. (OR_cons): the
+// Romberg sum over the segment path of sign(A1(Psi(s_k))) times the flux
+// difference across the sub-segment, completed by b4x = u(Psi(s_k)) Delta
+// alpha; the face's own b4x uses the Romberg average of the node velocities.
+// Arguments as for xface.
+template <typename T>
+__host__ __device__ __forceinline__ void xface_or(const T qm[4], const T qp[4], const T dq[4],
+                                                  const Phys<T>& P, T Dm[4], T Dp[4]) {
+  // nodes s = 0, 1/4, 1/2, 3/4, 1 (interior nodes on the path, exact endpoints)
+  T mu_[5], u_[5], v_[5];
+#pragma unroll
+  for (int k = 1; k < 4; ++k) {
+    const T s = T(0.25 * k);
+    const T m = qm[0] + s * dq[0];
+    mu_[k] = qm[1] + s * dq[1];
+    const Vel<T> w = velocity(m, mu_[k], qm[2] + s * dq[2]);
+    u_[k] = w.u;
+    v_[k] = w.v;
+  }
+  {
+    const Vel<T> a = velocity(qm[0], qm[1], qm[2]);
+    const Vel<T> b = velocity(qp[0], qp[1], qp[2]);
+    mu_[0] = qm[1];
+    u_[0] = a.u;
+    v_[0] = a.v;
+    mu_[4] = qp[1];
+    u_[4] = b.u;
+    v_[4] = b.v;
+  }
+  // f components at nodes 0, 2, 4: (mu, mu u + alpha p, mu v); alpha p is
+  // linear in q, so its jump over a sub-segment of length l is c2 l dr
+  const T f1_0 = mu_[0] * u_[0], f2_0 = mu_[0] * v_[0];
+  const T f1_2 = mu_[2] * u_[2], f2_2 = mu_[2] * v_[2];
+  const T f1_4 = mu_[4] * u_[4], f2_4 = mu_[4] * v_[4];
+  const T dr = dq[0] - P.rho0 * dq[3];
+  T V[4] = {0, 0, 0, 0};
+  {  // [0, 1/2], node 1/4, weight 4/3
+    const T r[4] = {mu_[2] - mu_[0], f1_2 - f1_0 + T(0.5) * P.c2 * dr, f2_2 - f2_0,
+                    T(0.5) * u_[1] * dq[3]};
+    T o[4];
+    sign_A1(u_[1], v_[1], r, P, o);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) V[c] += T(4.0 / 3.0) * o[c];
+  }
+  {  // [1/2, 1], node 3/4, weight 4/3
+    const T r[4] = {mu_[4] - mu_[2], f1_4 - f1_2 + T(0.5) * P.c2 * dr, f2_4 - f2_2,
+                    T(0.5) * u_[3] * dq[3]};
+    T o[4];
+    sign_A1(u_[3], v_[3], r, P, o);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) V[c] += T(4.0 / 3.0) * o[c];
+  }
+  {  // [0, 1], node 1/2, weight -1/3
+    const T r[4] = {dq[1], f1_4 - f1_0 + P.c2 * dr, f2_4 - f2_0, u_[2] * dq[3]};
+    T o[4];
+    sign_A1(u_[2], v_[2], r, P, o);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) V[c] -= T(1.0 / 3.0) * o[c];
+  }
+  const T ubar = T(2.0 / 3.0) * (u_[1] + u_[3]) - T(1.0 / 3.0) * u_[2];
+  const T F[4] = {dq[1], f1_4 - f1_0 + P.c2 * dr, f2_4 - f2_0, ubar * dq[3]};
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    Dm[c] = T(0.5) * (F[c] - V[c]);
+    Dp[c] = T(0.5) * (F[c] + V[c]);
+  }
+}
+
 // sign(A2(q)) r = R2 sign(Lambda2) R2^-1 r for r with zero 5th entry, closed form
 // of the printed eigenstructure; the eigenvalue-0 mode has sign 0.
 template <typename T>

@@ -38,7 +38,7 @@ struct SmemO1 {
   unsigned char flag[WY][WX];
 };
 
-template <typename T, bool DEV>
+template <typename T, bool DEV, bool XOR>
 __global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? 2 : 4))
     step_o1_kernel(StepParams p, KConsts<T> kc, const T* __restrict__ qin, T* __restrict__ qout,
                    const uint8_t* __restrict__ solid, const int32_t* __restrict__ Kref,
@@ -136,7 +136,8 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? 2 : 4))
           dq[2] = T(0);
           dq[3] = T(0);
         }
-        xface(qm, qp, dq, P, Dm, Dp);
+        if (XOR) xface_or(qm, qp, dq, P, Dm, Dp);
+        else xface(qm, qp, dq, P, Dm, Dp);
       }
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
@@ -232,38 +233,50 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? 2 : 4))
   block_epilogue<T, TX, TY>(my_rate, my_w, bad, inside, gi_me, S.col, S.wmax, colsum, sc);
 }
 
-template <typename T, bool DEV>
-void launch_o1_t(const StepParams& p, const T* in, T* out, const uint8_t* solid,
-                 const int32_t* Kref, const int32_t* Kcur, unsigned long long* colsum,
-                 DevScalars* sc, const T* rt, const T* rq, const T* pq, cudaStream_t st) {
+template <typename T, bool DEV, bool XOR>
+void launch_o1_xt(const StepParams& p, const T* in, T* out, const uint8_t* solid,
+                  const int32_t* Kref, const int32_t* Kcur, unsigned long long* colsum,
+                  DevScalars* sc, const T* rt, const T* rq, const T* pq, cudaStream_t st) {
   const size_t smem = sizeof(SmemO1<T>);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(step_o1_kernel<T, DEV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(step_o1_kernel<T, DEV, XOR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     attr_set = true;
   }
   dim3 block(TX, TY);
   dim3 grid((p.nx + TX - 1) / TX, (p.ny + TY - 1) / TY);
-  step_o1_kernel<T, DEV><<<grid, block, smem, st>>>(p, make_consts<T>(p), in, out, solid, Kref,
-                                                     Kcur, colsum, sc, rt, rq, pq);
+  step_o1_kernel<T, DEV, XOR><<<grid, block, smem, st>>>(p, make_consts<T>(p), in, out, solid,
+                                                          Kref, Kcur, colsum, sc, rt, rq, pq);
+}
+
+template <typename T, bool DEV>
+void launch_o1_t(const StepParams& p, const T* in, T* out, const uint8_t* solid,
+                 const int32_t* Kref, const int32_t* Kcur, unsigned long long* colsum,
+                 DevScalars* sc, const T* rt, const T* rq, const T* pq, bool osher_romberg_x,
+                 cudaStream_t st) {
+  if (osher_romberg_x)
+    launch_o1_xt<T, DEV, true>(p, in, out, solid, Kref, Kcur, colsum, sc, rt, rq, pq, st);
+  else
+    launch_o1_xt<T, DEV, false>(p, in, out, solid, Kref, Kcur, colsum, sc, rt, rq, pq, st);
 }
 
 }  // namespace
 
 void launch_step_o1_f64(const StepParams& p, const StateF64& s, const uint8_t* solid,
                         const int32_t* Kcur, unsigned long long* colsum, DevScalars* sc,
-                        const Tables& tb, const QuarterTables& tq, cudaStream_t st) {
+                        const Tables& tb, const QuarterTables& tq, cudaStream_t st,
+                        bool osher_romberg_x) {
   launch_o1_t<double, false>(p, s.in, s.out, solid, Kcur, Kcur, colsum, sc, tb.rhoE_d, tq.rhoE_d,
-                             tq.pE_d, st);
+                             tq.pE_d, osher_romberg_x, st);
 }
 
 void launch_step_o1_f32(const StepParams& p, const StateF32& s, const uint8_t* solid,
                         const int32_t* Kref, const int32_t* Kcur, unsigned long long* colsum,
                         DevScalars* sc, const Tables& tb, const QuarterTables& tq,
-                        cudaStream_t st) {
+                        cudaStream_t st, bool osher_romberg_x) {
   launch_o1_t<float, true>(p, s.in, s.out, solid, Kref, Kcur, colsum, sc, tb.rhoE_f, tq.rhoE_f,
-                           tq.pE_f, st);
+                           tq.pE_f, osher_romberg_x, st);
 }
 
 }  // namespace fv

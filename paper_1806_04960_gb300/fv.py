@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libfv.so")
 FV_OK, FV_EINVAL, FV_ENOMEM, FV_ECUDA, FV_ENONFINITE, FV_ETIMEOUT = range(6)
 FV_FP64, FV_FP32_DEV = 0, 1
 FV_BC_WALL, FV_BC_TRANSMISSIVE = 0, 1
+FV_XFACE_GL, FV_XFACE_OR = 0, 1
 STATUS_NAMES = {0: "FV_OK", 1: "FV_EINVAL", 2: "FV_ENOMEM", 3: "FV_ECUDA",
                 4: "FV_ENONFINITE", 5: "FV_ETIMEOUT"}
 
@@ -83,6 +84,8 @@ for _f in ("fv_create", "fv_set_state", "fv_step", "fv_step_timed", "fv_get_stat
 _lib.fv_host_xface.argtypes = [_D, _D, _D, _D, _D]
 _lib.fv_host_yface.argtypes = [_D, _D, _D, _D, _D]
 _lib.fv_host_xface.restype = C.c_int
+_lib.fv_host_xface_or.argtypes = [_D, _D, _D, _D, _D]
+_lib.fv_host_xface_or.restype = C.c_int
 _lib.fv_host_cell_ops.argtypes = [_D]
 _lib.fv_step_static.argtypes = [C.POINTER(fv_grid), C.POINTER(fv_eos), C.POINTER(C.c_int32),
                                 C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, _D]
@@ -109,6 +112,8 @@ _lib.fv_adjoint.argtypes = [_H, C.POINTER(fv_adjoint_spec), C.c_void_p, C.c_int,
 _lib.fv_adjoint.restype = C.c_int
 _lib.fv_set_order.argtypes = [_H, C.c_int32]
 _lib.fv_set_order.restype = C.c_int
+_lib.fv_set_xface.argtypes = [_H, C.c_int32]
+_lib.fv_set_xface.restype = C.c_int
 _lib.fv_host_yface_o1.argtypes = [_D, _D, C.c_double, _D, C.c_double, C.c_double, C.c_double,
                                   _D, _D]
 _lib.fv_host_yface_o1.restype = C.c_int
@@ -125,7 +130,8 @@ ABI_SYMBOLS = ("fv_create", "fv_set_state", "fv_step", "fv_step_timed", "fv_get_
                "fv_host_yface", "fv_host_cell_ops", "fv_host_adj_check", "fv_step_static", "fv_batch_create",
                "fv_batch_set_state", "fv_batch_step", "fv_batch_step_timed", "fv_batch_get_state",
                "fv_batch_get_diag", "fv_batch_size", "fv_batch_destroy", "fv_adjoint",
-               "fv_host_adjoint_step", "fv_set_order", "fv_host_yface_o1")
+               "fv_host_adjoint_step", "fv_set_order", "fv_host_yface_o1",
+               "fv_host_xface_or", "fv_set_xface")
 
 
 def _check(st):
@@ -173,6 +179,11 @@ def fv_host_xface(qm, qp, model):
     return _host_face(_lib.fv_host_xface, qm, qp, model)
 
 
+def fv_host_xface_or(qm, qp, model):
+    """Host evaluation of the kernels' Osher-Romberg x-face fluctuations."""
+    return _host_face(_lib.fv_host_xface_or, qm, qp, model)
+
+
 def fv_host_yface(qm, qp, model):
     """Host evaluation of the kernels' y-face fluctuations (D-, D+)."""
     return _host_face(_lib.fv_host_yface, qm, qp, model)
@@ -215,6 +226,10 @@ def fv_host_yface_o1(fa, aEa, fb, aEb, ya, dy, model):
 
 def fv_set_order(h, order: int) -> None:
     _check(_lib.fv_set_order(h, int(order)))
+
+
+def fv_set_xface(h, solver: int) -> None:
+    _check(_lib.fv_set_xface(h, int(solver)))
 
 
 def fv_host_cell_ops() -> dict:
@@ -325,6 +340,10 @@ class Solver:
     def set_order(self, order: int) -> None:
         """Scheme of the following steps: 2 (default) or 1 (fv_set_order)."""
         fv_set_order(self.h, order)
+
+    def set_xface(self, solver: int) -> None:
+        """x-face viscosity: FV_XFACE_GL (default) or FV_XFACE_OR (fv_set_xface)."""
+        fv_set_xface(self.h, solver)
 
     def step(self, n: int, cfl: float | None = None, want_time: bool = False):
         return fv_step(self.h, n, self.case.cfl if cfl is None else cfl, want_time)

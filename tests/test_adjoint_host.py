@@ -243,3 +243,16 @@ def test_host_first_order_y_face_matches_oracle():
                             g=MODEL[3])
         for a, b in zip(got, ref):
             assert np.allclose(a, b, rtol=1e-11, atol=1e-9 * np.abs(b).max()), (k, a, b)
+
+
+def test_host_osher_romberg_x_face_matches_oracle():
+    """The kernels' xface_or (host instantiation) against the oracle's
+    conservative Osher-Romberg x face (Eq. (OR_cons), reading R-orx)."""
+    from oracle import oracle as O
+    rng = np.random.default_rng(41)
+    for _ in range(12):
+        qm, qp = face_state(rng), face_state(rng)
+        got = fv.fv_host_xface_or(qm, qp, MODEL)
+        ref = O.dfluct_x_or(qm, qp, rho0=MODEL[0], k0=MODEL[1], g=MODEL[3])
+        for a, b in zip(got, ref):
+            assert np.allclose(a, b, rtol=1e-11, atol=1e-9 * np.abs(b).max())
