@@ -70,6 +70,14 @@ __device__ __forceinline__ double mul_rn<double>(double a, double b) {
   return __dmul_rn(a, b);
 }
 
+// Detected level K = round(column sum) of Eq. (Free_surf_detector) from the
+// 2^-32 fixed-point sum, half away from zero; at most ny (a column of ny cells),
+// so that every table lookup stays in range whatever the state.
+__device__ __forceinline__ int32_t level_of(unsigned long long colsum, int ny) {
+  const unsigned long long k = (colsum + (1ull << 31)) >> 32;
+  return k > (unsigned long long)ny ? ny : (int32_t)k;
+}
+
 // Per-cell epilogue of a step on the new state qn (stored form) with full
 // alpha rho m_full: admissibility, the signal rate of the next dt (reading
 // R-cfl) and the detector weight of Eq. (Free_surf_detector) on the common
@@ -87,7 +95,7 @@ __device__ __forceinline__ void cell_epilogue(const StepParams& p, const KConsts
     const T rt_ = (tabs(u) + kc.P.c) * kc.inv_dx + (tabs(v) + kc.P.c) * kc.inv_dy;
     my_rate = rt_ >= T(0) ? rt_ : T(0);
     T w = (qn[3] - kc.eps) * kc.inv_1meps;
-    w = w < T(0) ? T(0) : (w > T(1) ? T(1) : w);
+    w = w >= T(0) ? (w > T(1) ? T(1) : w) : T(0);  // NaN -> 0 (the status flag reports it)
     // 2^-24 resolution in float, placed on the common 2^-32 fixed-point scale
     my_w = (unsigned long long)__float2uint_rn((float)w * 16777216.0f) << 8;
   } else {
@@ -99,7 +107,7 @@ __device__ __forceinline__ void cell_epilogue(const StepParams& p, const KConsts
     const double rd = (fabs(ud) + p.c) / p.dx + (fabs(vd) + p.c) / p.dy;
     my_rate = rd >= 0.0 ? (T)rd : T(0);
     double w = (ad - p.eps) / (1.0 - p.eps);
-    w = w < 0.0 ? 0.0 : (w > 1.0 ? 1.0 : w);
+    w = w >= 0.0 ? (w > 1.0 ? 1.0 : w) : 0.0;  // NaN -> 0 (the status flag reports it)
     my_w = (unsigned long long)__double2ll_rn(w * 4294967296.0);
   }
 }

@@ -42,28 +42,50 @@ constexpr int TX = 32, TY = 8;
 constexpr int NT = TX * TY;
 constexpr int WX = TX + 4, WY = TY + 4;  // window: tile + 2-cell halo
 constexpr int RX = TX + 2, RY = TY + 2;  // reconstructed cells: tile + 1 ring
-constexpr int NREC = 20;                 // aE, mEc, mES, mEN, fW[4], fE[4], fS[4], fN[4]
 constexpr unsigned char F_FLUID = 0, F_SOLID = 1, F_OUT = 2;
 constexpr unsigned long long ONE_FIXED = 1ull << 32;
+
+
+// Four components of one state as one shared-memory element, so that a state
+// moves with one vector access (LDS.128 / STS.128 in FP32, two in FP64).
+template <typename T>
+struct alignas(4 * sizeof(T)) V4 {
+  T x, y, z, w;
+};
+
+template <typename T>
+__device__ __forceinline__ void unpack(const V4<T>& v, T a[4]) {
+  a[0] = v.x;
+  a[1] = v.y;
+  a[2] = v.z;
+  a[3] = v.w;
+}
+
+template <typename T>
+__device__ __forceinline__ V4<T> pack(const T a[4]) {
+  return V4<T>{a[0], a[1], a[2], a[3]};
+}
 
 template <typename T>
 struct Smem {
   union {
-    T w[4][WY][WX];  // load phase: m (FP64: full; FP32: m^f of own level), mu, mv, a
+    V4<T> w[WY][WX];  // load phase: (m, mu, mv, a); m: FP64 full, FP32 m^f of own level
     struct {
-      T Dx[8][TY][TX + 1];  // face phase: D-[4], D+[4] of x faces
-      T Dy[8][TY + 1][TX];  // y faces
+      V4<T> Dx[2][TY][TX + 1];  // face phase: D-, D+ of x faces
+      V4<T> Dy[2][TY + 1][TX];  // y faces
     } d;
   } u;
-  T rec[NREC][RY][RX];
-  T cen[6][TY][TX];  // base (centre fluctuation at t^{n+1/2}), dax, day
+  V4<T> rs[RY][RX];     // reconstructed cells: (aE, mEc, mES, mEN)
+  V4<T> rf[4][RY][RX];  // their face fluctuation states W, E, S, N at t^{n+1/2}
+  V4<T> base[TY][TX];   // centre fluctuation at t^{n+1/2}
+  T ga[2][TY][TX];      // limited alpha slopes dax, day
   unsigned long long col[TY][TX];
   double wmax[NT / 32];
   int K[WX];
   unsigned char flag[WY][WX];
 };
 
-enum { R_AE = 0, R_MEC = 1, R_MES = 2, R_MEN = 3, R_FW = 4, R_FE = 8, R_FS = 12, R_FN = 16 };
+enum { F_W = 0, F_E = 1, F_S = 2, F_N = 3 };
 
 // One tile (bx, by) of one domain; called by the whole CTA.
 // XOR: x faces by the conservative Osher-Romberg viscosity of Eq. (OR_cons)
@@ -114,10 +136,7 @@ __device__ __forceinline__ void step_tile(const StepParams& p, const KConsts<T>&
           const int Kr = Kref[gi], Kc = Kcur[gi];
           if (Kr != Kc) m += a * (tab(rt, 2 * (gj - Kr) + 1, ny) - tab(rt, 2 * (gj - Kc) + 1, ny));
         }
-        S.u.w[0][wj][wi] = m;
-        S.u.w[1][wj][wi] = qin[N + c];
-        S.u.w[2][wj][wi] = qin[2 * N + c];
-        S.u.w[3][wj][wi] = a;
+        S.u.w[wj][wi] = V4<T>{m, qin[N + c], qin[2 * N + c], a};
       }
     }
   }
@@ -126,16 +145,16 @@ __device__ __forceinline__ void step_tile(const StepParams& p, const KConsts<T>&
     S.K[idx] = (gi >= 0 && gi < nx) ? Kcur[gi] : 0;
   }
   __syncthreads();
+  // rho^E at h half cells above the level (Eq. (BNs_eq3)); levels are at most
+  // ny (level_of), so h stays inside the table
+  auto rE = [&](int h) -> T { return tab(rt, h, ny); };
 
   // Own-cell state for the update, kept in registers.
   const int gi_me = i0 + tx, gj_me = j0 + ty;
   const bool inside = gi_me < nx && gj_me < ny;
   const unsigned char flag_me = S.flag[ty + 2][tx + 2];
   T qold[4] = {0, 0, 0, 0};
-  if (flag_me == F_FLUID) {
-#pragma unroll
-    for (int v = 0; v < 4; ++v) qold[v] = S.u.w[v][ty + 2][tx + 2];
-  }
+  if (flag_me == F_FLUID) unpack(S.u.w[ty + 2][tx + 2], qold);
 
   // ---------------------------------------------------------------- recon
   ReconConsts<T> RC = kc.R;
@@ -146,35 +165,37 @@ __device__ __forceinline__ void step_tile(const StepParams& p, const KConsts<T>&
     if (S.flag[wj][wi] != F_FLUID) continue;
     const int gj = j0 - 1 + ry;
     const int K = S.K[wi];
-    const T aE = S.u.w[3][wj][wi];
-    const T rEc = tab(rt, 2 * (gj - K) + 1, ny);
-    const T rES = tab(rt, 2 * (gj - K), ny);
-    const T rEN = tab(rt, 2 * (gj + 1 - K), ny);
+    const V4<T> wc = S.u.w[wj][wi];
+    const T aE = wc.w;
+    const T rEc = rE(2 * (gj - K) + 1);
+    const T rES = rE(2 * (gj - K));
+    const T rEN = rE(2 * (gj + 1 - K));
     const T mEc = aE * rEc;
     T Qf[4];
-    Qf[0] = DEV ? S.u.w[0][wj][wi] : S.u.w[0][wj][wi] - mEc;
-    Qf[1] = S.u.w[1][wj][wi];
-    Qf[2] = S.u.w[2][wj][wi];
+    Qf[0] = DEV ? wc.x : wc.x - mEc;
+    Qf[1] = wc.y;
+    Qf[2] = wc.z;
     Qf[3] = T(0);
 
     // fluctuation of a neighbour w.r.t. this cell's Q^E; ghost if not fluid
     auto nbf = [&](int dwi, int dwj, T out[4]) -> bool {
       const int ni = wi + dwi, nj = wj + dwj;
       if (S.flag[nj][ni] != F_FLUID) return false;
-      const T an = S.u.w[3][nj][ni];
+      const V4<T> wn = S.u.w[nj][ni];
+      const T an = wn.w;
       const int gjn = gj + dwj;
-      const T rn = tab(rt, 2 * (gjn - K) + 1, ny);
+      const T rn = rE(2 * (gjn - K) + 1);
       if (DEV) {
         const int Kn = S.K[ni];
         T mshift;
         if (Kn == K) mshift = (an - aE) * rn;
-        else mshift = an * tab(rt, 2 * (gjn - Kn) + 1, ny) - aE * rn;
-        out[0] = S.u.w[0][nj][ni] + mshift;
+        else mshift = an * rE(2 * (gjn - Kn) + 1) - aE * rn;
+        out[0] = wn.x + mshift;
       } else {
-        out[0] = S.u.w[0][nj][ni] - aE * rn;
+        out[0] = wn.x - aE * rn;
       }
-      out[1] = S.u.w[1][nj][ni];
-      out[2] = S.u.w[2][nj][ni];
+      out[1] = wn.y;
+      out[2] = wn.z;
       out[3] = an - aE;
       return true;
     };
@@ -213,22 +234,15 @@ __device__ __forceinline__ void step_tile(const StepParams& p, const KConsts<T>&
     const T mES = aE * rES, mEN = aE * rEN;
     T base[4], ga[2];
     recon_core(Qf, fW, fE, fS, fN, mx, mn, aE, mEc, mES, mEN, rEc, P, RC, base, ga);
-    S.rec[R_AE][ry][rx] = aE;
-    S.rec[R_MEC][ry][rx] = mEc;
-    S.rec[R_MES][ry][rx] = mES;
-    S.rec[R_MEN][ry][rx] = mEN;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      S.rec[R_FW + c][ry][rx] = fW[c];
-      S.rec[R_FE + c][ry][rx] = fE[c];
-      S.rec[R_FS + c][ry][rx] = fS[c];
-      S.rec[R_FN + c][ry][rx] = fN[c];
-    }
+    S.rs[ry][rx] = V4<T>{aE, mEc, mES, mEN};
+    S.rf[F_W][ry][rx] = pack(fW);
+    S.rf[F_E][ry][rx] = pack(fE);
+    S.rf[F_S][ry][rx] = pack(fS);
+    S.rf[F_N][ry][rx] = pack(fN);
     if (rx >= 1 && rx <= TX && ry >= 1 && ry <= TY) {
-#pragma unroll
-      for (int c = 0; c < 4; ++c) S.cen[c][ry - 1][rx - 1] = base[c];
-      S.cen[4][ry - 1][rx - 1] = ga[0];
-      S.cen[5][ry - 1][rx - 1] = ga[1];
+      S.base[ry - 1][rx - 1] = pack(base);
+      S.ga[0][ry - 1][rx - 1] = ga[0];
+      S.ga[1][ry - 1][rx - 1] = ga[1];
     }
   }
   __syncthreads();  // window no longer needed: its storage becomes Dx/Dy
@@ -244,14 +258,12 @@ __device__ __forceinline__ void step_tile(const StepParams& p, const KConsts<T>&
       if (L || R) {
         T qm[4], qp[4], dq[4];
         if (L && R) {
-          const T mEL = S.rec[R_MEC][ry][rxL], mER = S.rec[R_MEC][ry][rxR];
-          const T aL = S.rec[R_AE][ry][rxL], aR = S.rec[R_AE][ry][rxR];
+          const V4<T> sL = S.rs[ry][rxL], sR = S.rs[ry][rxR];
+          const T mEL = sL.y, mER = sR.y;
+          const T aL = sL.x, aR = sR.x;
           T fl[4], fr[4];
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            fl[c] = S.rec[R_FE + c][ry][rxL];
-            fr[c] = S.rec[R_FW + c][ry][rxR];
-          }
+          unpack(S.rf[F_E][ry][rxL], fl);
+          unpack(S.rf[F_W][ry][rxR], fr);
           qm[0] = mEL + fl[0]; qm[1] = fl[1]; qm[2] = fl[2]; qm[3] = aL + fl[3];
           qp[0] = mER + fr[0]; qp[1] = fr[1]; qp[2] = fr[2]; qp[3] = aR + fr[3];
           dq[0] = (mER - mEL) + (fr[0] - fl[0]);
@@ -260,13 +272,14 @@ __device__ __forceinline__ void step_tile(const StepParams& p, const KConsts<T>&
           dq[3] = (aR - aL) + (fr[3] - fl[3]);
         } else {
           const int rx = L ? rxL : rxR;
-          const int base_i = L ? R_FE : R_FW;
-          const T mE = S.rec[R_MEC][ry][rx], aE = S.rec[R_AE][ry][rx];
+          const V4<T> sc_ = S.rs[ry][rx];
+          const V4<T> fc = S.rf[L ? F_E : F_W][ry][rx];
+          const T mE = sc_.y, aE = sc_.x;
           T q[4];
-          q[0] = mE + S.rec[base_i][ry][rx];
-          q[1] = S.rec[base_i + 1][ry][rx];
-          q[2] = S.rec[base_i + 2][ry][rx];
-          q[3] = aE + S.rec[base_i + 3][ry][rx];
+          q[0] = mE + fc.x;
+          q[1] = fc.y;
+          q[2] = fc.z;
+          q[3] = aE + fc.w;
           const bool outside = L ? (S.flag[ry + 1][rxR + 1] == F_OUT) : (S.flag[ry + 1][rxL + 1] == F_OUT);
           const bool transmissive = outside && (L ? trE : trW);
           T g[4] = {q[0], transmissive ? q[1] : -q[1], q[2], q[3]};
@@ -283,11 +296,8 @@ __device__ __forceinline__ void step_tile(const StepParams& p, const KConsts<T>&
         if (XOR) xface_or(qm, qp, dq, P, Dm, Dp);
         else xface(qm, qp, dq, P, Dm, Dp);
       }
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        S.u.d.Dx[c][fy][fx] = Dm[c];
-        S.u.d.Dx[4 + c][fy][fx] = Dp[c];
-      }
+      S.u.d.Dx[0][fy][fx] = pack(Dm);
+      S.u.d.Dx[1][fy][fx] = pack(Dp);
     } else {
       const int k = idx - (TX + 1) * TY;
       const int fx = k % TX, fy = k / TX;
@@ -298,14 +308,12 @@ __device__ __forceinline__ void step_tile(const StepParams& p, const KConsts<T>&
         T qm[4], qp[4], dq[4];
         T dap = T(0);
         if (B && Tt) {
-          const T mEB = S.rec[R_MEN][ryB][rx], mET = S.rec[R_MES][ryT][rx];
-          const T aB = S.rec[R_AE][ryB][rx], aT = S.rec[R_AE][ryT][rx];
+          const V4<T> sB = S.rs[ryB][rx], sT = S.rs[ryT][rx];
+          const T mEB = sB.w, mET = sT.z;
+          const T aB = sB.x, aT = sT.x;
           T fb[4], ft[4];
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            fb[c] = S.rec[R_FN + c][ryB][rx];
-            ft[c] = S.rec[R_FS + c][ryT][rx];
-          }
+          unpack(S.rf[F_N][ryB][rx], fb);
+          unpack(S.rf[F_S][ryT][rx], ft);
           qm[0] = mEB + fb[0]; qm[1] = fb[1]; qm[2] = fb[2]; qm[3] = aB + fb[3];
           qp[0] = mET + ft[0]; qp[1] = ft[1]; qp[2] = ft[2]; qp[3] = aT + ft[3];
           dq[0] = (mET - mEB) + (ft[0] - fb[0]);
@@ -315,17 +323,18 @@ __device__ __forceinline__ void step_tile(const StepParams& p, const KConsts<T>&
           // jump of alpha p: equilibrium part (rho^E_f - rho0) Delta alpha^E is
           // exactly zero at the level face; fluctuation part c2 (dm^f - rho0 da^f)
           const int K = S.K[rx + 1];
-          const T rEf = tab(rt, 2 * (j0 - 1 + ryT - K), ny);
+          const T rEf = rE(2 * (j0 - 1 + ryT - K));
           dap = P.c2 * ((rEf - P.rho0) * (aT - aB) + ((ft[0] - fb[0]) - P.rho0 * (ft[3] - fb[3])));
         } else {
           const int ry = B ? ryB : ryT;
-          const int base_i = B ? R_FN : R_FS;
-          const T mE = S.rec[B ? R_MEN : R_MES][ry][rx], aE = S.rec[R_AE][ry][rx];
+          const V4<T> sc_ = S.rs[ry][rx];
+          const V4<T> fc = S.rf[B ? F_N : F_S][ry][rx];
+          const T mE = B ? sc_.w : sc_.z, aE = sc_.x;
           T q[4];
-          q[0] = mE + S.rec[base_i][ry][rx];
-          q[1] = S.rec[base_i + 1][ry][rx];
-          q[2] = S.rec[base_i + 2][ry][rx];
-          q[3] = aE + S.rec[base_i + 3][ry][rx];
+          q[0] = mE + fc.x;
+          q[1] = fc.y;
+          q[2] = fc.z;
+          q[3] = aE + fc.w;
           const bool outside = B ? (S.flag[ryT + 1][rx + 1] == F_OUT) : (S.flag[ryB + 1][rx + 1] == F_OUT);
           const bool transmissive = outside && (B ? trN : trS);
           T g[4] = {q[0], q[1], transmissive ? q[2] : -q[2], q[3]};
@@ -341,11 +350,8 @@ __device__ __forceinline__ void step_tile(const StepParams& p, const KConsts<T>&
         }
         yface(qm, qp, dq, dap, P, Dm, Dp);
       }
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        S.u.d.Dy[c][fy][fx] = Dm[c];
-        S.u.d.Dy[4 + c][fy][fx] = Dp[c];
-      }
+      S.u.d.Dy[0][fy][fx] = pack(Dm);
+      S.u.d.Dy[1][fy][fx] = pack(Dp);
     }
   }
   __syncthreads();
@@ -357,26 +363,27 @@ __device__ __forceinline__ void step_tile(const StepParams& p, const KConsts<T>&
   if (inside && flag_me == F_FLUID) {
     const int rx = tx + 1, ry = ty + 1;
     const int K = S.K[tx + 2];
-    const T aE = S.rec[R_AE][ry][rx];
-    const T mEc = S.rec[R_MEC][ry][rx], mES = S.rec[R_MES][ry][rx], mEN = S.rec[R_MEN][ry][rx];
+    const V4<T> sme = S.rs[ry][rx];
+    const T mEc = sme.y, mES = sme.z, mEN = sme.w;
     T fW[4], fE[4], fS[4], fN[4], base[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      fW[c] = S.rec[R_FW + c][ry][rx];
-      fE[c] = S.rec[R_FE + c][ry][rx];
-      fS[c] = S.rec[R_FS + c][ry][rx];
-      fN[c] = S.rec[R_FN + c][ry][rx];
-      base[c] = S.cen[c][ty][tx];
-    }
-    const T dax = S.cen[4][ty][tx], day = S.cen[5][ty][tx];
+    unpack(S.rf[F_W][ry][rx], fW);
+    unpack(S.rf[F_E][ry][rx], fE);
+    unpack(S.rf[F_S][ry][rx], fS);
+    unpack(S.rf[F_N][ry][rx], fN);
+    unpack(S.base[ty][tx], base);
+    const T dax = S.ga[0][ty][tx], day = S.ga[1][ty][tx];
     T Ix[4], Iy[4];
     interior_terms(fW, fE, fS, fN, base, mEc, mES, mEN, dax, day, dx, dy, P, Ix, Iy);
     const T rdx = dt / dx, rdy = dt / dy;
-    T xs[4], ys[4];
+    T xs[4], ys[4], DpW[4], DmE[4], DpS[4], DmN[4];
+    unpack(S.u.d.Dx[1][ty][tx], DpW);
+    unpack(S.u.d.Dx[0][ty][tx + 1], DmE);
+    unpack(S.u.d.Dy[1][ty][tx], DpS);
+    unpack(S.u.d.Dy[0][ty + 1][tx], DmN);
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      xs[c] = S.u.d.Dx[4 + c][ty][tx] + S.u.d.Dx[c][ty][tx + 1] + Ix[c];
-      ys[c] = S.u.d.Dy[4 + c][ty][tx] + S.u.d.Dy[c][ty + 1][tx] + Iy[c];
+      xs[c] = DpW[c] + DmE[c] + Ix[c];
+      ys[c] = DpS[c] + DmN[c] + Iy[c];
     }
     T qn[4];
     T m_full;
@@ -385,7 +392,7 @@ __device__ __forceinline__ void step_tile(const StepParams& p, const KConsts<T>&
       T dQ[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) dQ[c] = -rdx * xs[c] - rdy * ys[c];
-      const T rEc = tab(rt, 2 * (gj_me - K) + 1, ny);
+      const T rEc = rE(2 * (gj_me - K) + 1);
       qn[0] = qold[0] + (dQ[0] - rEc * dQ[3]);
       qn[1] = qold[1] + dQ[1];
       qn[2] = qold[2] + dQ[2];
@@ -463,7 +470,7 @@ __global__ void batch_finalize_kernel(const BatchDomain<T>* __restrict__ doms, d
   const BatchDomain<T>& d = doms[blockIdx.x];
   for (int i = threadIdx.x; i < d.p.nx; i += blockDim.x) {
     d.Kref[i] = d.Kcur[i];
-    d.Kcur[i] = (int32_t)((d.colsum[i] + (1ull << 31)) >> 32);
+    d.Kcur[i] = level_of(d.colsum[i], d.p.ny);
     d.colsum[i] = 0ull;
   }
   if (threadIdx.x == 0) {
@@ -494,7 +501,7 @@ __global__ void finalize_kernel(StepParams p, int32_t* Kref, int32_t* Kcur,
                                 unsigned long long* colsum, DevScalars* sc, int count_step) {
   for (int i = threadIdx.x; i < p.nx; i += blockDim.x) {
     Kref[i] = Kcur[i];
-    Kcur[i] = (int32_t)((colsum[i] + (1ull << 31)) >> 32);
+    Kcur[i] = level_of(colsum[i], p.ny);
     colsum[i] = 0ull;
   }
   if (threadIdx.x == 0) {
@@ -536,7 +543,7 @@ __global__ void prologue_kernel(StepParams p, const double* __restrict__ q,
     double r = (fabs(u) + p.c) / p.dx + (fabs(v) + p.c) / p.dy;
     if (r >= 0.0) my_rate = fmax(my_rate, r);
     double w = (a - p.eps) / (1.0 - p.eps);
-    w = w < 0.0 ? 0.0 : (w > 1.0 ? 1.0 : w);
+    w = w >= 0.0 ? (w > 1.0 ? 1.0 : w) : 0.0;  // NaN -> 0 (the status flag reports the state)
     const unsigned long long qw = (unsigned long long)__double2ll_rn(w * 4294967296.0);
     if (qw) atomicAdd(&colsum[i], qw);
   }
