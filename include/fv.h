@@ -130,6 +130,19 @@ fv_status fv_set_order(fv_handle* h, int32_t order);
 #define FV_XFACE_OR 1
 fv_status fv_set_xface(fv_handle* h, int32_t solver);
 
+/* Staging of the second-order step kernel used by the following fv_step,
+ * fv_step_timed and fv_adjoint calls.  The arithmetic of a step (Eq. (Scheme))
+ * is the same in every staging and the results are bitwise identical; only
+ * the speed differs.  FV_TILING_TILE = one CTA per 32 x 8 tile of cells;
+ * FV_TILING_STRIP = one CTA per 32-column strip marching upwards in blocks of
+ * 8 rows, sharing the reconstructed rows and y faces between blocks
+ * (faster in both precisions); FV_TILING_AUTO (default) = the strip kernel.
+ * The batch (fv_batch_*) stages by tiles.  FV_EINVAL for another value. */
+#define FV_TILING_AUTO 0
+#define FV_TILING_TILE 1
+#define FV_TILING_STRIP 2
+fv_status fv_set_tiling(fv_handle* h, int32_t tiling);
+
 /* fv_step plus timing: CUDA events recorded on the handle's stream around
  * every launch of the fused step kernel give *kernel_ms, the summed device
  * time of those launches, and *total_ms, the device time of the whole call

@@ -70,7 +70,8 @@ static void launch_one_step(fv_handle* h, const StepParams& p, int a, int b) {
     if (h->order == 1)
       launch_step_o1_f64(p, s, h->d_solid, h->d_Kcur, h->d_colsum, h->d_sc, tb, tq, h->stream, orx);
     else
-      launch_step_f64(p, s, h->d_solid, h->d_Kcur, h->d_colsum, h->d_sc, tb, h->stream, orx);
+      launch_step_f64(p, s, h->d_solid, h->d_Kcur, h->d_colsum, h->d_sc, tb, h->stream, orx,
+                      h->tiling);
   } else {
     StateF32 s{(const float*)h->d_q[a], (float*)h->d_q[b]};
     if (h->order == 1)
@@ -78,7 +79,7 @@ static void launch_one_step(fv_handle* h, const StepParams& p, int a, int b) {
                          h->stream, orx);
     else
       launch_step_f32(p, s, h->d_solid, h->d_Kref, h->d_Kcur, h->d_colsum, h->d_sc, tb, h->stream,
-                      orx);
+                      orx, h->tiling);
   }
 }
 
@@ -308,6 +309,14 @@ fv_status fv_set_xface(fv_handle* h, int32_t solver) {
   if (solver != FV_XFACE_GL && solver != FV_XFACE_OR)
     return fail(FV_EINVAL, "fv_set_xface: solver must be FV_XFACE_GL or FV_XFACE_OR");
   h->xface = solver;
+  return FV_OK;
+}
+
+fv_status fv_set_tiling(fv_handle* h, int32_t tiling) {
+  if (!h) return fail(FV_EINVAL, "fv_set_tiling: null handle");
+  if (tiling != FV_TILING_AUTO && tiling != FV_TILING_TILE && tiling != FV_TILING_STRIP)
+    return fail(FV_EINVAL, "fv_set_tiling: tiling must be FV_TILING_AUTO, _TILE or _STRIP");
+  h->tiling = tiling;
   return FV_OK;
 }
 

@@ -29,6 +29,7 @@ struct fv_handle {
   float* d_pq_f = nullptr;
   int order = 2;                // scheme of fv_step: 2 (Eq. (Scheme)) or 1 (Sections 3.2-3.3)
   int xface = FV_XFACE_GL;      // x-face viscosity (fv_set_xface)
+  int tiling = FV_TILING_AUTO;  // step-kernel staging (fv_set_tiling)
   void* d_q[2] = {nullptr, nullptr};
   int cur = 0;
   double* d_stage = nullptr;    // FP32 path: double staging buffer

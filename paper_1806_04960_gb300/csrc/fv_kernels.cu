@@ -33,38 +33,19 @@
 #include "fv_consts.cuh"
 #include "fv_kernels.cuh"
 #include "fv_model.cuh"
+#include "fv_tile.cuh"
 
 namespace fv {
 
 namespace {
 
+using namespace tile;
+
 constexpr int TX = 32, TY = 8;
 constexpr int NT = TX * TY;
 constexpr int WX = TX + 4, WY = TY + 4;  // window: tile + 2-cell halo
 constexpr int RX = TX + 2, RY = TY + 2;  // reconstructed cells: tile + 1 ring
-constexpr unsigned char F_FLUID = 0, F_SOLID = 1, F_OUT = 2;
-constexpr unsigned long long ONE_FIXED = 1ull << 32;
 
-
-// Four components of one state as one shared-memory element, so that a state
-// moves with one vector access (LDS.128 / STS.128 in FP32, two in FP64).
-template <typename T>
-struct alignas(4 * sizeof(T)) V4 {
-  T x, y, z, w;
-};
-
-template <typename T>
-__device__ __forceinline__ void unpack(const V4<T>& v, T a[4]) {
-  a[0] = v.x;
-  a[1] = v.y;
-  a[2] = v.z;
-  a[3] = v.w;
-}
-
-template <typename T>
-__device__ __forceinline__ V4<T> pack(const T a[4]) {
-  return V4<T>{a[0], a[1], a[2], a[3]};
-}
 
 template <typename T>
 struct Smem {
@@ -85,8 +66,6 @@ struct Smem {
   unsigned char flag[WY][WX];
 };
 
-enum { F_W = 0, F_E = 1, F_S = 2, F_N = 3 };
-
 // One tile (bx, by) of one domain; called by the whole CTA.
 // XOR: x faces by the conservative Osher-Romberg viscosity of Eq. (OR_cons)
 // instead of the Gauss-Legendre quadrature of Eq. (OsherMatrixFormal_approx).
@@ -106,38 +85,20 @@ __device__ __forceinline__ void step_tile(const StepParams& p, const KConsts<T>&
   const size_t N = (size_t)nx * ny;
 
   const Phys<T>& P = kc.P;
-  // boundary kinds as scalars (a runtime index into the parameter struct would
-  // place it in local memory)
-  const bool trW = p.side[0] == 1, trE = p.side[1] == 1, trS = p.side[2] == 1, trN = p.side[3] == 1;
-  const T dx = kc.dx, dy = kc.dy, eps = kc.eps;
-  const T inv_dx = kc.inv_dx, inv_dy = kc.inv_dy, inv_1meps = kc.inv_1meps;
+  const Sides sd = sides_of(p);
+  const T dx = kc.dx, dy = kc.dy;
   // dt of this step, computed once per step by the finalize/prepare kernels
   const T dt = sizeof(T) == 8 ? (T)sc->dt_cur : (T)sc->dt_cur_f;
 
   // ---------------------------------------------------------------- load
-  // Each warp loads whole window rows: its 32 lanes the 128-byte-aligned
-  // centre (coalesced), lanes 0-3 the two halo columns on either side.
-  const int lane = tid & 31, warp = tid >> 5;
-  for (int wj = warp; wj < WY; wj += NT / 32) {
-    const int gj = j0 - 2 + wj;
-    for (int pass = 0; pass < 2; ++pass) {
-      if (pass == 1 && lane >= 4) break;
-      const int wi = pass == 0 ? lane + 2 : (lane < 2 ? lane : TX + lane);
-      const int gi = i0 - 2 + wi;
-      unsigned char f = F_OUT;
-      if (gi >= 0 && gj >= 0 && gi < nx && gj < ny) f = solid[(size_t)gj * nx + gi] ? F_SOLID : F_FLUID;
-      S.flag[wj][wi] = f;
-      if (f == F_FLUID) {
-        const size_t c = (size_t)gj * nx + gi;
-        T m = qin[c];
-        const T a = qin[3 * N + c];
-        if (DEV) {
-          // re-base m^f from the level it was stored with to this step's level
-          const int Kr = Kref[gi], Kc = Kcur[gi];
-          if (Kr != Kc) m += a * (tab(rt, 2 * (gj - Kr) + 1, ny) - tab(rt, 2 * (gj - Kc) + 1, ny));
-        }
-        S.u.w[wj][wi] = V4<T>{m, qin[N + c], qin[2 * N + c], a};
-      }
+  // The window row by row (coalesced), every cell's loads issued together.
+#pragma unroll
+  for (int k = 0; k < (WX * WY + NT - 1) / NT; ++k) {
+    const int idx = tid + k * NT;
+    if (idx < WX * WY) {
+      const int wj = idx / WX, wi = idx % WX;
+      S.flag[wj][wi] = load_cell<T, DEV>(qin, solid, Kref, Kcur, rt, nx, ny, N, i0 - 2 + wi,
+                                         j0 - 2 + wj, S.u.w[wj][wi]);
     }
   }
   for (int idx = tid; idx < WX; idx += NT) {
@@ -145,9 +106,6 @@ __device__ __forceinline__ void step_tile(const StepParams& p, const KConsts<T>&
     S.K[idx] = (gi >= 0 && gi < nx) ? Kcur[gi] : 0;
   }
   __syncthreads();
-  // rho^E at h half cells above the level (Eq. (BNs_eq3)); levels are at most
-  // ny (level_of), so h stays inside the table
-  auto rE = [&](int h) -> T { return tab(rt, h, ny); };
 
   // Own-cell state for the update, kept in registers.
   const int gi_me = i0 + tx, gj_me = j0 + ty;
@@ -163,82 +121,13 @@ __device__ __forceinline__ void step_tile(const StepParams& p, const KConsts<T>&
     const int rx = idx % RX, ry = idx / RX;
     const int wi = rx + 1, wj = ry + 1;
     if (S.flag[wj][wi] != F_FLUID) continue;
-    const int gj = j0 - 1 + ry;
-    const int K = S.K[wi];
-    const V4<T> wc = S.u.w[wj][wi];
-    const T aE = wc.w;
-    const T rEc = rE(2 * (gj - K) + 1);
-    const T rES = rE(2 * (gj - K));
-    const T rEN = rE(2 * (gj + 1 - K));
-    const T mEc = aE * rEc;
-    T Qf[4];
-    Qf[0] = DEV ? wc.x : wc.x - mEc;
-    Qf[1] = wc.y;
-    Qf[2] = wc.z;
-    Qf[3] = T(0);
-
-    // fluctuation of a neighbour w.r.t. this cell's Q^E; ghost if not fluid
-    auto nbf = [&](int dwi, int dwj, T out[4]) -> bool {
-      const int ni = wi + dwi, nj = wj + dwj;
-      if (S.flag[nj][ni] != F_FLUID) return false;
-      const V4<T> wn = S.u.w[nj][ni];
-      const T an = wn.w;
-      const int gjn = gj + dwj;
-      const T rn = rE(2 * (gjn - K) + 1);
-      if (DEV) {
-        const int Kn = S.K[ni];
-        T mshift;
-        if (Kn == K) mshift = (an - aE) * rn;
-        else mshift = an * rE(2 * (gjn - Kn) + 1) - aE * rn;
-        out[0] = wn.x + mshift;
-      } else {
-        out[0] = wn.x - aE * rn;
-      }
-      out[1] = wn.y;
-      out[2] = wn.z;
-      out[3] = an - aE;
-      return true;
-    };
-    auto ghost = [&](int dwi, int dwj, int normal, int side, T out[4]) {
-      const unsigned char f = S.flag[wj + dwj][wi + dwi];
-#pragma unroll
-      for (int v = 0; v < 4; ++v) out[v] = Qf[v];
-      const bool tr = side == 0 ? trW : side == 1 ? trE : side == 2 ? trS : trN;
-      if (!(f == F_OUT && tr)) {
-        if (normal == 1) out[1] = -out[1];
-        else out[2] = -out[2];
-      }
-    };
-    T fW[4], fE[4], fS[4], fN[4];
-    if (!nbf(-1, 0, fW)) ghost(-1, 0, 1, 0, fW);
-    if (!nbf(1, 0, fE)) ghost(1, 0, 1, 1, fE);
-    if (!nbf(0, -1, fS)) ghost(0, -1, 2, 2, fS);
-    if (!nbf(0, 1, fN)) ghost(0, 1, 2, 3, fN);
-    T mx[4], mn[4];
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      mx[v] = fmax(fmax(fmax(Qf[v], fW[v]), fmax(fE[v], fS[v])), fN[v]);
-      mn[v] = fmin(fmin(fmin(Qf[v], fW[v]), fmin(fE[v], fS[v])), fN[v]);
-    }
-#pragma unroll
-    for (int d = 0; d < 4; ++d) {
-      T fd[4];
-      if (nbf((d & 1) ? 1 : -1, (d & 2) ? 1 : -1, fd)) {
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          mx[v] = fmax(mx[v], fd[v]);
-          mn[v] = fmin(mn[v], fd[v]);
-        }
-      }
-    }
-    const T mES = aE * rES, mEN = aE * rEN;
+    V4<T> rs, rf[4];
     T base[4], ga[2];
-    recon_core(Qf, fW, fE, fS, fN, mx, mn, aE, mEc, mES, mEN, rEc, P, RC, base, ga);
-    S.rs[ry][rx] = V4<T>{aE, mEc, mES, mEN};
-    S.rf[F_W][ry][rx] = pack(fW);
-    S.rf[F_E][ry][rx] = pack(fE);
-    S.rf[F_S][ry][rx] = pack(fS);
-    S.rf[F_N][ry][rx] = pack(fN);
+    recon_cell<T, DEV>(S.u.w[wj - 1], S.u.w[wj], S.u.w[wj + 1], S.flag[wj - 1], S.flag[wj],
+                       S.flag[wj + 1], S.K, wi, j0 - 1 + ry, rt, ny, sd, P, RC, rs, rf, base, ga);
+    S.rs[ry][rx] = rs;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) S.rf[f][ry][rx] = rf[f];
     if (rx >= 1 && rx <= TX && ry >= 1 && ry <= TY) {
       S.base[ry - 1][rx - 1] = pack(base);
       S.ga[0][ry - 1][rx - 1] = ga[0];
@@ -249,107 +138,21 @@ __device__ __forceinline__ void step_tile(const StepParams& p, const KConsts<T>&
 
   // ---------------------------------------------------------------- faces
   for (int idx = tid; idx < (TX + 1) * TY + TX * (TY + 1); idx += NT) {
-    T Dm[4] = {0, 0, 0, 0}, Dp[4] = {0, 0, 0, 0};
+    T Dm[4], Dp[4];
     if (idx < (TX + 1) * TY) {
       const int fx = idx % (TX + 1), fy = idx / (TX + 1);
       const int rxL = fx, rxR = fx + 1, ry = fy + 1;
-      const bool L = S.flag[ry + 1][rxL + 1] == F_FLUID;
-      const bool R = S.flag[ry + 1][rxR + 1] == F_FLUID;
-      if (L || R) {
-        T qm[4], qp[4], dq[4];
-        if (L && R) {
-          const V4<T> sL = S.rs[ry][rxL], sR = S.rs[ry][rxR];
-          const T mEL = sL.y, mER = sR.y;
-          const T aL = sL.x, aR = sR.x;
-          T fl[4], fr[4];
-          unpack(S.rf[F_E][ry][rxL], fl);
-          unpack(S.rf[F_W][ry][rxR], fr);
-          qm[0] = mEL + fl[0]; qm[1] = fl[1]; qm[2] = fl[2]; qm[3] = aL + fl[3];
-          qp[0] = mER + fr[0]; qp[1] = fr[1]; qp[2] = fr[2]; qp[3] = aR + fr[3];
-          dq[0] = (mER - mEL) + (fr[0] - fl[0]);
-          dq[1] = fr[1] - fl[1];
-          dq[2] = fr[2] - fl[2];
-          dq[3] = (aR - aL) + (fr[3] - fl[3]);
-        } else {
-          const int rx = L ? rxL : rxR;
-          const V4<T> sc_ = S.rs[ry][rx];
-          const V4<T> fc = S.rf[L ? F_E : F_W][ry][rx];
-          const T mE = sc_.y, aE = sc_.x;
-          T q[4];
-          q[0] = mE + fc.x;
-          q[1] = fc.y;
-          q[2] = fc.z;
-          q[3] = aE + fc.w;
-          const bool outside = L ? (S.flag[ry + 1][rxR + 1] == F_OUT) : (S.flag[ry + 1][rxL + 1] == F_OUT);
-          const bool transmissive = outside && (L ? trE : trW);
-          T g[4] = {q[0], transmissive ? q[1] : -q[1], q[2], q[3]};
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            qm[c] = L ? q[c] : g[c];
-            qp[c] = L ? g[c] : q[c];
-          }
-          dq[0] = T(0);
-          dq[1] = qp[1] - qm[1];
-          dq[2] = T(0);
-          dq[3] = T(0);
-        }
-        if (XOR) xface_or(qm, qp, dq, P, Dm, Dp);
-        else xface(qm, qp, dq, P, Dm, Dp);
-      }
+      x_face<T, XOR>(S.flag[ry + 1][rxL + 1], S.flag[ry + 1][rxR + 1], &S.rs[ry][rxL],
+                     &S.rf[F_E][ry][rxL], &S.rs[ry][rxR], &S.rf[F_W][ry][rxR], sd, P, Dm, Dp);
       S.u.d.Dx[0][fy][fx] = pack(Dm);
       S.u.d.Dx[1][fy][fx] = pack(Dp);
     } else {
       const int k = idx - (TX + 1) * TY;
       const int fx = k % TX, fy = k / TX;
       const int rx = fx + 1, ryB = fy, ryT = fy + 1;
-      const bool B = S.flag[ryB + 1][rx + 1] == F_FLUID;
-      const bool Tt = S.flag[ryT + 1][rx + 1] == F_FLUID;
-      if (B || Tt) {
-        T qm[4], qp[4], dq[4];
-        T dap = T(0);
-        if (B && Tt) {
-          const V4<T> sB = S.rs[ryB][rx], sT = S.rs[ryT][rx];
-          const T mEB = sB.w, mET = sT.z;
-          const T aB = sB.x, aT = sT.x;
-          T fb[4], ft[4];
-          unpack(S.rf[F_N][ryB][rx], fb);
-          unpack(S.rf[F_S][ryT][rx], ft);
-          qm[0] = mEB + fb[0]; qm[1] = fb[1]; qm[2] = fb[2]; qm[3] = aB + fb[3];
-          qp[0] = mET + ft[0]; qp[1] = ft[1]; qp[2] = ft[2]; qp[3] = aT + ft[3];
-          dq[0] = (mET - mEB) + (ft[0] - fb[0]);
-          dq[1] = ft[1] - fb[1];
-          dq[2] = ft[2] - fb[2];
-          dq[3] = (aT - aB) + (ft[3] - fb[3]);
-          // jump of alpha p: equilibrium part (rho^E_f - rho0) Delta alpha^E is
-          // exactly zero at the level face; fluctuation part c2 (dm^f - rho0 da^f)
-          const int K = S.K[rx + 1];
-          const T rEf = rE(2 * (j0 - 1 + ryT - K));
-          dap = P.c2 * ((rEf - P.rho0) * (aT - aB) + ((ft[0] - fb[0]) - P.rho0 * (ft[3] - fb[3])));
-        } else {
-          const int ry = B ? ryB : ryT;
-          const V4<T> sc_ = S.rs[ry][rx];
-          const V4<T> fc = S.rf[B ? F_N : F_S][ry][rx];
-          const T mE = B ? sc_.w : sc_.z, aE = sc_.x;
-          T q[4];
-          q[0] = mE + fc.x;
-          q[1] = fc.y;
-          q[2] = fc.z;
-          q[3] = aE + fc.w;
-          const bool outside = B ? (S.flag[ryT + 1][rx + 1] == F_OUT) : (S.flag[ryB + 1][rx + 1] == F_OUT);
-          const bool transmissive = outside && (B ? trN : trS);
-          T g[4] = {q[0], q[1], transmissive ? q[2] : -q[2], q[3]};
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            qm[c] = B ? q[c] : g[c];
-            qp[c] = B ? g[c] : q[c];
-          }
-          dq[0] = T(0);
-          dq[1] = T(0);
-          dq[2] = qp[2] - qm[2];
-          dq[3] = T(0);
-        }
-        yface(qm, qp, dq, dap, P, Dm, Dp);
-      }
+      y_face<T>(S.flag[ryB + 1][rx + 1], S.flag[ryT + 1][rx + 1], &S.rs[ryB][rx],
+                &S.rf[F_N][ryB][rx], &S.rs[ryT][rx], &S.rf[F_S][ryT][rx], S.K[rx + 1],
+                j0 - 1 + ryT, rt, ny, sd, P, Dm, Dp);
       S.u.d.Dy[0][fy][fx] = pack(Dm);
       S.u.d.Dy[1][fy][fx] = pack(Dp);
     }
@@ -363,46 +166,15 @@ __device__ __forceinline__ void step_tile(const StepParams& p, const KConsts<T>&
   if (inside && flag_me == F_FLUID) {
     const int rx = tx + 1, ry = ty + 1;
     const int K = S.K[tx + 2];
-    const V4<T> sme = S.rs[ry][rx];
-    const T mEc = sme.y, mES = sme.z, mEN = sme.w;
-    T fW[4], fE[4], fS[4], fN[4], base[4];
-    unpack(S.rf[F_W][ry][rx], fW);
-    unpack(S.rf[F_E][ry][rx], fE);
-    unpack(S.rf[F_S][ry][rx], fS);
-    unpack(S.rf[F_N][ry][rx], fN);
-    unpack(S.base[ty][tx], base);
-    const T dax = S.ga[0][ty][tx], day = S.ga[1][ty][tx];
-    T Ix[4], Iy[4];
-    interior_terms(fW, fE, fS, fN, base, mEc, mES, mEN, dax, day, dx, dy, P, Ix, Iy);
-    const T rdx = dt / dx, rdy = dt / dy;
-    T xs[4], ys[4], DpW[4], DmE[4], DpS[4], DmN[4];
-    unpack(S.u.d.Dx[1][ty][tx], DpW);
-    unpack(S.u.d.Dx[0][ty][tx + 1], DmE);
-    unpack(S.u.d.Dy[1][ty][tx], DpS);
-    unpack(S.u.d.Dy[0][ty + 1][tx], DmN);
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      xs[c] = DpW[c] + DmE[c] + Ix[c];
-      ys[c] = DpS[c] + DmN[c] + Iy[c];
-    }
+    const V4<T> rf[4] = {S.rf[F_W][ry][rx], S.rf[F_E][ry][rx], S.rf[F_S][ry][rx],
+                         S.rf[F_N][ry][rx]};
+    const T rEc = DEV ? tab(rt, 2 * (gj_me - K) + 1, ny) : T(0);
     T qn[4];
-    T m_full;
-    if (DEV) {
-      // deviation form: m^f_new = m^f + dm - rho^E_c da (own level, own new alpha)
-      T dQ[4];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) dQ[c] = -rdx * xs[c] - rdy * ys[c];
-      const T rEc = rE(2 * (gj_me - K) + 1);
-      qn[0] = qold[0] + (dQ[0] - rEc * dQ[3]);
-      qn[1] = qold[1] + dQ[1];
-      qn[2] = qold[2] + dQ[2];
-      qn[3] = qold[3] + dQ[3];
-      m_full = qn[3] * rEc + qn[0];
-    } else {
-#pragma unroll
-      for (int c = 0; c < 4; ++c) qn[c] = qold[c] - rdx * xs[c] - rdy * ys[c];
-      m_full = qn[0];
-    }
+    const T m_full = update_cell<T, DEV>(qold, S.rs[ry][rx], rf, S.base[ty][tx], S.ga[0][ty][tx],
+                                         S.ga[1][ty][tx], S.u.d.Dx[1][ty][tx],
+                                         S.u.d.Dx[0][ty][tx + 1], S.u.d.Dy[1][ty][tx],
+                                         S.u.d.Dy[0][ty + 1][tx], rEc, dt / dx, dt / dy, dx, dy, P,
+                                         qn);
     const size_t c = (size_t)gj_me * nx + gi_me;
 #pragma unroll
     for (int v = 0; v < 4; ++v) qout[v * N + c] = qn[v];
@@ -754,16 +526,23 @@ void launch_batch_prepare(bool f64, const void* table, int ndom, double cfl, cud
 
 void launch_step_f64(const StepParams& p, const StateF64& s, const uint8_t* solid,
                      const int32_t* Kcur, unsigned long long* colsum, DevScalars* sc,
-                     const Tables& tb, cudaStream_t st, bool osher_romberg_x) {
-  launch_step_t<double, false>(p, s.in, s.out, solid, Kcur, Kcur, colsum, sc, tb.rhoE_d,
-                               tb.rhoE_d, osher_romberg_x, st);
+                     const Tables& tb, cudaStream_t st, bool osher_romberg_x, int tiling) {
+  if (tiling == TILING_TILE)
+    launch_step_t<double, false>(p, s.in, s.out, solid, Kcur, Kcur, colsum, sc, tb.rhoE_d,
+                                 tb.rhoE_d, osher_romberg_x, st);
+  else
+    launch_strip_f64(p, s, solid, Kcur, colsum, sc, tb, st, osher_romberg_x);
 }
 
 void launch_step_f32(const StepParams& p, const StateF32& s, const uint8_t* solid,
                      const int32_t* Kref, const int32_t* Kcur, unsigned long long* colsum,
-                     DevScalars* sc, const Tables& tb, cudaStream_t st, bool osher_romberg_x) {
-  launch_step_t<float, true>(p, s.in, s.out, solid, Kref, Kcur, colsum, sc, tb.rhoE_d,
-                             tb.rhoE_f, osher_romberg_x, st);
+                     DevScalars* sc, const Tables& tb, cudaStream_t st, bool osher_romberg_x,
+                     int tiling) {
+  if (tiling == TILING_TILE)
+    launch_step_t<float, true>(p, s.in, s.out, solid, Kref, Kcur, colsum, sc, tb.rhoE_d,
+                               tb.rhoE_f, osher_romberg_x, st);
+  else
+    launch_strip_f32(p, s, solid, Kref, Kcur, colsum, sc, tb, st, osher_romberg_x);
 }
 
 void launch_finalize(const StepParams& p, int32_t* Kref, int32_t* Kcur,

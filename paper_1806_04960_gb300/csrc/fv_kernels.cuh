@@ -58,13 +58,28 @@ struct StateF32 {
 
 // osher_romberg_x: x faces by the conservative Osher-Romberg viscosity of Eq.
 // (OR_cons) instead of the Gauss-Legendre Osher of Eq. (OsherMatrixFormal_approx).
+// tiling: which kernel stages the step (the same arithmetic, the same results):
+// TILING_TILE = step_kernel, one CTA per 32 x 8 tile (csrc/fv_kernels.cu);
+// TILING_STRIP = strip_kernel, one CTA per 32-column strip (csrc/fv_strip.cu);
+// TILING_AUTO = the strip kernel.
+enum StepTiling { TILING_AUTO = 0, TILING_TILE = 1, TILING_STRIP = 2 };
 void launch_step_f64(const StepParams& p, const StateF64& s, const uint8_t* solid,
                      const int32_t* Kcur, unsigned long long* colsum, DevScalars* sc,
-                     const Tables& tb, cudaStream_t st, bool osher_romberg_x = false);
+                     const Tables& tb, cudaStream_t st, bool osher_romberg_x = false,
+                     int tiling = TILING_AUTO);
 void launch_step_f32(const StepParams& p, const StateF32& s, const uint8_t* solid,
                      const int32_t* Kref, const int32_t* Kcur, unsigned long long* colsum,
                      DevScalars* sc, const Tables& tb, cudaStream_t st,
-                     bool osher_romberg_x = false);
+                     bool osher_romberg_x = false, int tiling = TILING_AUTO);
+void launch_strip_f64(const StepParams& p, const StateF64& s, const uint8_t* solid,
+                      const int32_t* Kcur, unsigned long long* colsum, DevScalars* sc,
+                      const Tables& tb, cudaStream_t st, bool osher_romberg_x);
+void launch_strip_f32(const StepParams& p, const StateF32& s, const uint8_t* solid,
+                      const int32_t* Kref, const int32_t* Kcur, unsigned long long* colsum,
+                      DevScalars* sc, const Tables& tb, cudaStream_t st, bool osher_romberg_x);
+// Strip height (rows, a multiple of 8) for an nx x ny grid when `resident`
+// strip CTAs fit on the device at once.
+int strip_height(int nx, int ny, int resident);
 // First-order scheme of Sections 3.2-3.3 (csrc/fv_order1.cu).
 void launch_step_o1_f64(const StepParams& p, const StateF64& s, const uint8_t* solid,
                         const int32_t* Kcur, unsigned long long* colsum, DevScalars* sc,

@@ -1,0 +1,293 @@
+// One time step of Eq. (Scheme) by column strips: one CTA per strip of 32
+// columns and H rows (H a multiple of 8), marching upwards in blocks of 8 rows.
+// The cell and face arithmetic is that of the tile kernel (fv_tile.cuh); what
+// differs is the staging.  Consecutive blocks share two reconstructed rows and
+// one row of y faces, which a tile kernel recomputes for every tile: the
+// window of Q^n (WRING rows), the reconstruction records and the y-face
+// fluctuations (RING rows) live in ring buffers, so that per block only 8 new
+// window rows are loaded, 8 rows (+ the ring columns) reconstructed and 8 rows
+// of y faces solved.  The window ring holds the 10 rows a block reads plus the
+// 8 the next block loads, so a block's load never waits for the previous
+// block's update.  With 320 threads every phase of a block is one pass:
+//
+//   load    rows j0+2 .. j0+9 of the window (288 cells, loads issued together)
+//   recon   rows j0+1 .. j0+8, 34 columns (272 cells)
+//   faces   x faces of rows j0 .. j0+7 (264; warps 0-8) and y faces above rows
+//           j0 .. j0+7 (256; warp 9, then warps 0-6), no warp holding both kinds
+//   update  rows j0 .. j0+7 (256 cells)
+//
+// A prologue per strip loads rows jstart-2 .. jstart+1, reconstructs rows
+// jstart-1 and jstart and solves the y faces between them.  The epilogue
+// (signal rate, detector column sums, status) is reduced once per strip.
+#include <cuda_runtime.h>
+
+#include "fv_consts.cuh"
+#include "fv_kernels.cuh"
+#include "fv_model.cuh"
+#include "fv_tile.cuh"
+
+namespace fv {
+
+namespace {
+
+using namespace tile;
+
+constexpr int SX = 32;          // strip width (cells)
+constexpr int BY = 8;           // rows per block
+constexpr int NTS = 320;        // threads per CTA (10 warps)
+constexpr int SWX = SX + 4;     // window columns: 2-cell halo on both sides
+constexpr int SRX = SX + 2;     // reconstructed columns: 1-cell ring
+constexpr int RING = 10;        // rows of the record and y-face rings
+constexpr int WRING = 18;       // rows of the window ring
+constexpr int NXF = (SX + 1) * BY;  // x faces of a block
+constexpr int NYF = SX * BY;        // y faces of a block
+
+static_assert(BY * SWX <= NTS && BY * SRX <= NTS && NXF <= NTS, "one pass per phase");
+static_assert(NYF - (NTS - 9 * 32) <= 7 * 32, "y faces: warp 9, then warps 0-6");
+
+template <typename T>
+struct StripSmem {
+  V4<T> w[WRING][SWX];         // window rows of Q^n (stored form, re-based)
+  V4<T> rs[RING][SRX];         // (alpha^E, m^E centre, bottom, top face)
+  V4<T> rf[4][RING][SRX];      // face fluctuation states W, E, S, N at t^{n+1/2}
+  V4<T> base[RING][SX];        // centre fluctuation at t^{n+1/2}
+  V4<T> Dx[2][BY][SX + 1];     // D-, D+ of the block's x faces
+  V4<T> Dy[2][RING][SX];       // D-, D+ of the y faces, by the row below the face
+  T ga[2][RING][SX];           // limited alpha slopes
+  unsigned long long col[BY][SX];
+  double wmax[NTS / 32];
+  int K[SWX];                  // levels of the window columns
+  unsigned char flag[WRING][SWX];
+};
+
+template <typename T, bool DEV, bool XOR>
+__global__ void __launch_bounds__(NTS, (sizeof(T) == 8 ? 1 : 3))
+    strip_kernel(StepParams p, KConsts<T> kc, const T* __restrict__ qin, T* __restrict__ qout,
+                 const uint8_t* __restrict__ solid, const int32_t* __restrict__ Kref,
+                 const int32_t* __restrict__ Kcur, unsigned long long* __restrict__ colsum,
+                 DevScalars* __restrict__ sc, const T* __restrict__ rt, int H) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  StripSmem<T>& S = *reinterpret_cast<StripSmem<T>*>(smem_raw);
+  const int t = threadIdx.x;
+  const int nx = p.nx, ny = p.ny;
+  const size_t N = (size_t)nx * ny;
+  const int i0 = blockIdx.x * SX;
+  const int jstart = blockIdx.y * H;
+  const int jend = min(jstart + H, ny);
+  const int r0 = jstart - 2;  // first window row; every ring is indexed from it
+  auto wslot = [&](int r) -> int { return (r - r0) % WRING; };
+  auto slot = [&](int r) -> int { return (r - r0) % RING; };
+
+  const Phys<T>& P = kc.P;
+  const Sides sd = sides_of(p);
+  const T dx = kc.dx, dy = kc.dy;
+  // dt of this step, computed once per step by the finalize/prepare kernels
+  const T dt = sizeof(T) == 8 ? (T)sc->dt_cur : (T)sc->dt_cur_f;
+  const T rdx = dt / dx, rdy = dt / dy;
+  ReconConsts<T> RC = kc.R;
+  RC.half_dt = T(0.5) * dt;
+
+  auto load_rows = [&](int ra, int nrows) {
+    for (int idx = t; idx < nrows * SWX; idx += NTS) {
+      const int rr = ra + idx / SWX, wi = idx % SWX;
+      const int s = wslot(rr);
+      S.flag[s][wi] = load_cell<T, DEV>(qin, solid, Kref, Kcur, rt, nx, ny, N, i0 - 2 + wi, rr,
+                                        S.w[s][wi]);
+    }
+  };
+  auto recon_rows = [&](int ra, int nrows) {
+    for (int idx = t; idx < nrows * SRX; idx += NTS) {
+      const int rr = ra + idx / SRX, rx = idx % SRX, wi = rx + 1;
+      const int ws = wslot(rr);
+      if (S.flag[ws][wi] != F_FLUID) continue;
+      const int s = slot(rr), sS = wslot(rr - 1), sN = wslot(rr + 1);
+      V4<T> rs, rf[4];
+      T base[4], ga[2];
+      recon_cell<T, DEV>(S.w[sS], S.w[ws], S.w[sN], S.flag[sS], S.flag[ws], S.flag[sN], S.K, wi,
+                         rr, rt, ny, sd, P, RC, rs, rf, base, ga);
+      S.rs[s][rx] = rs;
+#pragma unroll
+      for (int f = 0; f < 4; ++f) S.rf[f][s][rx] = rf[f];
+      if (rx >= 1 && rx <= SX) {
+        S.base[s][rx - 1] = pack(base);
+        S.ga[0][s][rx - 1] = ga[0];
+        S.ga[1][s][rx - 1] = ga[1];
+      }
+    }
+  };
+  // y face between rows rB and rB + 1 of strip column fx
+  auto yface_at = [&](int rB, int fx) {
+    const int rx = fx + 1, sB = slot(rB), sT = slot(rB + 1);
+    T Dm[4], Dp[4];
+    y_face<T>(S.flag[wslot(rB)][rx + 1], S.flag[wslot(rB + 1)][rx + 1], &S.rs[sB][rx], &S.rf[F_N][sB][rx],
+              &S.rs[sT][rx], &S.rf[F_S][sT][rx], S.K[rx + 1], rB + 1, rt, ny, sd, P, Dm, Dp);
+    S.Dy[0][sB][fx] = pack(Dm);
+    S.Dy[1][sB][fx] = pack(Dp);
+  };
+
+  // ------------------------------------------------------------ prologue
+  for (int idx = t; idx < SWX; idx += NTS) {
+    const int gi = i0 - 2 + idx;
+    S.K[idx] = (gi >= 0 && gi < nx) ? Kcur[gi] : 0;
+  }
+  load_rows(jstart - 2, 4);
+  __syncthreads();
+  recon_rows(jstart - 1, 2);
+  __syncthreads();
+  if (t < SX) yface_at(jstart - 1, t);
+
+  T my_rate = T(0);
+  unsigned long long my_w = 0;
+  bool bad = false;
+  const int ux = t % SX, uy = t / SX;  // update: column and row in the block (t < 256)
+  const int gi_me = i0 + ux;
+
+  for (int j0 = jstart; j0 < jend; j0 += BY) {
+    // ---------------------------------------------------------- load
+    load_rows(j0 + 2, BY);
+    __syncthreads();
+    // ---------------------------------------------------------- recon
+    recon_rows(j0 + 1, BY);
+    __syncthreads();
+    // ---------------------------------------------------------- faces
+    if (t < NXF) {
+      const int fx = t % (SX + 1), fy = t / (SX + 1);
+      const int s = slot(j0 + fy), ws = wslot(j0 + fy);
+      T Dm[4], Dp[4];
+      x_face<T, XOR>(S.flag[ws][fx + 1], S.flag[ws][fx + 2], &S.rs[s][fx], &S.rf[F_E][s][fx],
+                     &S.rs[s][fx + 1], &S.rf[F_W][s][fx + 1], sd, P, Dm, Dp);
+      S.Dx[0][fy][fx] = pack(Dm);
+      S.Dx[1][fy][fx] = pack(Dp);
+    } else if (t >= 9 * 32) {
+      const int k = t - 9 * 32;
+      yface_at(j0 + k / SX, k % SX);
+    }
+    if (t < NYF - (NTS - 9 * 32)) {
+      const int k = t + (NTS - 9 * 32);
+      yface_at(j0 + k / SX, k % SX);
+    }
+    __syncthreads();
+    // ---------------------------------------------------------- update
+    if (t < SX * BY) {
+      const int r = j0 + uy;
+      const int s = slot(r), ws = wslot(r);
+      const bool inside = gi_me < nx && r < ny;
+      const unsigned char flag_me = S.flag[ws][ux + 2];
+      if (inside && flag_me == F_FLUID) {
+        T qold[4];
+        unpack(S.w[ws][ux + 2], qold);
+        const int K = S.K[ux + 2];
+        const V4<T> rf[4] = {S.rf[F_W][s][ux + 1], S.rf[F_E][s][ux + 1], S.rf[F_S][s][ux + 1],
+                             S.rf[F_N][s][ux + 1]};
+        const T rEc = DEV ? tab(rt, 2 * (r - K) + 1, ny) : T(0);
+        T qn[4];
+        const T m_full = update_cell<T, DEV>(qold, S.rs[s][ux + 1], rf, S.base[s][ux],
+                                             S.ga[0][s][ux], S.ga[1][s][ux], S.Dx[1][uy][ux],
+                                             S.Dx[0][uy][ux + 1], S.Dy[1][slot(r - 1)][ux],
+                                             S.Dy[0][s][ux], rEc, rdx, rdy, dx, dy, P, qn);
+        const size_t c = (size_t)r * nx + gi_me;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) qout[v * N + c] = qn[v];
+        T rate = T(0);
+        unsigned long long w = 0;
+        cell_epilogue<T, DEV>(p, kc, qn, m_full, rate, w, bad);
+        my_rate = fmax(my_rate, rate);
+        my_w += w;
+      } else if (inside) {
+        const size_t c = (size_t)r * nx + gi_me;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) qout[v * N + c] = T(0);
+        if (flag_me == F_SOLID) my_w += ONE_FIXED;
+      }
+    }
+    // The next block's load writes window rows j0+10 .. j0+17, slots no
+    // phase of this block reads; its recon and faces write record and y-face
+    // slots read above, behind its first barrier.
+  }
+
+  // ------------------------------------------------------------ epilogue
+  if (bad) atomicOr(&sc->status, 1);
+  if (t < SX * BY) S.col[uy][ux] = my_w;
+  T r_t = my_rate;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) r_t = fmax(r_t, __shfl_xor_sync(0xffffffffu, r_t, o));
+  if ((t & 31) == 0) S.wmax[t >> 5] = (double)r_t;
+  __syncthreads();
+  if (t < SX && gi_me < nx) {
+    unsigned long long s = 0;
+#pragma unroll
+    for (int r = 0; r < BY; ++r) s += S.col[r][t];
+    if (s) atomicAdd(&colsum[gi_me], s);
+  }
+  if (t == 0) {
+    double mrate = 0.0;
+#pragma unroll
+    for (int k = 0; k < NTS / 32; ++k) mrate = fmax(mrate, S.wmax[k]);
+    if (mrate > 0.0) atomicMax(&sc->rate_acc, (unsigned long long)__double_as_longlong(mrate));
+  }
+}
+
+template <typename T, bool DEV, bool XOR>
+void launch_strip_xt(const StepParams& p, const T* in, T* out, const uint8_t* solid,
+                     const int32_t* Kref, const int32_t* Kcur, unsigned long long* colsum,
+                     DevScalars* sc, const T* rt, cudaStream_t st) {
+  const size_t smem = sizeof(StripSmem<T>);
+  static int resident = 0;
+  if (!resident) {
+    cudaFuncSetAttribute(strip_kernel<T, DEV, XOR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, strip_kernel<T, DEV, XOR>, NTS, smem);
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    resident = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+  }
+  const int H = strip_height(p.nx, p.ny, resident);
+  const dim3 grid((p.nx + SX - 1) / SX, (p.ny + H - 1) / H);
+  strip_kernel<T, DEV, XOR><<<grid, NTS, smem, st>>>(p, make_consts<T>(p), in, out, solid, Kref,
+                                                      Kcur, colsum, sc, rt, H);
+}
+
+}  // namespace
+
+int strip_height(int nx, int ny, int resident) {
+  // Every CTA does about (H/8 + 0.4) blocks of work (the prologue is about
+  // 0.4 of a block); CTAs run in waves of `resident`.  Minimise waves x work.
+  const int ncol = (nx + SX - 1) / SX;
+  const int hmax = ((ny + BY - 1) / BY) * BY;
+  if (resident < 1) resident = 1;
+  int best = BY;
+  double best_cost = 1e300;
+  for (int k = 32; k >= 1; --k) {
+    const int H = k * BY;
+    if (H > hmax) continue;
+    const long long ctas = (long long)ncol * ((ny + H - 1) / H);
+    const long long waves = (ctas + resident - 1) / resident;
+    const double cost = (double)waves * ((double)H / BY + 0.4);
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = H;
+    }
+  }
+  return best;
+}
+
+void launch_strip_f64(const StepParams& p, const StateF64& s, const uint8_t* solid,
+                      const int32_t* Kcur, unsigned long long* colsum, DevScalars* sc,
+                      const Tables& tb, cudaStream_t st, bool osher_romberg_x) {
+  if (osher_romberg_x)
+    launch_strip_xt<double, false, true>(p, s.in, s.out, solid, Kcur, Kcur, colsum, sc, tb.rhoE_d, st);
+  else
+    launch_strip_xt<double, false, false>(p, s.in, s.out, solid, Kcur, Kcur, colsum, sc, tb.rhoE_d, st);
+}
+
+void launch_strip_f32(const StepParams& p, const StateF32& s, const uint8_t* solid,
+                      const int32_t* Kref, const int32_t* Kcur, unsigned long long* colsum,
+                      DevScalars* sc, const Tables& tb, cudaStream_t st, bool osher_romberg_x) {
+  if (osher_romberg_x)
+    launch_strip_xt<float, true, true>(p, s.in, s.out, solid, Kref, Kcur, colsum, sc, tb.rhoE_f, st);
+  else
+    launch_strip_xt<float, true, false>(p, s.in, s.out, solid, Kref, Kcur, colsum, sc, tb.rhoE_f, st);
+}
+
+}  // namespace fv

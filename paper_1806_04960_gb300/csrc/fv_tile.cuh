@@ -1,0 +1,342 @@
+// Cell- and face-level pieces of one time step of Eq. (Scheme), shared by the
+// two step kernels: step_kernel (fv_kernels.cu, one CTA per 32 x 8 tile) and
+// strip_kernel (fv_strip.cu, one CTA per 32-column strip marching upwards in
+// blocks of 8 rows).  The kernels differ only in how they stage the window of
+// Q^n and the reconstructed states in shared memory; every arithmetic
+// operation of a step is written here once, so both produce the same bits.
+//
+// Window coordinates: a window row is an array of cells of one grid row,
+// indexed by the window column wi = gi - i0 + 2 (two halo cells on the left
+// of the tile's first column i0).  Reconstructed (ring) coordinates: rx =
+// gi - i0 + 1.
+#pragma once
+
+#include <cstdint>
+
+#include "fv_consts.cuh"
+#include "fv_kernels.cuh"
+#include "fv_model.cuh"
+
+namespace fv {
+namespace tile {
+
+// Four components of one state as one shared-memory element, so that a state
+// moves with one vector access (LDS.128 / STS.128 in FP32, two in FP64).
+template <typename T>
+struct alignas(4 * sizeof(T)) V4 {
+  T x, y, z, w;
+};
+
+template <typename T>
+__device__ __forceinline__ void unpack(const V4<T>& v, T a[4]) {
+  a[0] = v.x;
+  a[1] = v.y;
+  a[2] = v.z;
+  a[3] = v.w;
+}
+
+template <typename T>
+__device__ __forceinline__ V4<T> pack(const T a[4]) {
+  return V4<T>{a[0], a[1], a[2], a[3]};
+}
+
+constexpr unsigned char F_FLUID = 0, F_SOLID = 1, F_OUT = 2;
+constexpr unsigned long long ONE_FIXED = 1ull << 32;
+enum { F_W = 0, F_E = 1, F_S = 2, F_N = 3 };
+
+// Boundary kinds of the four domain sides (true = transmissive, else wall).
+struct Sides {
+  bool W, E, S, N;
+};
+
+__device__ __forceinline__ Sides sides_of(const StepParams& p) {
+  return Sides{p.side[0] == 1, p.side[1] == 1, p.side[2] == 1, p.side[3] == 1};
+}
+
+// Window cell (gi, gj): its flag and, if fluid, its state (m, mu, mv, a).  All
+// loads of an in-domain cell are issued together (the state arrays hold zeros
+// in solid cells).  In deviation form m^f is re-based from the level it was
+// stored with (Kref) to this step's level (Kcur) of its column.
+template <typename T, bool DEV>
+__device__ __forceinline__ unsigned char load_cell(const T* __restrict__ qin,
+                                                   const uint8_t* __restrict__ solid,
+                                                   const int32_t* __restrict__ Kref,
+                                                   const int32_t* __restrict__ Kcur,
+                                                   const T* __restrict__ rt, int nx, int ny,
+                                                   size_t N, int gi, int gj, V4<T>& w) {
+  if (gi < 0 || gj < 0 || gi >= nx || gj >= ny) return F_OUT;
+  const size_t c = (size_t)gj * nx + gi;
+  const uint8_t s = solid[c];
+  T m = qin[c];
+  const T mu = qin[N + c], mv = qin[2 * N + c], a = qin[3 * N + c];
+  int Kr = 0, Kc = 0;
+  if (DEV) {
+    Kr = Kref[gi];
+    Kc = Kcur[gi];
+  }
+  if (s) return F_SOLID;
+  // re-base m^f from the level it was stored with to this step's level
+  if (DEV && Kr != Kc) m += a * (tab(rt, 2 * (gj - Kr) + 1, ny) - tab(rt, 2 * (gj - Kc) + 1, ny));
+  w = V4<T>{m, mu, mv, a};
+  return F_FLUID;
+}
+
+// Reconstruction of one cell (Section 3.4): fluctuations of the cell and its
+// eight neighbours with respect to the cell's water-at-rest state Q^E (alpha^E
+// = alpha of the cell, rho^E of its column level K at the neighbour's height);
+// walls and solid neighbours seen as the mirror state; the limiter bounds over
+// the 3 x 3 stencil; recon_core (slopes, Barth-Jespersen factor, order
+// switch, half-step predictor).  wS, wC, wN: window rows below, of and above
+// the cell (and their flags fS, fC, fN); Kw: the levels of the window columns;
+// wi: the cell's window column; gj: its grid row.
+// Outputs: rs = (alpha^E, m^E at the centre, bottom and top face), rf = the
+// four face fluctuation states (W, E, S, N) at t^{n+1/2}, base = the centre
+// fluctuation at t^{n+1/2}, ga = the limited alpha slopes.
+template <typename T, bool DEV>
+__device__ __forceinline__ void recon_cell(const V4<T>* wS, const V4<T>* wC, const V4<T>* wN,
+                                           const unsigned char* fS, const unsigned char* fC,
+                                           const unsigned char* fN, const int* Kw, int wi, int gj,
+                                           const T* __restrict__ rt, int ny, const Sides& sd,
+                                           const Phys<T>& P, const ReconConsts<T>& RC, V4<T>& rs,
+                                           V4<T> rf[4], T base[4], T ga[2]) {
+  auto rE = [&](int h) -> T { return tab(rt, h, ny); };
+  const int K = Kw[wi];
+  const V4<T> wc = wC[wi];
+  const T aE = wc.w;
+  const T rEc = rE(2 * (gj - K) + 1);
+  const T rES = rE(2 * (gj - K));
+  const T rEN = rE(2 * (gj + 1 - K));
+  const T mEc = aE * rEc;
+  T Qf[4];
+  Qf[0] = DEV ? wc.x : wc.x - mEc;
+  Qf[1] = wc.y;
+  Qf[2] = wc.z;
+  Qf[3] = T(0);
+
+  auto wrow = [&](int dwj) -> const V4<T>* { return dwj < 0 ? wS : (dwj > 0 ? wN : wC); };
+  auto frow = [&](int dwj) -> const unsigned char* { return dwj < 0 ? fS : (dwj > 0 ? fN : fC); };
+  // fluctuation of a neighbour w.r.t. this cell's Q^E; false if not fluid
+  auto nbf = [&](int dwi, int dwj, T out[4]) -> bool {
+    const int ni = wi + dwi;
+    if (frow(dwj)[ni] != F_FLUID) return false;
+    const V4<T> wn = wrow(dwj)[ni];
+    const T an = wn.w;
+    const int gjn = gj + dwj;
+    const T rn = rE(2 * (gjn - K) + 1);
+    if (DEV) {
+      const int Kn = Kw[ni];
+      T mshift;
+      if (Kn == K) mshift = (an - aE) * rn;
+      else mshift = an * rE(2 * (gjn - Kn) + 1) - aE * rn;
+      out[0] = wn.x + mshift;
+    } else {
+      out[0] = wn.x - aE * rn;
+    }
+    out[1] = wn.y;
+    out[2] = wn.z;
+    out[3] = an - aE;
+    return true;
+  };
+  // mirror state behind a wall or a solid neighbour; the cell's own state
+  // behind a transmissive side
+  auto ghost = [&](int dwi, int dwj, int normal, bool tr, T out[4]) {
+    const unsigned char f = frow(dwj)[wi + dwi];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) out[v] = Qf[v];
+    if (!(f == F_OUT && tr)) {
+      if (normal == 1) out[1] = -out[1];
+      else out[2] = -out[2];
+    }
+  };
+  T fW[4], fE[4], fSo[4], fNo[4];
+  if (!nbf(-1, 0, fW)) ghost(-1, 0, 1, sd.W, fW);
+  if (!nbf(1, 0, fE)) ghost(1, 0, 1, sd.E, fE);
+  if (!nbf(0, -1, fSo)) ghost(0, -1, 2, sd.S, fSo);
+  if (!nbf(0, 1, fNo)) ghost(0, 1, 2, sd.N, fNo);
+  T mx[4], mn[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    mx[v] = fmax(fmax(fmax(Qf[v], fW[v]), fmax(fE[v], fSo[v])), fNo[v]);
+    mn[v] = fmin(fmin(fmin(Qf[v], fW[v]), fmin(fE[v], fSo[v])), fNo[v]);
+  }
+#pragma unroll
+  for (int d = 0; d < 4; ++d) {
+    T fd[4];
+    if (nbf((d & 1) ? 1 : -1, (d & 2) ? 1 : -1, fd)) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        mx[v] = fmax(mx[v], fd[v]);
+        mn[v] = fmin(mn[v], fd[v]);
+      }
+    }
+  }
+  const T mES = aE * rES, mEN = aE * rEN;
+  recon_core(Qf, fW, fE, fSo, fNo, mx, mn, aE, mEc, mES, mEN, rEc, P, RC, base, ga);
+  rs = V4<T>{aE, mEc, mES, mEN};
+  rf[F_W] = pack(fW);
+  rf[F_E] = pack(fE);
+  rf[F_S] = pack(fSo);
+  rf[F_N] = pack(fNo);
+}
+
+// x face between the reconstructed cells L (left) and R (right) with flags fl,
+// fr: L's (alpha^E, m^E ...) record sL and east face state eL, R's record sR
+// and west face state wR (read only where the cell is fluid).  Both fluid: the
+// Osher solver on the two reconstructed states; one fluid: the mirror state
+// (a wall or a solid neighbour) or the transmissive copy on the other side.
+// XOR selects the conservative Osher-Romberg viscosity of Eq. (OR_cons)
+// instead of the Gauss-Legendre quadrature of Eq. (OsherMatrixFormal_approx).
+template <typename T, bool XOR>
+__device__ __forceinline__ void x_face(unsigned char fl, unsigned char fr, const V4<T>* sL,
+                                       const V4<T>* eL, const V4<T>* sR, const V4<T>* wR,
+                                       const Sides& sd, const Phys<T>& P, T Dm[4], T Dp[4]) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) Dm[c] = Dp[c] = T(0);
+  const bool L = fl == F_FLUID, R = fr == F_FLUID;
+  if (!(L || R)) return;
+  T qm[4], qp[4], dq[4];
+  if (L && R) {
+    const V4<T> a = *sL, b = *sR;
+    const T mEL = a.y, mER = b.y;
+    const T aL = a.x, aR = b.x;
+    T fl4[4], fr4[4];
+    unpack(*eL, fl4);
+    unpack(*wR, fr4);
+    qm[0] = mEL + fl4[0]; qm[1] = fl4[1]; qm[2] = fl4[2]; qm[3] = aL + fl4[3];
+    qp[0] = mER + fr4[0]; qp[1] = fr4[1]; qp[2] = fr4[2]; qp[3] = aR + fr4[3];
+    dq[0] = (mER - mEL) + (fr4[0] - fl4[0]);
+    dq[1] = fr4[1] - fl4[1];
+    dq[2] = fr4[2] - fl4[2];
+    dq[3] = (aR - aL) + (fr4[3] - fl4[3]);
+  } else {
+    const V4<T> s = L ? *sL : *sR;
+    const V4<T> fc = L ? *eL : *wR;
+    const T mE = s.y, aE = s.x;
+    T q[4];
+    q[0] = mE + fc.x;
+    q[1] = fc.y;
+    q[2] = fc.z;
+    q[3] = aE + fc.w;
+    const bool outside = L ? (fr == F_OUT) : (fl == F_OUT);
+    const bool transmissive = outside && (L ? sd.E : sd.W);
+    T g[4] = {q[0], transmissive ? q[1] : -q[1], q[2], q[3]};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      qm[c] = L ? q[c] : g[c];
+      qp[c] = L ? g[c] : q[c];
+    }
+    dq[0] = T(0);
+    dq[1] = qp[1] - qm[1];
+    dq[2] = T(0);
+    dq[3] = T(0);
+  }
+  if (XOR) xface_or(qm, qp, dq, P, Dm, Dp);
+  else xface(qm, qp, dq, P, Dm, Dp);
+}
+
+// y face between the reconstructed cells B (below) and T (above) of a column
+// with level K; gjT is T's grid row.  sB, nB: B's record and north face
+// state; sT, sT_: T's record and south face state.  The jump of alpha p is
+// split into its equilibrium part (rho^E_f - rho0) Delta alpha^E, exactly
+// zero at the level face, and the fluctuation part c2 (dm^f - rho0 da^f).
+template <typename T>
+__device__ __forceinline__ void y_face(unsigned char fb, unsigned char ft, const V4<T>* sB,
+                                       const V4<T>* nB, const V4<T>* sT, const V4<T>* sT_,
+                                       int K, int gjT, const T* __restrict__ rt, int ny,
+                                       const Sides& sd, const Phys<T>& P, T Dm[4], T Dp[4]) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) Dm[c] = Dp[c] = T(0);
+  const bool B = fb == F_FLUID, Tt = ft == F_FLUID;
+  if (!(B || Tt)) return;
+  T qm[4], qp[4], dq[4];
+  T dap = T(0);
+  if (B && Tt) {
+    const V4<T> a = *sB, b = *sT;
+    const T mEB = a.w, mET = b.z;
+    const T aB = a.x, aT = b.x;
+    T fb4[4], ft4[4];
+    unpack(*nB, fb4);
+    unpack(*sT_, ft4);
+    qm[0] = mEB + fb4[0]; qm[1] = fb4[1]; qm[2] = fb4[2]; qm[3] = aB + fb4[3];
+    qp[0] = mET + ft4[0]; qp[1] = ft4[1]; qp[2] = ft4[2]; qp[3] = aT + ft4[3];
+    dq[0] = (mET - mEB) + (ft4[0] - fb4[0]);
+    dq[1] = ft4[1] - fb4[1];
+    dq[2] = ft4[2] - fb4[2];
+    dq[3] = (aT - aB) + (ft4[3] - fb4[3]);
+    const T rEf = tab(rt, 2 * (gjT - K), ny);
+    dap = P.c2 * ((rEf - P.rho0) * (aT - aB) + ((ft4[0] - fb4[0]) - P.rho0 * (ft4[3] - fb4[3])));
+  } else {
+    const V4<T> s = B ? *sB : *sT;
+    const V4<T> fc = B ? *nB : *sT_;
+    const T mE = B ? s.w : s.z, aE = s.x;
+    T q[4];
+    q[0] = mE + fc.x;
+    q[1] = fc.y;
+    q[2] = fc.z;
+    q[3] = aE + fc.w;
+    const bool outside = B ? (ft == F_OUT) : (fb == F_OUT);
+    const bool transmissive = outside && (B ? sd.N : sd.S);
+    T g[4] = {q[0], q[1], transmissive ? q[2] : -q[2], q[3]};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      qm[c] = B ? q[c] : g[c];
+      qp[c] = B ? g[c] : q[c];
+    }
+    dq[0] = T(0);
+    dq[1] = T(0);
+    dq[2] = qp[2] - qm[2];
+    dq[3] = T(0);
+  }
+  yface(qm, qp, dq, dap, P, Dm, Dp);
+}
+
+// Update of one fluid cell: Q^{n+1} = Q^n - dt/dx (D+_W + D-_E + I_x)
+// - dt/dy (D+_S + D-_N + I_y) with the interior integral of Eq.
+// (b^y_3_final_integral) plus the conservative part.  rs, rf, base, ga: the
+// cell's reconstruction; DpW, DmE, DpS, DmN: the fluctuations of its four
+// faces; rEc: rho^E at its centre (deviation form).  qn: the new state in
+// stored form; returns the full alpha rho.
+template <typename T, bool DEV>
+__device__ __forceinline__ T update_cell(const T qold[4], const V4<T>& rs, const V4<T>* rf,
+                                         const V4<T>& base4, T dax, T day, const V4<T>& DpW4,
+                                         const V4<T>& DmE4, const V4<T>& DpS4, const V4<T>& DmN4,
+                                         T rEc, T rdx, T rdy, T dx, T dy, const Phys<T>& P,
+                                         T qn[4]) {
+  const T mEc = rs.y, mES = rs.z, mEN = rs.w;
+  T fW[4], fE[4], fS[4], fN[4], base[4];
+  unpack(rf[F_W], fW);
+  unpack(rf[F_E], fE);
+  unpack(rf[F_S], fS);
+  unpack(rf[F_N], fN);
+  unpack(base4, base);
+  T Ix[4], Iy[4];
+  interior_terms(fW, fE, fS, fN, base, mEc, mES, mEN, dax, day, dx, dy, P, Ix, Iy);
+  T xs[4], ys[4], DpW[4], DmE[4], DpS[4], DmN[4];
+  unpack(DpW4, DpW);
+  unpack(DmE4, DmE);
+  unpack(DpS4, DpS);
+  unpack(DmN4, DmN);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    xs[c] = DpW[c] + DmE[c] + Ix[c];
+    ys[c] = DpS[c] + DmN[c] + Iy[c];
+  }
+  if constexpr (DEV) {
+    // deviation form: m^f_new = m^f + dm - rho^E_c da (own level, own new alpha)
+    T dQ[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) dQ[c] = -rdx * xs[c] - rdy * ys[c];
+    qn[0] = qold[0] + (dQ[0] - rEc * dQ[3]);
+    qn[1] = qold[1] + dQ[1];
+    qn[2] = qold[2] + dQ[2];
+    qn[3] = qold[3] + dQ[3];
+    return qn[3] * rEc + qn[0];
+  } else {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) qn[c] = qold[c] - rdx * xs[c] - rdy * ys[c];
+    return qn[0];
+  }
+}
+
+}  // namespace tile
+}  // namespace fv

@@ -19,6 +19,7 @@ FV_OK, FV_EINVAL, FV_ENOMEM, FV_ECUDA, FV_ENONFINITE, FV_ETIMEOUT = range(6)
 FV_FP64, FV_FP32_DEV = 0, 1
 FV_BC_WALL, FV_BC_TRANSMISSIVE = 0, 1
 FV_XFACE_GL, FV_XFACE_OR = 0, 1
+FV_TILING_AUTO, FV_TILING_TILE, FV_TILING_STRIP = 0, 1, 2
 STATUS_NAMES = {0: "FV_OK", 1: "FV_EINVAL", 2: "FV_ENOMEM", 3: "FV_ECUDA",
                 4: "FV_ENONFINITE", 5: "FV_ETIMEOUT"}
 
@@ -114,6 +115,8 @@ _lib.fv_set_order.argtypes = [_H, C.c_int32]
 _lib.fv_set_order.restype = C.c_int
 _lib.fv_set_xface.argtypes = [_H, C.c_int32]
 _lib.fv_set_xface.restype = C.c_int
+_lib.fv_set_tiling.argtypes = [_H, C.c_int32]
+_lib.fv_set_tiling.restype = C.c_int
 _lib.fv_host_yface_o1.argtypes = [_D, _D, C.c_double, _D, C.c_double, C.c_double, C.c_double,
                                   _D, _D]
 _lib.fv_host_yface_o1.restype = C.c_int
@@ -131,7 +134,7 @@ ABI_SYMBOLS = ("fv_create", "fv_set_state", "fv_step", "fv_step_timed", "fv_get_
                "fv_batch_set_state", "fv_batch_step", "fv_batch_step_timed", "fv_batch_get_state",
                "fv_batch_get_diag", "fv_batch_size", "fv_batch_destroy", "fv_adjoint",
                "fv_host_adjoint_step", "fv_set_order", "fv_host_yface_o1",
-               "fv_host_xface_or", "fv_set_xface")
+               "fv_host_xface_or", "fv_set_xface", "fv_set_tiling")
 
 
 def _check(st):
@@ -230,6 +233,10 @@ def fv_set_order(h, order: int) -> None:
 
 def fv_set_xface(h, solver: int) -> None:
     _check(_lib.fv_set_xface(h, int(solver)))
+
+
+def fv_set_tiling(h, tiling: int) -> None:
+    _check(_lib.fv_set_tiling(h, int(tiling)))
 
 
 def fv_host_cell_ops() -> dict:
@@ -344,6 +351,11 @@ class Solver:
     def set_xface(self, solver: int) -> None:
         """x-face viscosity: FV_XFACE_GL (default) or FV_XFACE_OR (fv_set_xface)."""
         fv_set_xface(self.h, solver)
+
+    def set_tiling(self, tiling: int) -> None:
+        """Step-kernel staging: FV_TILING_AUTO (default), FV_TILING_TILE or
+        FV_TILING_STRIP (fv_set_tiling); the results are bitwise the same."""
+        fv_set_tiling(self.h, tiling)
 
     def step(self, n: int, cfl: float | None = None, want_time: bool = False):
         return fv_step(self.h, n, self.case.cfl if cfl is None else cfl, want_time)

@@ -1,0 +1,122 @@
+"""The two stagings of the second-order step (fv_set_tiling): the tile kernel
+(one CTA per 32 x 8 tile) and the strip kernel (one CTA per 32-column strip
+marching upwards, sharing reconstructed rows and y faces between its blocks)
+run the same cell and face arithmetic, so every output must agree bit for bit:
+the state, the simulated time, the levels K_i of the detector, the status.
+The strip kernel is the default, so the oracle parity tests of the other
+files pin it directly; this file carries that to the tile kernel.
+
+Cases span the strip kernel's edge conditions: heights that are not a multiple
+of the 8-row block or of the strip height, one-row and one-column grids,
+widths that are not a multiple of the 32-column strip, walls, solid obstacles
+touching the strip boundaries, transmissive sides, a free surface crossing
+the blocks, and both x-face solvers.
+"""
+import numpy as np
+import pytest
+
+from paper_1806_04960_gb300 import cases
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fv():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1806_04960_gb300 import build
+    build.build()
+    from paper_1806_04960_gb300 import fv as mod
+    return mod
+
+
+def run(fv, case, prec, tiling, n, xface=0, cfl=None):
+    s = fv.Solver(case, prec)
+    s.set_tiling(tiling)
+    s.set_xface(xface)
+    s.set_state(case.q)
+    t = s.step(n, case.cfl if cfl is None else cfl, want_time=True)
+    out = (s.get_state(), t, s.levels(), s.diag().status, s.diag().steps)
+    s.close()
+    return out
+
+
+def same(a, b):
+    qa, ta, Ka, sa, na = a
+    qb, tb, Kb, sb, nb = b
+    assert np.array_equal(qa, qb), np.abs(qa - qb).max()
+    assert ta == tb and sa == sb and na == nb
+    assert np.array_equal(Ka, Kb)
+
+
+def ragged(nx, ny, seed=3):
+    return cases.perturbed(cases.dambreak(nx, ny, lx=4.0 * nx / 128, ly=2.0 * ny / 64,
+                                          x_col=0.3 * nx / 32 + 0.01,
+                                          rects=[(2.5 * nx / 128, 2.7 * nx / 128, 0.0, 0.3 * ny / 64)]),
+                           seed)
+
+
+CASES = {
+    "c1": lambda: cases.c1(),
+    "ragged_45x13": lambda: ragged(45, 13),
+    "one_cell": lambda: ragged(1, 1),
+    "column_1x20": lambda: ragged(1, 20),
+    "row_33x1": lambda: ragged(33, 1),
+    "ragged_100x37": lambda: ragged(100, 37),
+    "ragged_257x203": lambda: ragged(257, 203, seed=7),
+    "transmissive": lambda: cases.riemann_x(150, rho_l=1010.0, rho_r=1000.0, u_l=0.5, u_r=-0.5, ny=5),
+    "lake_obstacles": lambda: cases.c2_lake(256, 128),
+    "c2_512x256": lambda: cases.c2(512, 256),
+    "drop_96": lambda: cases.drop(96),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("prec", ["FV_FP32_DEV", "FV_FP64"])
+def test_strip_equals_tile(fv, name, prec):
+    c = CASES[name]()
+    p = getattr(fv, prec)
+    n = 30 if c.nx * c.ny > 100000 else 60
+    a = run(fv, c, p, fv.FV_TILING_TILE, n)
+    b = run(fv, c, p, fv.FV_TILING_STRIP, n)
+    same(a, b)
+    assert a[3] == 0
+
+
+@pytest.mark.parametrize("prec", ["FV_FP32_DEV", "FV_FP64"])
+def test_strip_equals_tile_osher_romberg_x(fv, prec):
+    p = getattr(fv, prec)
+    for c in (cases.c1(), ragged(100, 37)):
+        same(run(fv, c, p, fv.FV_TILING_TILE, 40, xface=fv.FV_XFACE_OR),
+             run(fv, c, p, fv.FV_TILING_STRIP, 40, xface=fv.FV_XFACE_OR))
+
+
+def test_default_tiling_and_errors(fv):
+    """FV_TILING_AUTO is the strip kernel in both precisions; other values
+    are rejected."""
+    c = ragged(100, 37)
+    same(run(fv, c, fv.FV_FP32_DEV, fv.FV_TILING_AUTO, 20), run(fv, c, fv.FV_FP32_DEV, fv.FV_TILING_STRIP, 20))
+    same(run(fv, c, fv.FV_FP64, fv.FV_TILING_AUTO, 20), run(fv, c, fv.FV_FP64, fv.FV_TILING_STRIP, 20))
+    s = fv.Solver(c, fv.FV_FP32_DEV)
+    with pytest.raises(fv.FvError) as ei:
+        s.set_tiling(3)
+    assert ei.value.status == fv.FV_EINVAL
+    s.close()
+
+
+def test_adjoint_strip_equals_tile(fv):
+    """The adjoint's forward sweep and replays use the handle's staging; the
+    gradient is the same either way."""
+    c = cases.generic(cases.c5(64, 32), seed=11)
+    g = cases.c5_gauges(c)
+    target = np.repeat(c.q[0].ravel()[g][None, :] + 500.0, 30, axis=0)
+    out = []
+    for tiling in (fv.FV_TILING_TILE, fv.FV_TILING_STRIP):
+        s = fv.Solver(c, fv.FV_FP32_DEV)
+        s.set_tiling(tiling)
+        s.set_state(c.q)
+        grad, info, _ = s.adjoint(30, g, target, cfl=c.cfl)
+        out.append((grad, info.loss))
+        s.close()
+    assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
