@@ -146,12 +146,12 @@ def peaks():
 
 
 def recorded_traffic():
-    """DRAM bytes per step-kernel launch from the committed ncu record, if the
+    """DRAM bytes per strip-kernel launch from the committed ncu record, if the
     kernel sources still hash to the captured value; else None."""
     import hashlib
-    rec = os.path.join(ROOT, "profiles", "step_kernel_dram.txt")
+    rec = os.path.join(ROOT, "profiles", "strip_kernel_dram.txt")
     srcs = [os.path.join(ROOT, "paper_1806_04960_gb300", "csrc", f)
-            for f in ("fv_kernels.cu", "fv_model.cuh", "fv_consts.cuh")]
+            for f in ("fv_strip.cu", "fv_tile.cuh", "fv_model.cuh", "fv_consts.cuh")]
     if not os.path.exists(rec) or not all(os.path.exists(f) for f in srcs):
         return {}
     h = hashlib.sha256(b"".join(open(f, "rb").read() for f in srcs)).hexdigest()

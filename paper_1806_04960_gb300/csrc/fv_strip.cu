@@ -8,12 +8,14 @@
 // window rows are loaded, 8 rows (+ the ring columns) reconstructed and 8 rows
 // of y faces solved.  The window ring holds the 10 rows a block reads plus the
 // 8 the next block loads, so a block's load never waits for the previous
-// block's update.  With 320 threads every phase of a block is one pass:
+// block's update.  With 288 threads (FP32; 320 in FP64) every phase of a block
+// is one pass, apart from the faces:
 //
 //   load    rows j0+2 .. j0+9 of the window (288 cells, loads issued together)
 //   recon   rows j0+1 .. j0+8, 34 columns (272 cells)
-//   faces   x faces of rows j0 .. j0+7 (264; warps 0-8) and y faces above rows
-//           j0 .. j0+7 (256; warp 9, then warps 0-6), no warp holding both kinds
+//   faces   x faces of rows j0 .. j0+7 (264; warps 0-8), then y faces above
+//           rows j0 .. j0+7 (256; warps 0-7; with 320 threads warp 9 takes
+//           the first 32), no warp holding both kinds at once
 //   update  rows j0 .. j0+7 (256 cells)
 //
 // A prologue per strip loads rows jstart-2 .. jstart+1, reconstructs rows
@@ -34,7 +36,6 @@ using namespace tile;
 
 constexpr int SX = 32;          // strip width (cells)
 constexpr int BY = 8;           // rows per block
-constexpr int NTS = 320;        // threads per CTA (10 warps)
 constexpr int SWX = SX + 4;     // window columns: 2-cell halo on both sides
 constexpr int SRX = SX + 2;     // reconstructed columns: 1-cell ring
 constexpr int RING = 10;        // rows of the record and y-face rings
@@ -42,8 +43,13 @@ constexpr int WRING = 18;       // rows of the window ring
 constexpr int NXF = (SX + 1) * BY;  // x faces of a block
 constexpr int NYF = SX * BY;        // y faces of a block
 
-static_assert(BY * SWX <= NTS && BY * SRX <= NTS && NXF <= NTS, "one pass per phase");
-static_assert(NYF - (NTS - 9 * 32) <= 7 * 32, "y faces: warp 9, then warps 0-6");
+// Threads per CTA: 9 warps in FP32 (measured faster: every warp loads, and
+// at most one idles in a phase), 10 in FP64.
+template <typename T>
+__host__ __device__ constexpr int strip_threads() {
+  return sizeof(T) == 8 ? 320 : 288;
+}
+static_assert(BY * SWX <= 288 && BY * SRX <= 288 && NXF <= 288, "one pass per phase");
 
 template <typename T>
 struct StripSmem {
@@ -55,28 +61,32 @@ struct StripSmem {
   V4<T> Dy[2][RING][SX];       // D-, D+ of the y faces, by the row below the face
   T ga[2][RING][SX];           // limited alpha slopes
   unsigned long long col[BY][SX];
-  double wmax[NTS / 32];
+  double wmax[10];
   int K[SWX];                  // levels of the window columns
   unsigned char flag[WRING][SWX];
 };
 
 template <typename T, bool DEV, bool XOR>
-__global__ void __launch_bounds__(NTS, (sizeof(T) == 8 ? 1 : 3))
+__global__ void __launch_bounds__(strip_threads<T>(), (sizeof(T) == 8 ? 1 : 3))
     strip_kernel(StepParams p, KConsts<T> kc, const T* __restrict__ qin, T* __restrict__ qout,
                  const uint8_t* __restrict__ solid, const int32_t* __restrict__ Kref,
                  const int32_t* __restrict__ Kcur, unsigned long long* __restrict__ colsum,
                  DevScalars* __restrict__ sc, const T* __restrict__ rt, int H) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   StripSmem<T>& S = *reinterpret_cast<StripSmem<T>*>(smem_raw);
+  constexpr int NTS = strip_threads<T>();
+  constexpr int YF0 = NTS - 9 * 32;  // y faces taken by the warps past the x faces' nine
   const int t = threadIdx.x;
   const int nx = p.nx, ny = p.ny;
   const size_t N = (size_t)nx * ny;
   const int i0 = blockIdx.x * SX;
   const int jstart = blockIdx.y * H;
   const int jend = min(jstart + H, ny);
-  const int r0 = jstart - 2;  // first window row; every ring is indexed from it
-  auto wslot = [&](int r) -> int { return (r - r0) % WRING; };
-  auto slot = [&](int r) -> int { return (r - r0) % RING; };
+  // Row r sits in window slot wslot(r) = (r - jstart + 2) mod WRING and in
+  // record / y-face slot slot(r) = (r - jstart + 2) mod RING.  Slots are
+  // carried as a base plus an offset, wrapped by one compare and subtract.
+  auto wwrap = [](int x) -> int { return x >= WRING ? x - WRING : x; };
+  auto rwrap = [](int x) -> int { return x >= RING ? x - RING : x; };
 
   const Phys<T>& P = kc.P;
   const Sides sd = sides_of(p);
@@ -87,20 +97,24 @@ __global__ void __launch_bounds__(NTS, (sizeof(T) == 8 ? 1 : 3))
   ReconConsts<T> RC = kc.R;
   RC.half_dt = T(0.5) * dt;
 
-  auto load_rows = [&](int ra, int nrows) {
+  // rows ra .. ra+nrows-1; wa = wslot(ra)
+  auto load_rows = [&](int ra, int wa, int nrows) {
     for (int idx = t; idx < nrows * SWX; idx += NTS) {
-      const int rr = ra + idx / SWX, wi = idx % SWX;
-      const int s = wslot(rr);
+      const int k = idx / SWX, wi = idx % SWX;
+      const int rr = ra + k;
+      const int s = wwrap(wa + k);
       S.flag[s][wi] = load_cell<T, DEV>(qin, solid, Kref, Kcur, rt, nx, ny, N, i0 - 2 + wi, rr,
                                         S.w[s][wi]);
     }
   };
-  auto recon_rows = [&](int ra, int nrows) {
+  // rows ra .. ra+nrows-1; wa = wslot(ra - 1), sa = slot(ra)
+  auto recon_rows = [&](int ra, int wa, int sa, int nrows) {
     for (int idx = t; idx < nrows * SRX; idx += NTS) {
-      const int rr = ra + idx / SRX, rx = idx % SRX, wi = rx + 1;
-      const int ws = wslot(rr);
+      const int k = idx / SRX, rx = idx % SRX, wi = rx + 1;
+      const int rr = ra + k;
+      const int ws = wwrap(wa + k + 1);
       if (S.flag[ws][wi] != F_FLUID) continue;
-      const int s = slot(rr), sS = wslot(rr - 1), sN = wslot(rr + 1);
+      const int s = rwrap(sa + k), sS = wwrap(wa + k), sN = wwrap(wa + k + 2);
       V4<T> rs, rf[4];
       T base[4], ga[2];
       recon_cell<T, DEV>(S.w[sS], S.w[ws], S.w[sN], S.flag[sS], S.flag[ws], S.flag[sN], S.K, wi,
@@ -115,11 +129,12 @@ __global__ void __launch_bounds__(NTS, (sizeof(T) == 8 ? 1 : 3))
       }
     }
   };
-  // y face between rows rB and rB + 1 of strip column fx
-  auto yface_at = [&](int rB, int fx) {
-    const int rx = fx + 1, sB = slot(rB), sT = slot(rB + 1);
+  // y face between rows rB and rB + 1 of strip column fx; wB = wslot(rB),
+  // sB = slot(rB)
+  auto yface_at = [&](int rB, int wB, int sB, int fx) {
+    const int rx = fx + 1, sT = rwrap(sB + 1), wT = wwrap(wB + 1);
     T Dm[4], Dp[4];
-    y_face<T>(S.flag[wslot(rB)][rx + 1], S.flag[wslot(rB + 1)][rx + 1], &S.rs[sB][rx], &S.rf[F_N][sB][rx],
+    y_face<T>(S.flag[wB][rx + 1], S.flag[wT][rx + 1], &S.rs[sB][rx], &S.rf[F_N][sB][rx],
               &S.rs[sT][rx], &S.rf[F_S][sT][rx], S.K[rx + 1], rB + 1, rt, ny, sd, P, Dm, Dp);
     S.Dy[0][sB][fx] = pack(Dm);
     S.Dy[1][sB][fx] = pack(Dp);
@@ -130,11 +145,11 @@ __global__ void __launch_bounds__(NTS, (sizeof(T) == 8 ? 1 : 3))
     const int gi = i0 - 2 + idx;
     S.K[idx] = (gi >= 0 && gi < nx) ? Kcur[gi] : 0;
   }
-  load_rows(jstart - 2, 4);
+  load_rows(jstart - 2, 0, 4);
   __syncthreads();
-  recon_rows(jstart - 1, 2);
+  recon_rows(jstart - 1, 0, 1, 2);
   __syncthreads();
-  if (t < SX) yface_at(jstart - 1, t);
+  if (t < SX) yface_at(jstart - 1, 1, 1, t);
 
   T my_rate = T(0);
   unsigned long long my_w = 0;
@@ -142,35 +157,38 @@ __global__ void __launch_bounds__(NTS, (sizeof(T) == 8 ? 1 : 3))
   const int ux = t % SX, uy = t / SX;  // update: column and row in the block (t < 256)
   const int gi_me = i0 + ux;
 
-  for (int j0 = jstart; j0 < jend; j0 += BY) {
+  // slots of row j0 in the window ring and in the record ring
+  int wb = 2, sb = 2;
+  for (int j0 = jstart; j0 < jend; j0 += BY, wb = wwrap(wb + BY), sb = rwrap(sb + BY)) {
     // ---------------------------------------------------------- load
-    load_rows(j0 + 2, BY);
+    load_rows(j0 + 2, wwrap(wb + 2), BY);
     __syncthreads();
     // ---------------------------------------------------------- recon
-    recon_rows(j0 + 1, BY);
+    recon_rows(j0 + 1, wb, rwrap(sb + 1), BY);
     __syncthreads();
     // ---------------------------------------------------------- faces
     if (t < NXF) {
       const int fx = t % (SX + 1), fy = t / (SX + 1);
-      const int s = slot(j0 + fy), ws = wslot(j0 + fy);
+      const int s = rwrap(sb + fy), ws = wwrap(wb + fy);
       T Dm[4], Dp[4];
       x_face<T, XOR>(S.flag[ws][fx + 1], S.flag[ws][fx + 2], &S.rs[s][fx], &S.rf[F_E][s][fx],
                      &S.rs[s][fx + 1], &S.rf[F_W][s][fx + 1], sd, P, Dm, Dp);
       S.Dx[0][fy][fx] = pack(Dm);
       S.Dx[1][fy][fx] = pack(Dp);
-    } else if (t >= 9 * 32) {
-      const int k = t - 9 * 32;
-      yface_at(j0 + k / SX, k % SX);
+    } else if (YF0 > 0 && t >= 9 * 32) {
+      const int k = t - 9 * 32, fy = k / SX;
+      yface_at(j0 + fy, wwrap(wb + fy), rwrap(sb + fy), k % SX);
     }
-    if (t < NYF - (NTS - 9 * 32)) {
-      const int k = t + (NTS - 9 * 32);
-      yface_at(j0 + k / SX, k % SX);
+    if (t < NYF - YF0) {
+      const int k = t + YF0, fy = k / SX;
+      yface_at(j0 + fy, wwrap(wb + fy), rwrap(sb + fy), k % SX);
     }
     __syncthreads();
     // ---------------------------------------------------------- update
     if (t < SX * BY) {
       const int r = j0 + uy;
-      const int s = slot(r), ws = wslot(r);
+      const int s = rwrap(sb + uy), ws = wwrap(wb + uy);
+      const int sbelow = s == 0 ? RING - 1 : s - 1;  // slot of row r - 1
       const bool inside = gi_me < nx && r < ny;
       const unsigned char flag_me = S.flag[ws][ux + 2];
       if (inside && flag_me == F_FLUID) {
@@ -183,7 +201,7 @@ __global__ void __launch_bounds__(NTS, (sizeof(T) == 8 ? 1 : 3))
         T qn[4];
         const T m_full = update_cell<T, DEV>(qold, S.rs[s][ux + 1], rf, S.base[s][ux],
                                              S.ga[0][s][ux], S.ga[1][s][ux], S.Dx[1][uy][ux],
-                                             S.Dx[0][uy][ux + 1], S.Dy[1][slot(r - 1)][ux],
+                                             S.Dx[0][uy][ux + 1], S.Dy[1][sbelow][ux],
                                              S.Dy[0][s][ux], rEc, rdx, rdy, dx, dy, P, qn);
         const size_t c = (size_t)r * nx + gi_me;
 #pragma unroll
@@ -231,6 +249,7 @@ template <typename T, bool DEV, bool XOR>
 void launch_strip_xt(const StepParams& p, const T* in, T* out, const uint8_t* solid,
                      const int32_t* Kref, const int32_t* Kcur, unsigned long long* colsum,
                      DevScalars* sc, const T* rt, cudaStream_t st) {
+  constexpr int NTS = strip_threads<T>();
   const size_t smem = sizeof(StripSmem<T>);
   static int resident = 0;
   if (!resident) {
