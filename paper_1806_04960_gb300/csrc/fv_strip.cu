@@ -11,7 +11,9 @@
 // block's update.  With 288 threads (FP32; 320 in FP64) every phase of a block
 // is one pass, apart from the faces:
 //
-//   load    rows j0+2 .. j0+9 of the window (288 cells, loads issued together)
+//   load    rows j0+2 .. j0+9 of the window (288 cells): their global loads
+//           were issued by the previous block before its faces phase and are
+//           only stored here (the first block of a strip loads directly)
 //   recon   rows j0+1 .. j0+8, 34 columns (272 cells)
 //   faces   x faces of rows j0 .. j0+7 (264; warps 0-8), then y faces above
 //           rows j0 .. j0+7 (256; warps 0-7; with 320 threads warp 9 takes
@@ -157,16 +159,31 @@ __global__ void __launch_bounds__(strip_threads<T>(), (sizeof(T) == 8 ? 1 : 3))
   const int ux = t % SX, uy = t / SX;  // update: column and row in the block (t < 256)
   const int gi_me = i0 + ux;
 
+  // the next block's window cell of this thread (t < 288), loaded one block
+  // ahead: cell (pwi, pk) of its 8 new rows
+  CellLoad<T> pre{};
+  const int pk = t / SWX, pwi = t % SWX;
+
   // slots of row j0 in the window ring and in the record ring
   int wb = 2, sb = 2;
   for (int j0 = jstart; j0 < jend; j0 += BY, wb = wwrap(wb + BY), sb = rwrap(sb + BY)) {
     // ---------------------------------------------------------- load
-    load_rows(j0 + 2, wwrap(wb + 2), BY);
+    if (j0 == jstart) {
+      load_rows(j0 + 2, wwrap(wb + 2), BY);
+    } else if (t < BY * SWX) {
+      const int s = wwrap(wwrap(wb + 2) + pk);
+      S.flag[s][pwi] = commit_cell<T, DEV>(pre, rt, ny, j0 + 2 + pk, S.w[s][pwi]);
+    }
     __syncthreads();
     // ---------------------------------------------------------- recon
     recon_rows(j0 + 1, wb, rwrap(sb + 1), BY);
     __syncthreads();
     // ---------------------------------------------------------- faces
+    // (in a strip's last block a fetch of row -1, which loads nothing: every
+    // block then defines the registers, so they are not live across a block)
+    if (NTS == BY * SWX || t < BY * SWX)
+      fetch_cell<T, DEV>(qin, solid, Kref, Kcur, nx, ny, N, i0 - 2 + pwi,
+                         j0 + BY < jend ? j0 + BY + 2 + pk : -1, pre);
     if (t < NXF) {
       const int fx = t % (SX + 1), fy = t / (SX + 1);
       const int s = rwrap(sb + fy), ws = wwrap(wb + fy);

@@ -53,10 +53,58 @@ __device__ __forceinline__ Sides sides_of(const StepParams& p) {
   return Sides{p.side[0] == 1, p.side[1] == 1, p.side[2] == 1, p.side[3] == 1};
 }
 
-// Window cell (gi, gj): its flag and, if fluid, its state (m, mu, mv, a).  All
-// loads of an in-domain cell are issued together (the state arrays hold zeros
-// in solid cells).  In deviation form m^f is re-based from the level it was
-// stored with (Kref) to this step's level (Kcur) of its column.
+// Raw global loads of one window cell (gi, gj), issued together (the state
+// arrays hold zeros in solid cells), so that they can be started a phase
+// before they are used.
+template <typename T>
+struct CellLoad {
+  T m, mu, mv, a;
+  int Kr, Kc;  // levels the column was stored with / of this step (deviation form)
+  uint8_t solid;
+  bool in;  // inside the domain
+};
+
+template <typename T, bool DEV>
+__device__ __forceinline__ void fetch_cell(const T* __restrict__ qin,
+                                           const uint8_t* __restrict__ solid,
+                                           const int32_t* __restrict__ Kref,
+                                           const int32_t* __restrict__ Kcur, int nx, int ny,
+                                           size_t N, int gi, int gj, CellLoad<T>& L) {
+  L.in = gi >= 0 && gj >= 0 && gi < nx && gj < ny;
+  if (!L.in) {  // every field defined on every path: no live range spans two fetches
+    L.m = L.mu = L.mv = L.a = T(0);
+    L.Kr = L.Kc = 0;
+    L.solid = 0;
+    return;
+  }
+  const size_t c = (size_t)gj * nx + gi;
+  L.solid = solid[c];
+  L.m = qin[c];
+  L.mu = qin[N + c];
+  L.mv = qin[2 * N + c];
+  L.a = qin[3 * N + c];
+  if (DEV) {
+    L.Kr = Kref[gi];
+    L.Kc = Kcur[gi];
+  }
+}
+
+// The cell's flag and, if fluid, its state (m, mu, mv, a) into w.  In
+// deviation form m^f is re-based from the level it was stored with (Kref) to
+// this step's level (Kcur) of its column; gj is the cell's grid row.
+template <typename T, bool DEV>
+__device__ __forceinline__ unsigned char commit_cell(const CellLoad<T>& L,
+                                                     const T* __restrict__ rt, int ny, int gj,
+                                                     V4<T>& w) {
+  if (!L.in) return F_OUT;
+  if (L.solid) return F_SOLID;
+  T m = L.m;
+  if (DEV && L.Kr != L.Kc)
+    m += L.a * (tab(rt, 2 * (gj - L.Kr) + 1, ny) - tab(rt, 2 * (gj - L.Kc) + 1, ny));
+  w = V4<T>{m, L.mu, L.mv, L.a};
+  return F_FLUID;
+}
+
 template <typename T, bool DEV>
 __device__ __forceinline__ unsigned char load_cell(const T* __restrict__ qin,
                                                    const uint8_t* __restrict__ solid,
@@ -64,21 +112,9 @@ __device__ __forceinline__ unsigned char load_cell(const T* __restrict__ qin,
                                                    const int32_t* __restrict__ Kcur,
                                                    const T* __restrict__ rt, int nx, int ny,
                                                    size_t N, int gi, int gj, V4<T>& w) {
-  if (gi < 0 || gj < 0 || gi >= nx || gj >= ny) return F_OUT;
-  const size_t c = (size_t)gj * nx + gi;
-  const uint8_t s = solid[c];
-  T m = qin[c];
-  const T mu = qin[N + c], mv = qin[2 * N + c], a = qin[3 * N + c];
-  int Kr = 0, Kc = 0;
-  if (DEV) {
-    Kr = Kref[gi];
-    Kc = Kcur[gi];
-  }
-  if (s) return F_SOLID;
-  // re-base m^f from the level it was stored with to this step's level
-  if (DEV && Kr != Kc) m += a * (tab(rt, 2 * (gj - Kr) + 1, ny) - tab(rt, 2 * (gj - Kc) + 1, ny));
-  w = V4<T>{m, mu, mv, a};
-  return F_FLUID;
+  CellLoad<T> L;
+  fetch_cell<T, DEV>(qin, solid, Kref, Kcur, nx, ny, N, gi, gj, L);
+  return commit_cell<T, DEV>(L, rt, ny, gj, w);
 }
 
 // Reconstruction of one cell (Section 3.4): fluctuations of the cell and its
