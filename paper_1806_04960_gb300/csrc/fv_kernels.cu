@@ -269,14 +269,18 @@ __global__ void batch_prepare_kernel(const BatchDomain<T>* __restrict__ doms, in
 }
 
 // ----------------------------------------------------------------------------
-__global__ void finalize_kernel(StepParams p, int32_t* Kref, int32_t* Kcur,
-                                unsigned long long* colsum, DevScalars* sc, int count_step) {
-  for (int i = threadIdx.x; i < p.nx; i += blockDim.x) {
-    Kref[i] = Kcur[i];
-    Kcur[i] = level_of(colsum[i], p.ny);
+// One thread per column over the grid; the scalars in block 0.
+__global__ void finalize_kernel(StepParams p, int32_t* __restrict__ Kref, int32_t* __restrict__ Kcur,
+                                unsigned long long* __restrict__ colsum,
+                                DevScalars* __restrict__ sc, int count_step) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p.nx; i += gridDim.x * blockDim.x) {
+    const unsigned long long cs = colsum[i];
+    const int32_t k = Kcur[i];
     colsum[i] = 0ull;
+    Kref[i] = k;
+    Kcur[i] = level_of(cs, p.ny);
   }
-  if (threadIdx.x == 0) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (count_step) {
       const double dt = sc->rate_cur > 0.0 ? p.cfl / sc->rate_cur : 0.0;
       sc->t += dt;
@@ -548,7 +552,9 @@ void launch_step_f32(const StepParams& p, const StateF32& s, const uint8_t* soli
 void launch_finalize(const StepParams& p, int32_t* Kref, int32_t* Kcur,
                      unsigned long long* colsum, DevScalars* sc, int count_step,
                      cudaStream_t st) {
-  finalize_kernel<<<1, 1024, 0, st>>>(p, Kref, Kcur, colsum, sc, count_step);
+  int blocks = (p.nx + 255) / 256;
+  if (blocks > 152) blocks = 152;
+  finalize_kernel<<<blocks, 256, 0, st>>>(p, Kref, Kcur, colsum, sc, count_step);
 }
 
 void launch_prepare(double cfl, DevScalars* sc, cudaStream_t st) {
