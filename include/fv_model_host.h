@@ -36,6 +36,15 @@ int fv_host_yface(const double* model, const double* qm, const double* qp, doubl
 int fv_host_xface_or(const double* model, const double* qm, const double* qp, double* Dm,
                      double* Dp);
 
+/* fv_host_face_f32: D-, D+ of an x face (which = 0, Gauss-Legendre Osher) or a
+ * y face (which = 1, well-balanced Osher-Romberg with the alpha p jump of the
+ * two states) in FP32: the states are rounded to float and the float solver
+ * runs either in the paired form the FP32 step kernels use (paired = 1, two
+ * quadrature nodes or Romberg terms per float2 operation) or in the scalar
+ * form (paired = 0).  model as for fv_host_xface; outputs widened to double.
+ * Returns 1 for a null pointer or another `which`, else 0. */
+int fv_host_face_f32(int which, const double* model, const double* qm, const double* qp,
+                     int paired, double* Dm, double* Dp);
 /* fv_host_yface_o1: D-, D+ of the first-order y face (Sections 3.2-3.3)
  * between the centre of a lower cell at height ya above the level and an upper
  * one dy higher: fa, fb = fluctuations (alpha rho - alpha^E rho^E, alpha rho u,

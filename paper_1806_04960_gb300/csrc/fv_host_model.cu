@@ -45,6 +45,39 @@ extern "C" int fv_host_yface(const double* model, const double* qm, const double
   return 0;
 }
 
+extern "C" int fv_host_face_f32(int which, const double* model, const double* qm,
+                                const double* qp, int paired, double* Dm, double* Dp) {
+  if (!model || !qm || !qp || !Dm || !Dp || which < 0 || which > 1) return 1;
+  const fv::Phys<double> Pd = phys(model);
+  fv::Phys<float> P;
+  P.c = (float)Pd.c;
+  P.c2 = (float)Pd.c2;
+  P.inv_c = (float)Pd.inv_c;
+  P.rho0 = (float)Pd.rho0;
+  P.k0 = (float)Pd.k0;
+  P.g = (float)Pd.g;
+  P.kappa = (float)Pd.kappa;
+  float a[4], b[4], dq[4], m[4], p[4];
+  for (int c = 0; c < 4; ++c) {
+    a[c] = (float)qm[c];
+    b[c] = (float)qp[c];
+    dq[c] = b[c] - a[c];
+  }
+  if (which == 0) {
+    if (paired) fv::xface_f2(a, b, dq, P, m, p);
+    else fv::xface_scalar<float>(a, b, dq, P, m, p);
+  } else {
+    const float dap = P.c2 * (dq[0] - P.rho0 * dq[3]);
+    if (paired) fv::yface_f2(a, b, dq, dap, P, m, p);
+    else fv::yface_scalar<float>(a, b, dq, dap, P, m, p);
+  }
+  for (int c = 0; c < 4; ++c) {
+    Dm[c] = m[c];
+    Dp[c] = p[c];
+  }
+  return 0;
+}
+
 extern "C" int fv_host_yface_o1(const double* model, const double* fa, double aEa,
                                 const double* fb, double aEb, double ya, double dy, double* Dm,
                                 double* Dp) {

@@ -12,6 +12,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+#include <type_traits>
+
 namespace fv {
 
 template <typename T>
@@ -57,6 +60,17 @@ __host__ __device__ __forceinline__ Vel<T> velocity(T m, T mu, T mv) {
   return {mu * r, mv * r};
 }
 
+// Paired FP32 forms of the face solvers (two evaluations of the same
+// arithmetic in the two lanes of float2, one instruction per pair on sm_100
+// and later); defined at the end of this file, used by xface and yface in
+// FP32 device code.
+__host__ __device__ __forceinline__ void xface_f2(const float qm[4], const float qp[4],
+                                                  const float dq[4], const Phys<float>& P,
+                                                  float Dm[4], float Dp[4]);
+__host__ __device__ __forceinline__ void yface_f2(const float qm[4], const float qp[4],
+                                                  const float dq[4], float dap,
+                                                  const Phys<float>& P, float Dm[4], float Dp[4]);
+
 // ---------------------------------------------------------------------------
 // x faces: Osher viscosity, Eq. (OsherMatrixFormal_approx): 3-point
 // Gauss-Legendre quadrature of |A1(Psi(s))| dq on the segment path, with
@@ -66,8 +80,8 @@ __host__ __device__ __forceinline__ Vel<T> velocity(T m, T mu, T mv) {
 // the caller.
 // ---------------------------------------------------------------------------
 template <typename T>
-__host__ __device__ __forceinline__ void xface(const T qm[4], const T qp[4], const T dq[4],
-                                               const Phys<T>& P, T Dm[4], T Dp[4]) {
+__host__ __device__ __forceinline__ void xface_scalar(const T qm[4], const T qp[4], const T dq[4],
+                                                      const Phys<T>& P, T Dm[4], T Dp[4]) {
   const T s_gl[3] = {T(0.5 - 0.38729833462074168852), T(0.5), T(0.5 + 0.38729833462074168852)};
   const T w_gl[3] = {T(5.0 / 18.0), T(8.0 / 18.0), T(5.0 / 18.0)};
   T V0 = 0, V1 = 0, V2 = 0, V3 = 0, ubar = 0;
@@ -228,8 +242,8 @@ __host__ __device__ __forceinline__ void sign_A2(T u, T v, const T r[4], const P
 // dap: jump of alpha p = c2 (m - rho0 alpha) from qm to qp, formed by the
 // caller so that it is exactly zero between two states of one rest profile.
 template <typename T>
-__host__ __device__ __forceinline__ void yface(const T qm[4], const T qp[4], const T dq[4],
-                                               T dap, const Phys<T>& P, T Dm[4], T Dp[4]) {
+__host__ __device__ __forceinline__ void yface_scalar(const T qm[4], const T qp[4], const T dq[4],
+                                                      T dap, const Phys<T>& P, T Dm[4], T Dp[4]) {
   // nodes s = 0, 1/4, 1/2, 3/4, 1 (interior nodes on the path, exact endpoints)
   T mu_[5], mv_[5], u_[5], v_[5];
 #pragma unroll
@@ -425,6 +439,215 @@ __host__ __device__ __forceinline__ void interior_terms(const T fW[4], const T f
   Iy[2] = (fN[2] * vN.v - fS[2] * vS.v) + P.c2 * ((fN[0] - fS[0]) - P.rho0 * (fN[3] - fS[3])) +
           P.g * dy * base[0];
   Iy[3] = dy * vc.v * day;
+}
+
+// ---------------------------------------------------------------------------
+// Paired FP32 arithmetic: each helper applies one IEEE operation (rounded to
+// nearest) to both lanes; on the device one paired instruction, on the host
+// two scalar ones with the same results.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+__host__ __device__ __forceinline__ float2 add2(float2 a, float2 b) {
+#ifdef __CUDA_ARCH__
+  return __fadd2_rn(a, b);
+#else
+  return make_float2(a.x + b.x, a.y + b.y);
+#endif
+}
+__host__ __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  return add2(a, make_float2(-b.x, -b.y));
+}
+__host__ __device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+#ifdef __CUDA_ARCH__
+  return __fmul2_rn(a, b);
+#else
+  return make_float2(a.x * b.x, a.y * b.y);
+#endif
+}
+__host__ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+#ifdef __CUDA_ARCH__
+  return __ffma2_rn(a, b, c);
+#else
+  return make_float2(std::fma(a.x, b.x, c.x), std::fma(a.y, b.y, c.y));
+#endif
+}
+__host__ __device__ __forceinline__ float2 abs2(float2 a) {
+  return make_float2(tabs(a.x), tabs(a.y));
+}
+__host__ __device__ __forceinline__ float2 sgn2(float2 a) { return make_float2(sgn(a.x), sgn(a.y)); }
+__host__ __device__ __forceinline__ float2 rcp2(float2 a) { return make_float2(rcp(a.x), rcp(a.y)); }
+
+// One Gauss-Legendre node of xface on float2 lanes: node velocity (u, v) and
+// its contributions (r0, u r0 + c (a5 - a1), v Pk + |u| w2, |u| d4, u).
+struct XNode2 {
+  float2 V0, V1, V2, V3, u;
+};
+__host__ __device__ __forceinline__ XNode2 xnode2(float2 u, float2 v, const float dq[4], float dr,
+                                                 float w1c, float w5c, float B,
+                                                 const Phys<float>& P) {
+  // w1 = ((1 + uc) d1 - d2 / c - rho0 d4) / 2 and w5 = ((1 - uc) d1 + d2 / c - rho0 d4) / 2
+  // as (w1c + uc d1 / 2), (w5c - uc d1 / 2); w2 = d3 - v dr
+  const float2 uh = mul2(u, bc2(0.5f * P.inv_c * dq[0]));
+  const float2 w1 = add2(bc2(w1c), uh);
+  const float2 w5 = sub2(bc2(w5c), uh);
+  const float2 w2 = fma2(v, bc2(-dr), bc2(dq[2]));
+  const float2 l1 = abs2(add2(u, bc2(-P.c))), l5 = abs2(add2(u, bc2(P.c))), la = abs2(u);
+  const float2 a1 = mul2(l1, w1), a5 = mul2(l5, w5);
+  const float2 Pk = add2(a1, a5);
+  const float2 r0 = fma2(la, bc2(B), Pk);
+  XNode2 o;
+  o.V0 = r0;
+  o.V1 = fma2(u, r0, mul2(bc2(P.c), sub2(a5, a1)));
+  o.V2 = fma2(v, Pk, mul2(la, w2));
+  o.V3 = mul2(la, bc2(dq[3]));
+  o.u = u;
+  return o;
+}
+
+// xface in FP32 with the Gauss-Legendre nodes s0 and s2 (equal weights 5/18)
+// in the two lanes and the middle node s1 = 1/2 (weight 8/18) in the first
+// lane of a second call; the endpoint velocities of qm and qp as a pair.
+__host__ __device__ __forceinline__ void xface_f2(const float qm[4], const float qp[4],
+                                                  const float dq[4], const Phys<float>& P,
+                                                  float Dm[4], float Dp[4]) {
+  const float h = 0.38729833462074168852f;
+  const float dr = dq[0] - P.rho0 * dq[3];
+  const float B = P.rho0 * dq[3];
+  const float A = dq[1] * P.inv_c;
+  const float w1c = 0.5f * ((dq[0] - A) - B), w5c = 0.5f * ((dq[0] + A) - B);
+  // nodes s0, s2 | s1 and the endpoints qm, qp: one velocity evaluation each
+  const float2 s02 = make_float2(0.5f - h, 0.5f + h);
+  const float2 m02 = fma2(s02, bc2(dq[0]), bc2(qm[0]));
+  const float2 mu02 = fma2(s02, bc2(dq[1]), bc2(qm[1]));
+  const float2 mv02 = fma2(s02, bc2(dq[2]), bc2(qm[2]));
+  const float m1 = qm[0] + 0.5f * dq[0], mu1 = qm[1] + 0.5f * dq[1], mv1 = qm[2] + 0.5f * dq[2];
+  const float2 r02 = rcp2(m02);
+  const float2 rmp = rcp2(make_float2(qm[0], qp[0]));
+  const float2 r1e = make_float2(rcp(m1), 0.0f);
+  const float2 u02 = mul2(mu02, r02), v02 = mul2(mv02, r02);
+  const float2 mu1e = make_float2(mu1, 0.0f), mv1e = make_float2(mv1, 0.0f);
+  const float2 u1 = mul2(mu1e, r1e), v1 = mul2(mv1e, r1e);
+  const XNode2 a = xnode2(u02, v02, dq, dr, w1c, w5c, B, P);
+  const XNode2 b = xnode2(u1, v1, dq, dr, w1c, w5c, B, P);
+  const float ws = 5.0f / 18.0f, wm = 8.0f / 18.0f;
+  const float V0 = ws * (a.V0.x + a.V0.y) + wm * b.V0.x;
+  const float V1 = ws * (a.V1.x + a.V1.y) + wm * b.V1.x;
+  const float V2 = ws * (a.V2.x + a.V2.y) + wm * b.V2.x;
+  const float V3 = ws * (a.V3.x + a.V3.y) + wm * b.V3.x;
+  const float ubar = ws * (a.u.x + a.u.y) + wm * b.u.x;
+  // endpoint fluxes: (qm1 um, qp1 up) and (qm1 vm, qp1 vp)
+  const float2 mu_mp = make_float2(qm[1], qp[1]);
+  const float2 uv_u = mul2(mu_mp, rmp);                              // (um, up)
+  const float2 uv_v = mul2(make_float2(qm[2], qp[2]), rmp);          // (vm, vp)
+  const float2 f1 = mul2(mu_mp, uv_u), f2 = mul2(mu_mp, uv_v);
+  const float F[4] = {dq[1], (f1.y - f1.x) + P.c2 * dr, f2.y - f2.x, ubar * dq[3]};
+  const float V[4] = {V0, V1, V2, V3};
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const float2 d = mul2(bc2(0.5f), add2(bc2(F[c]), make_float2(-V[c], V[c])));
+    Dm[c] = d.x;
+    Dp[c] = d.y;
+  }
+}
+
+// sign_A2 on float2 lanes (closed form of sign_A2).
+__host__ __device__ __forceinline__ void sign_A2_f2(float2 u, float2 v, const float2 r[4],
+                                                    const Phys<float>& P, float2 out[4]) {
+  const float2 vc = mul2(v, bc2(P.inv_c));
+  const float2 rr = mul2(bc2(P.rho0), r[3]);
+  const float2 half = bc2(0.5f);
+  // w1 = ((1 + vc) r0 - r2 / c - rho0 r3) / 2, w5 = ((1 - vc) r0 + r2 / c - rho0 r3) / 2
+  const float2 r2c = mul2(r[2], bc2(P.inv_c));
+  const float2 vr0 = mul2(vc, r[0]);
+  const float2 base = sub2(r[0], rr);
+  const float2 w1 = mul2(half, add2(sub2(base, r2c), vr0));
+  const float2 w5 = mul2(half, sub2(add2(base, r2c), vr0));
+  const float2 w2 = fma2(make_float2(-u.x, -u.y), base, r[1]);
+  const float2 s1 = sgn2(add2(v, bc2(-P.c))), s5 = sgn2(add2(v, bc2(P.c))), s3 = sgn2(v);
+  const float2 a1 = mul2(s1, w1), a5 = mul2(s5, w5);
+  const float2 Pk = add2(a1, a5);
+  const float2 srho = mul2(s3, rr);
+  out[0] = add2(Pk, srho);
+  out[1] = fma2(u, Pk, mul2(s3, w2));
+  out[2] = fma2(v, add2(Pk, srho), mul2(bc2(P.c), sub2(a5, a1)));
+  out[3] = mul2(s3, r[3]);
+}
+
+// yface in FP32: the two half-segment terms of the Osher-Romberg sum (nodes
+// 1/4 and 3/4, weight 4/3) in the two lanes, the whole-segment term (node
+// 1/2, weight -1/3) in the first lane of a second call; the endpoint
+// velocities of qm and qp as a pair.
+__host__ __device__ __forceinline__ void yface_f2(const float qm[4], const float qp[4],
+                                                  const float dq[4], float dap,
+                                                  const Phys<float>& P, float Dm[4], float Dp[4]) {
+  const float2 s13 = make_float2(0.25f, 0.75f);
+  const float2 m13 = fma2(s13, bc2(dq[0]), bc2(qm[0]));
+  const float2 mu13 = fma2(s13, bc2(dq[1]), bc2(qm[1]));
+  const float2 mv13 = fma2(s13, bc2(dq[2]), bc2(qm[2]));
+  const float m2 = qm[0] + 0.5f * dq[0], mu2 = qm[1] + 0.5f * dq[1], mv2 = qm[2] + 0.5f * dq[2];
+  const float2 r13 = rcp2(m13);
+  const float2 r04 = rcp2(make_float2(qm[0], qp[0]));
+  const float r2_ = rcp(m2);
+  const float2 u13 = mul2(mu13, r13), v13 = mul2(mv13, r13);
+  const float u2 = mu2 * r2_, v2 = mv2 * r2_;
+  const float2 mu04 = make_float2(qm[1], qp[1]), mv04 = make_float2(qm[2], qp[2]);
+  const float2 v04 = mul2(mv04, r04);
+  // g = (mv, mu v, mv v) at the nodes 0, 4 (pair) and 2
+  const float2 g1_04 = mul2(mu04, v04), g2_04 = mul2(mv04, v04);
+  const float g1_2 = mu2 * v2, g2_2 = mv2 * v2;
+  const float hd = 0.5f * dap;
+  // half segments [0, 1/2] (lane x) and [1/2, 1] (lane y)
+  float2 rh[4];
+  rh[0] = bc2(0.5f * dq[2]);
+  rh[1] = sub2(make_float2(g1_2, g1_04.y), make_float2(g1_04.x, g1_2));
+  rh[2] = add2(sub2(make_float2(g2_2, g2_04.y), make_float2(g2_04.x, g2_2)), bc2(hd));
+  rh[3] = mul2(v13, bc2(0.5f * dq[3]));
+  float2 oh[4];
+  sign_A2_f2(u13, v13, rh, P, oh);
+  // whole segment (lane x)
+  const float G1 = g1_04.y - g1_04.x, G2 = (g2_04.y - g2_04.x) + dap;
+  float2 rw[4];
+  rw[0] = make_float2(dq[2], 0.0f);
+  rw[1] = make_float2(G1, 0.0f);
+  rw[2] = make_float2(G2, 0.0f);
+  rw[3] = make_float2(v2 * dq[3], 0.0f);
+  float2 ow[4];
+  sign_A2_f2(make_float2(u2, 0.0f), make_float2(v2, 0.0f), rw, P, ow);
+  const float vbar = (2.0f / 3.0f) * (v13.x + v13.y) - (1.0f / 3.0f) * v2;
+  const float G[4] = {dq[2], G1, G2, vbar * dq[3]};
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const float Vc = (4.0f / 3.0f) * (oh[c].x + oh[c].y) - (1.0f / 3.0f) * ow[c].x;
+    const float2 d = mul2(bc2(0.5f), add2(bc2(G[c]), make_float2(-Vc, Vc)));
+    Dm[c] = d.x;
+    Dp[c] = d.y;
+  }
+}
+
+// The face solvers used by the step kernels: the paired forms in FP32 device
+// code, the scalar ones otherwise (FP64, and the host).
+template <typename T>
+__host__ __device__ __forceinline__ void xface(const T qm[4], const T qp[4], const T dq[4],
+                                               const Phys<T>& P, T Dm[4], T Dp[4]) {
+#ifdef __CUDA_ARCH__
+  if constexpr (std::is_same<T, float>::value) {
+    xface_f2(qm, qp, dq, P, Dm, Dp);
+    return;
+  }
+#endif
+  xface_scalar(qm, qp, dq, P, Dm, Dp);
+}
+
+template <typename T>
+__host__ __device__ __forceinline__ void yface(const T qm[4], const T qp[4], const T dq[4],
+                                               T dap, const Phys<T>& P, T Dm[4], T Dp[4]) {
+#ifdef __CUDA_ARCH__
+  if constexpr (std::is_same<T, float>::value) {
+    yface_f2(qm, qp, dq, dap, P, Dm, Dp);
+    return;
+  }
+#endif
+  yface_scalar(qm, qp, dq, dap, P, Dm, Dp);
 }
 
 }  // namespace fv

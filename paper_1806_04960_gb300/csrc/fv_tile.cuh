@@ -40,6 +40,30 @@ __device__ __forceinline__ V4<T> pack(const T a[4]) {
   return V4<T>{a[0], a[1], a[2], a[3]};
 }
 
+// Largest / smallest of three values.  In FP32 one three-input instruction
+// (sm_100 and later); max and min are exact, so the result is that of two
+// fmax / fmin whatever the order.
+template <typename T>
+__device__ __forceinline__ T max3(T a, T b, T c) {
+  return fmax(fmax(a, b), c);
+}
+template <typename T>
+__device__ __forceinline__ T min3(T a, T b, T c) {
+  return fmin(fmin(a, b), c);
+}
+template <>
+__device__ __forceinline__ float max3<float>(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+template <>
+__device__ __forceinline__ float min3<float>(float a, float b, float c) {
+  float d;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+
 constexpr unsigned char F_FLUID = 0, F_SOLID = 1, F_OUT = 2;
 constexpr unsigned long long ONE_FIXED = 1ull << 32;
 enum { F_W = 0, F_E = 1, F_S = 2, F_N = 3 };
@@ -189,22 +213,23 @@ __device__ __forceinline__ void recon_cell(const V4<T>* wS, const V4<T>* wC, con
   if (!nbf(1, 0, fE)) ghost(1, 0, 1, sd.E, fE);
   if (!nbf(0, -1, fSo)) ghost(0, -1, 2, sd.S, fSo);
   if (!nbf(0, 1, fNo)) ghost(0, 1, 2, sd.N, fNo);
+  // limiter bounds over the 3 x 3 stencil; a diagonal neighbour that is not
+  // fluid contributes the cell's own fluctuation, already among the bounds
+  T fd[4][4];
+#pragma unroll
+  for (int d = 0; d < 4; ++d) {
+    if (!nbf((d & 1) ? 1 : -1, (d & 2) ? 1 : -1, fd[d])) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) fd[d][v] = Qf[v];
+    }
+  }
   T mx[4], mn[4];
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
-    mx[v] = fmax(fmax(fmax(Qf[v], fW[v]), fmax(fE[v], fSo[v])), fNo[v]);
-    mn[v] = fmin(fmin(fmin(Qf[v], fW[v]), fmin(fE[v], fSo[v])), fNo[v]);
-  }
-#pragma unroll
-  for (int d = 0; d < 4; ++d) {
-    T fd[4];
-    if (nbf((d & 1) ? 1 : -1, (d & 2) ? 1 : -1, fd)) {
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        mx[v] = fmax(mx[v], fd[v]);
-        mn[v] = fmin(mn[v], fd[v]);
-      }
-    }
+    mx[v] = max3(max3(Qf[v], fW[v], fE[v]), max3(fSo[v], fNo[v], fd[0][v]),
+                 max3(fd[1][v], fd[2][v], fd[3][v]));
+    mn[v] = min3(min3(Qf[v], fW[v], fE[v]), min3(fSo[v], fNo[v], fd[0][v]),
+                 min3(fd[1][v], fd[2][v], fd[3][v]));
   }
   const T mES = aE * rES, mEN = aE * rEN;
   recon_core(Qf, fW, fE, fSo, fNo, mx, mn, aE, mEc, mES, mEN, rEc, P, RC, base, ga);

@@ -115,6 +115,8 @@ _lib.fv_set_order.argtypes = [_H, C.c_int32]
 _lib.fv_set_order.restype = C.c_int
 _lib.fv_set_xface.argtypes = [_H, C.c_int32]
 _lib.fv_set_xface.restype = C.c_int
+_lib.fv_host_face_f32.argtypes = [C.c_int, _D, _D, _D, C.c_int, _D, _D]
+_lib.fv_host_face_f32.restype = C.c_int
 _lib.fv_set_tiling.argtypes = [_H, C.c_int32]
 _lib.fv_set_tiling.restype = C.c_int
 _lib.fv_host_yface_o1.argtypes = [_D, _D, C.c_double, _D, C.c_double, C.c_double, C.c_double,
@@ -134,7 +136,7 @@ ABI_SYMBOLS = ("fv_create", "fv_set_state", "fv_step", "fv_step_timed", "fv_get_
                "fv_batch_set_state", "fv_batch_step", "fv_batch_step_timed", "fv_batch_get_state",
                "fv_batch_get_diag", "fv_batch_size", "fv_batch_destroy", "fv_adjoint",
                "fv_host_adjoint_step", "fv_set_order", "fv_host_yface_o1",
-               "fv_host_xface_or", "fv_set_xface", "fv_set_tiling")
+               "fv_host_xface_or", "fv_set_xface", "fv_set_tiling", "fv_host_face_f32")
 
 
 def _check(st):
@@ -190,6 +192,19 @@ def fv_host_xface_or(qm, qp, model):
 def fv_host_yface(qm, qp, model):
     """Host evaluation of the kernels' y-face fluctuations (D-, D+)."""
     return _host_face(_lib.fv_host_yface, qm, qp, model)
+
+
+def fv_host_face_f32(which: int, qm, qp, model, paired: bool = True):
+    """Host evaluation of an FP32 face solver (which = 0: x, 1: y) in the
+    paired form of the FP32 kernels or in the scalar form (fv_host_face_f32)."""
+    m = np.ascontiguousarray(model, dtype=np.float64)
+    a = np.ascontiguousarray(qm, dtype=np.float64)
+    b = np.ascontiguousarray(qp, dtype=np.float64)
+    Dm, Dp = np.zeros(4), np.zeros(4)
+    P = lambda x: x.ctypes.data_as(_D)
+    _check(_lib.fv_host_face_f32(int(which), P(m), P(a), P(b), int(bool(paired)), P(Dm), P(Dp))
+           and FV_EINVAL)
+    return Dm, Dp
 
 
 HOST_ADJ_SIZES = {0: (8, 8), 1: (8, 8), 2: (29, 22), 3: (23, 8)}
