@@ -263,7 +263,7 @@ def measure_batch(fv, cases_mod, steps, warmup, stream_sync, barrier):
     b.close()
     return {"value": cells * steps / (total_ms * 1e-3) / 1e6, "unit": UNIT,
             "ms_per_step": total_ms / steps, "steps": steps, "domains": len(doms), "cells": cells,
-            "dtype": "f32", "launch": "persistent step kernel + per-domain finalize per step, "
+            "dtype": "f32", "launch": "persistent strip kernel + per-domain finalize per step, "
                                       "CUDA graph of all steps",
             "bad_domains": int(bad), "t_min": min(t), "t_max": max(t)}
 

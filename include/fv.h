@@ -137,7 +137,7 @@ fv_status fv_set_xface(fv_handle* h, int32_t solver);
  * FV_TILING_STRIP = one CTA per 32-column strip marching upwards in blocks of
  * 8 rows, sharing the reconstructed rows and y faces between blocks
  * (faster in both precisions); FV_TILING_AUTO (default) = the strip kernel.
- * The batch (fv_batch_*) stages by tiles.  FV_EINVAL for another value. */
+ * The batch (fv_batch_*) stages by strips.  FV_EINVAL for another value. */
 #define FV_TILING_AUTO 0
 #define FV_TILING_TILE 1
 #define FV_TILING_STRIP 2

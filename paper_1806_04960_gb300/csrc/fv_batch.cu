@@ -2,8 +2,8 @@
 //
 // Every domain has its own grid, equation of state, boundaries, level
 // detector, dt and time.  One step of the ensemble is one persistent launch of
-// batch_step_kernel over the tiles of all domains (round-robin over a grid of
-// a few CTAs per SM) followed by one per-domain finalize launch.  n steps are
+// batch_strip_kernel over the column strips of all domains (round-robin over
+// a grid of a few CTAs per SM) followed by one per-domain finalize launch.  n steps are
 // captured once into a CUDA graph on an internal stream and replayed.
 #include <cuda_runtime.h>
 
@@ -186,9 +186,9 @@ fv_status fv_batch_create(int32_t ndom, const fv_grid* grids, const fv_eos* eos,
       batch_release(b);
       return bfail(FV_ECUDA, std::string("fv_batch_create: ") + cudaGetErrorString(e));
     }
-    const int tx = (g.nx + 31) / 32, ty = (g.ny + 7) / 8;
-    for (int j = 0; j < ty; ++j)
-      for (int i = 0; i < tx; ++i) tiles.push_back(make_int4(k, i, j, 0));
+    const int sx = (g.nx + 31) / 32, sy = (g.ny + BATCH_STRIP_H - 1) / BATCH_STRIP_H;
+    for (int j = 0; j < sy; ++j)
+      for (int i = 0; i < sx; ++i) tiles.push_back(make_int4(k, i, j, BATCH_STRIP_H));
   }
   std::vector<unsigned char> table(batch_table_bytes(ndom, f64));
   batch_fill_table(b->desc.data(), ndom, f64, table.data());

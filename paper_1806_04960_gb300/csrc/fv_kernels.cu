@@ -202,39 +202,6 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? 2 : 4))
                          blockIdx.y, S);
 }
 
-// Batched step: every tile of every domain of an ensemble, distributed
-// round-robin over a persistent grid (one or a few CTAs per SM); each domain
-// uses its own dt, levels and accumulators.  parity selects which of the two
-// state buffers is read.
-template <typename T>
-struct BatchDomain {
-  StepParams p;
-  KConsts<T> kc;
-  T* q[2];
-  const uint8_t* solid;
-  int32_t* Kref;
-  int32_t* Kcur;
-  unsigned long long* colsum;
-  DevScalars* sc;
-  const double* rhoE_d;
-  const T* rt;
-};
-
-template <typename T, bool DEV>
-__global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? 2 : 4))
-    batch_step_kernel(const BatchDomain<T>* __restrict__ doms, const int4* __restrict__ tiles,
-                      int ntiles, int parity) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem<T>& S = *reinterpret_cast<Smem<T>*>(smem_raw);
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int4 td = tiles[t];
-    const BatchDomain<T>& d = doms[td.x];
-    step_tile<T, DEV, false>(d.p, d.kc, d.q[parity], d.q[1 - parity], d.solid, d.Kref, d.Kcur, d.colsum,
-                      d.sc, d.rhoE_d, d.rt, td.y, td.z, S);
-    __syncthreads();  // shared memory is reused by the next tile
-  }
-}
-
 // Per-domain finalize for a batch: one CTA per domain.
 template <typename T>
 __global__ void batch_finalize_kernel(const BatchDomain<T>* __restrict__ doms, double cfl,
@@ -476,38 +443,6 @@ void batch_fill_table(const BatchDomainDesc* d, int ndom, bool f64, void* host_d
     fill_table_t<double>(d, ndom, host_dst);
   else
     fill_table_t<float>(d, ndom, host_dst);
-}
-
-template <typename T, bool DEV>
-static int batch_grid_t() {
-  static int grid = 0;
-  if (!grid) {
-    const size_t smem = sizeof(Smem<T>);
-    cudaFuncSetAttribute(batch_step_kernel<T, DEV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    int per_sm = 0, dev = 0, sms = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_step_kernel<T, DEV>, NT, smem);
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    grid = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
-  }
-  return grid;
-}
-
-int batch_grid_size(bool f64) { return f64 ? batch_grid_t<double, false>() : batch_grid_t<float, true>(); }
-
-void launch_batch_step(bool f64, const void* table, const int4* tiles, int ntiles, int parity,
-                       cudaStream_t st) {
-  dim3 block(TX, TY);
-  if (f64) {
-    const int grid = batch_grid_t<double, false>();
-    batch_step_kernel<double, false><<<grid < ntiles ? grid : ntiles, block, sizeof(Smem<double>), st>>>(
-        static_cast<const BatchDomain<double>*>(table), tiles, ntiles, parity);
-  } else {
-    const int grid = batch_grid_t<float, true>();
-    batch_step_kernel<float, true><<<grid < ntiles ? grid : ntiles, block, sizeof(Smem<float>), st>>>(
-        static_cast<const BatchDomain<float>*>(table), tiles, ntiles, parity);
-  }
 }
 
 void launch_batch_finalize(bool f64, const void* table, int ndom, double cfl, int count_step,

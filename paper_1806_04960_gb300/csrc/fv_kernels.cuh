@@ -120,8 +120,11 @@ struct BatchDomainDesc {
 // batch_fill_table and copied to the device by the caller.
 size_t batch_table_bytes(int ndom, bool f64);
 void batch_fill_table(const BatchDomainDesc* descs, int ndom, bool f64, void* host_dst);
+// The batched step stages by strips (csrc/fv_strip.cu): work[k] = (domain,
+// strip column, strip row, strip height BATCH_STRIP_H, a multiple of 8).
+constexpr int BATCH_STRIP_H = 64;
 int batch_grid_size(bool f64);
-void launch_batch_step(bool f64, const void* table, const int4* tiles, int ntiles, int parity,
+void launch_batch_step(bool f64, const void* table, const int4* work, int nwork, int parity,
                        cudaStream_t st);
 void launch_batch_finalize(bool f64, const void* table, int ndom, double cfl, int count_step,
                            cudaStream_t st);

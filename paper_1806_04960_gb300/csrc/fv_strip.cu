@@ -68,21 +68,24 @@ struct StripSmem {
   unsigned char flag[WRING][SWX];
 };
 
+// Strip (sx, sy) of one domain: columns 32 sx .. 32 sx + 31, rows H sy ..
+// H sy + H - 1; called by the whole CTA.
 template <typename T, bool DEV, bool XOR>
-__global__ void __launch_bounds__(strip_threads<T>(), (sizeof(T) == 8 ? 1 : 3))
-    strip_kernel(StepParams p, KConsts<T> kc, const T* __restrict__ qin, T* __restrict__ qout,
-                 const uint8_t* __restrict__ solid, const int32_t* __restrict__ Kref,
-                 const int32_t* __restrict__ Kcur, unsigned long long* __restrict__ colsum,
-                 DevScalars* __restrict__ sc, const T* __restrict__ rt, int H) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  StripSmem<T>& S = *reinterpret_cast<StripSmem<T>*>(smem_raw);
+__device__ __forceinline__ void strip_body(const StepParams& p, const KConsts<T>& kc,
+                                           const T* __restrict__ qin, T* __restrict__ qout,
+                                           const uint8_t* __restrict__ solid,
+                                           const int32_t* __restrict__ Kref,
+                                           const int32_t* __restrict__ Kcur,
+                                           unsigned long long* __restrict__ colsum,
+                                           DevScalars* __restrict__ sc, const T* __restrict__ rt,
+                                           int sx, int sy, int H, StripSmem<T>& S) {
   constexpr int NTS = strip_threads<T>();
   constexpr int YF0 = NTS - 9 * 32;  // y faces taken by the warps past the x faces' nine
   const int t = threadIdx.x;
   const int nx = p.nx, ny = p.ny;
   const size_t N = (size_t)nx * ny;
-  const int i0 = blockIdx.x * SX;
-  const int jstart = blockIdx.y * H;
+  const int i0 = sx * SX;
+  const int jstart = sy * H;
   const int jend = min(jstart + H, ny);
   // Row r sits in window slot wslot(r) = (r - jstart + 2) mod WRING and in
   // record / y-face slot slot(r) = (r - jstart + 2) mod RING.  Slots are
@@ -263,6 +266,36 @@ __global__ void __launch_bounds__(strip_threads<T>(), (sizeof(T) == 8 ? 1 : 3))
 }
 
 template <typename T, bool DEV, bool XOR>
+__global__ void __launch_bounds__(strip_threads<T>(), (sizeof(T) == 8 ? 1 : 3))
+    strip_kernel(StepParams p, KConsts<T> kc, const T* __restrict__ qin, T* __restrict__ qout,
+                 const uint8_t* __restrict__ solid, const int32_t* __restrict__ Kref,
+                 const int32_t* __restrict__ Kcur, unsigned long long* __restrict__ colsum,
+                 DevScalars* __restrict__ sc, const T* __restrict__ rt, int H) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  StripSmem<T>& S = *reinterpret_cast<StripSmem<T>*>(smem_raw);
+  strip_body<T, DEV, XOR>(p, kc, qin, qout, solid, Kref, Kcur, colsum, sc, rt, blockIdx.x,
+                          blockIdx.y, H, S);
+}
+
+// Batched step: every strip (domain, sx, sy, H) of an ensemble, distributed
+// round-robin over a persistent grid; each domain uses its own parameters,
+// dt, levels and accumulators.  parity selects the state buffer read.
+template <typename T, bool DEV>
+__global__ void __launch_bounds__(strip_threads<T>(), (sizeof(T) == 8 ? 1 : 3))
+    batch_strip_kernel(const BatchDomain<T>* __restrict__ doms, const int4* __restrict__ work,
+                       int nwork, int parity) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  StripSmem<T>& S = *reinterpret_cast<StripSmem<T>*>(smem_raw);
+  for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+    const int4 sw = work[w];
+    const BatchDomain<T>& d = doms[sw.x];
+    strip_body<T, DEV, false>(d.p, d.kc, d.q[parity], d.q[1 - parity], d.solid, d.Kref, d.Kcur,
+                              d.colsum, d.sc, d.rt, sw.y, sw.z, sw.w, S);
+    __syncthreads();  // shared memory is reused by the next strip
+  }
+}
+
+template <typename T, bool DEV, bool XOR>
 void launch_strip_xt(const StepParams& p, const T* in, T* out, const uint8_t* solid,
                      const int32_t* Kref, const int32_t* Kcur, unsigned long long* colsum,
                      DevScalars* sc, const T* rt, cudaStream_t st) {
@@ -284,7 +317,43 @@ void launch_strip_xt(const StepParams& p, const T* in, T* out, const uint8_t* so
                                                       Kcur, colsum, sc, rt, H);
 }
 
+template <typename T, bool DEV>
+int batch_grid_t() {
+  static int grid = 0;
+  if (!grid) {
+    const size_t smem = sizeof(StripSmem<T>);
+    cudaFuncSetAttribute(batch_strip_kernel<T, DEV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_strip_kernel<T, DEV>,
+                                                  strip_threads<T>(), smem);
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    grid = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+  }
+  return grid;
+}
+
 }  // namespace
+
+int batch_grid_size(bool f64) {
+  return f64 ? batch_grid_t<double, false>() : batch_grid_t<float, true>();
+}
+
+void launch_batch_step(bool f64, const void* table, const int4* work, int nwork, int parity,
+                       cudaStream_t st) {
+  if (f64) {
+    const int grid = batch_grid_t<double, false>();
+    batch_strip_kernel<double, false>
+        <<<grid < nwork ? grid : nwork, strip_threads<double>(), sizeof(StripSmem<double>), st>>>(
+            static_cast<const BatchDomain<double>*>(table), work, nwork, parity);
+  } else {
+    const int grid = batch_grid_t<float, true>();
+    batch_strip_kernel<float, true>
+        <<<grid < nwork ? grid : nwork, strip_threads<float>(), sizeof(StripSmem<float>), st>>>(
+            static_cast<const BatchDomain<float>*>(table), work, nwork, parity);
+  }
+}
 
 int strip_height(int nx, int ny, int resident) {
   // Every CTA does about (H/8 + 0.4) blocks of work (the prologue is about

@@ -64,6 +64,24 @@ __device__ __forceinline__ float min3<float>(float a, float b, float c) {
   return d;
 }
 
+// One domain of a batch as the batched step kernel reads it (device table
+// filled on the host by batch_fill_table): parameters, constants, the two
+// state buffers (parity selects the one read), mask, levels, accumulators,
+// equilibrium tables.
+template <typename T>
+struct BatchDomain {
+  StepParams p;
+  KConsts<T> kc;
+  T* q[2];
+  const uint8_t* solid;
+  int32_t* Kref;
+  int32_t* Kcur;
+  unsigned long long* colsum;
+  DevScalars* sc;
+  const double* rhoE_d;
+  const T* rt;
+};
+
 constexpr unsigned char F_FLUID = 0, F_SOLID = 1, F_OUT = 2;
 constexpr unsigned long long ONE_FIXED = 1ull << 32;
 enum { F_W = 0, F_E = 1, F_S = 2, F_N = 3 };
