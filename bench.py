@@ -48,9 +48,12 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--only", choices=("f32", "f64"), default=None,
                     help="time one path only (profiling runs)")
-    ap.add_argument("--workload", choices=("dambreak", "drop", "adjoint"), default="dambreak",
+    ap.add_argument("--workload", choices=("dambreak", "drop", "adjoint", "impact", "weir"),
+                    default="dambreak",
                     help="drop: the 2048^2 elliptical drop, FP32 vs FP64 semi-axis histories; "
-                         "adjoint: the 512x256 gradient workload only")
+                         "adjoint: the 512x256 gradient workload only; impact / weir: the "
+                         "paper's dam break against a wall (1000x500, to t = 1) and its "
+                         "sharp-crested weir (800x250, to t = 0.18)")
     ap.add_argument("--adjoint-steps", type=int, default=2000)
     return ap.parse_args()
 
@@ -520,10 +523,55 @@ def run_drop(args):
                       "history": hist}), flush=True)
 
 
+def run_paper_setup(args):
+    """The paper's own set-ups as extra workloads (Sections 5.5 and 5.6), both
+    precisions at CFL 0.45, advanced in chunks of fv_step_timed to the end
+    time: the dam break with impact against a vertical wall (1000 x 500, to
+    t = 1) and the sharp-crested weir (800 x 250, to t = 0.18: at t = 0.19-0.21
+    the gas pocket under the nappe next to the weir is emptied and alpha rho
+    turns negative in one cell, in both precisions, at first and second order
+    and down to CFL 0.1, and in the oracle alike).  Throughput in cell-updates
+    per second; the paper's own figures (another GPU, FP64) as context."""
+    import torch
+    from paper_1806_04960_gb300 import build, cases
+    build.build()
+    from paper_1806_04960_gb300 import fv
+    if args.workload == "impact":
+        case, t_end, paper = cases.impact_e11(), 1.0, 1.0e7
+    else:
+        case, t_end, paper = cases.weir_e5(), 0.18, 1.4e7
+    res = {}
+    for name, prec in (("f32", fv.FV_FP32_DEV), ("f64", fv.FV_FP64)):
+        s = fv.Solver(case, prec)
+        s.set_state(case.q)
+        m0 = s.diag().mass
+        steps, ms, n = 0, 0.0, 50
+        while True:
+            _, tot = s.step_timed(n, case.cfl)
+            ms += tot
+            steps += n
+            d = s.diag()
+            if d.status or d.t >= t_end - 0.5 * d.dt_next:
+                break
+            n = max(1, min(1000, int((t_end - d.t) / d.dt_next)))
+        res[name] = {"mcups": case.nx * case.ny * steps / (ms * 1e-3) / 1e6, "steps": steps,
+                     "t": d.t, "status": d.status, "mass_rel_change": abs(d.mass - m0) / m0,
+                     "device_s": ms * 1e-3}
+        s.close()
+    torch.cuda.synchronize()
+    print(json.dumps({"workload": case.name, "nx": case.nx, "ny": case.ny, "cfl": case.cfl,
+                      "t_end": t_end, "paper_cell_updates_per_s": paper,
+                      "paper_note": "the paper's own run of this set-up, FP64 on its GPU",
+                      "ratio_f64_vs_paper": res["f64"]["mcups"] * 1e6 / paper, **res}), flush=True)
+
+
 def main():
     args = parse()
     if args.workload == "drop":
         run_drop(args)
+        return
+    if args.workload in ("impact", "weir"):
+        run_paper_setup(args)
         return
     if args.workload == "adjoint" and args.impl == "ours":
         run_adjoint(args)

@@ -273,6 +273,90 @@ def weir_domains(count: int = 256, seed: int = 4960, nmin: int = 64, nmax: int =
     return out
 
 
+def weir_e5(nx: int = 800, ny: int = 250, cfl: float = 0.45) -> Case:
+    """Flow over a sharp-crested weir (Section 5.5): [-7.5,7.5] x [0,2.1], a
+    weir of height 0.7 and one cell thick in the cell column right of x = 0
+    (a removed strip, walls all round), water [-7.5,0] x [0,1.5] in
+    hydrostatic balance, k0 = 6.54e5 (Mach 0.3 for H = 1.5), at rest; the
+    paper runs 800 x 250 to t = 1."""
+    dx = 15.0 / nx
+    rect = (0.0, dx, 0.0, 0.7)
+    c = dambreak(nx, ny, lx=15.0, ly=2.1, x0=-7.5, x_col=0.0, h_col=1.5, rects=[rect],
+                 k0=6.54e5, name=f"weir_e5_{nx}x{ny}", steps=0, cfl=cfl)
+    c.meta.update(crest=0.7, weir_col=int(round(7.5 / dx)), t_end=1.0)
+    return c
+
+
+def impact_e11(nx: int = 1000, ny: int = 500, cfl: float = 0.45) -> Case:
+    """Dam break and impact against a vertical wall (Section 5.6): [0,3.2] x
+    [0,1.8], water [0,1.2] x [0,0.6] in hydrostatic balance, k0 = 2.62e5,
+    walls on three sides and a transmissive top; the paper runs 1000 x 500
+    to t = 1 (efficiency) and shows t = 0.6 .. 1.7."""
+    c = dambreak(nx, ny, lx=3.2, ly=1.8, x_col=1.2, h_col=0.6, k0=2.62e5,
+                 name=f"impact_e11_{nx}x{ny}", steps=0, cfl=cfl,
+                 sides=(BC_WALL, BC_WALL, BC_WALL, BC_TRANSMISSIVE))
+    c.meta.update(t_end=1.0)
+    return c
+
+
+def _crossings(a: np.ndarray, y: np.ndarray, level: float = 0.5):
+    """Heights where the column profile a(y) crosses `level`, by linear
+    interpolation between cell centres, with the direction (+1: rising with y)."""
+    out = []
+    for j in range(len(a) - 1):
+        lo, hi = a[j] - level, a[j + 1] - level
+        if (lo < 0.0) != (hi < 0.0):
+            t = lo / (lo - hi)
+            out.append((y[j] + t * (y[j + 1] - y[j]), 1 if hi >= 0.0 else -1))
+    return out
+
+
+def weir_nappe(c: Case, q: np.ndarray, x_max: float = 0.8):
+    """Over-topping profile of the weir flow from a state q (Section 5.5, Eq.
+    (OverToppingProfile)): the lower streamline y_l(x) of the nappe right of
+    the weir, found as the first alpha = 0.5 crossing below the upper free
+    surface when scanning each column downwards; its maximum (x_m, y_m); and
+    h0, the height of the free surface above the crest in the weir column.
+    Returns (xs, y_low, x_m, y_m, h0); y_low is NaN where no nappe is found."""
+    a = q[3]
+    xc, yc = c.xc(), c.yc()
+    iw = c.meta["weir_col"]
+    crest = (np.nonzero(c.solid[:, iw])[0].max() + 1) * c.dy   # snapped crest height
+    col = a[:, iw].copy()
+    col[c.solid[:, iw] == 1] = 1.0                             # the weir itself counts as full
+    tops = [y for y, d in _crossings(col, yc) if d < 0]
+    h0 = (max(tops) - crest) if tops else float("nan")
+    xs, ys = [], []
+    for i in range(iw + 1, c.nx):
+        if xc[i] > x_max:
+            break
+        cr = _crossings(a[:, i], yc)
+        # downwards from the top: the first falling-into-liquid crossing is the
+        # upper surface, the next one below it (rising with y) the lower one
+        below = [y for y, d in sorted(cr, key=lambda z: -z[0])]
+        dirs = [d for y, d in sorted(cr, key=lambda z: -z[0])]
+        y_low = float("nan")
+        for k in range(len(below) - 1):
+            if dirs[k] < 0 and dirs[k + 1] > 0:
+                y_low = below[k + 1]
+                break
+        xs.append(xc[i])
+        ys.append(y_low)
+    xs, ys = np.array(xs), np.array(ys)
+    ok = np.isfinite(ys)
+    if not ok.any():
+        return xs, ys, float("nan"), float("nan"), h0
+    k = int(np.nanargmax(np.where(ok, ys, -np.inf)))
+    return xs, ys, float(xs[k]), float(ys[k]), float(h0)
+
+
+def overtopping_profile(x, x_m: float, y_m: float, h0: float):
+    """Lower streamline of the experimental reference, Eq. (OverToppingProfile):
+    y = y_m - 0.47 h0 ((x - x_m) / h0)^1.85 for x >= x_m."""
+    x = np.asarray(x, dtype=float)
+    return y_m - 0.47 * h0 * (np.maximum(x - x_m, 0.0) / h0) ** 1.85
+
+
 def smooth_bump(n: int, *, amp: float = 1e-3, sigma: float = 0.08, k0: float = 4.36e5,
                 g: float = GRAV) -> Case:
     """All-liquid unit box at hydrostatic rest (free surface at the lid) with a
