@@ -235,6 +235,7 @@ def measure_path(fv, case, prec, steps, warmup, stream_sync, barrier, device_ind
     s.set_state(case.q)
     if warmup:
         s.step(warmup, case.cfl)
+    rows = s.tune()          # strip height by measurement (fv_tune), outside the timed region
     stream_sync()
     barrier()
     with ClockSampler(device_index) as clk:
@@ -243,7 +244,7 @@ def measure_path(fv, case, prec, steps, warmup, stream_sync, barrier, device_ind
     d = s.diag()
     s.close()
     return {"kernel_ms": kernel_ms, "total_ms": total_ms, "status": d.status, "t": d.t,
-            "clocks": clk.summary()}
+            "clocks": clk.summary(), "strip_rows": rows}
 
 
 def measure_batch(fv, cases_mod, steps, warmup, stream_sync, barrier):
@@ -281,6 +282,7 @@ def measure_e2e(fv, case, prec, steps):
     out = torch.empty_like(qh).pin_memory()
     s.set_state(qh)          # warm the path once
     s.step(2, case.cfl)
+    s.tune()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     s.set_state(qh)
@@ -413,7 +415,8 @@ def run_ours(args):
                          "flops_per_cell": ops["flops"],
                          "hbm_achieved_gbs": bytes_alg / (kms * 1e-3) / 1e9,
                          "hbm_frac": bytes_alg / (kms * 1e-3) / 1e9 / pk["hbm_gbs"]},
-            "status": r["status"], "clocks": r["clocks"], "steps": r["steps"]}
+            "status": r["status"], "clocks": r["clocks"], "steps": r["steps"],
+            "strip_rows": r["strip_rows"]}
 
     e2e = None if args.no_e2e else measure_e2e(fv, case, fv.FV_FP32_DEV, min(steps, 50))
     batch = None
@@ -452,7 +455,9 @@ def run_ours(args):
                        "obstacles": 8, "cfl": case.cfl, "precision": "fp32 deviation form",
                        "l2": "inputs larger than L2 (state 134 MB f32 / 268 MB f64 per buffer, "
                              "double-buffered)",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "strip_rows": {"f32": f32["strip_rows"], "f64": f64["strip_rows"]},
+                       "strip_rows_note": "chosen by fv_tune before the timed region"},
             "roofline": f32["roofline"],
             "clocks": f32["clocks"],
             "gpu_launches": 2 * f32["steps"] + 1,

@@ -143,6 +143,24 @@ fv_status fv_set_xface(fv_handle* h, int32_t solver);
 #define FV_TILING_STRIP 2
 fv_status fv_set_tiling(fv_handle* h, int32_t tiling);
 
+/* Rows per strip of the strip kernel (a positive multiple of 8), or 0
+ * (default) for the built-in choice from the grid and the device's occupancy.
+ * Results do not depend on it; speed does.  FV_EINVAL for a negative value or
+ * one that is not a multiple of 8. */
+fv_status fv_set_strip_height(fv_handle* h, int32_t rows);
+
+/* Autotuner: times the strip kernel of the current order-2 step from the
+ * current state with strip heights of 32, 48, 64, 96, 128, 160, 192 and 256 rows
+ * (those not above the grid, rounded up to 8), three launches each after one
+ * warm-up, on the handle's stream, and keeps the fastest (fv_set_strip_height).
+ * The state, time, levels and accumulators are left as they were (the trial
+ * launches write only the other state buffer, which the next step
+ * overwrites).  *rows_out (nullable) receives the chosen height.  A no-op for
+ * the first-order scheme and the tile staging.  Synchronises the stream.
+ * FV_EINVAL without a state; FV_ECUDA on a CUDA error (the previous height is
+ * kept). */
+fv_status fv_tune(fv_handle* h, int32_t* rows_out);
+
 /* fv_step plus timing: CUDA events recorded on the handle's stream around
  * every launch of the fused step kernel give *kernel_ms, the summed device
  * time of those launches, and *total_ms, the device time of the whole call

@@ -647,13 +647,14 @@ void launch_reverse_step(AdjArgs<T> A, cudaStream_t st) {
 template <typename T, bool DEV>
 void launch_replay_step(const StepParams& p, const T* in, T* out, const uint8_t* solid,
                         const int32_t* Kref, const int32_t* Kcur, unsigned long long* colsum,
-                        DevScalars* sc, const Tables& tb, int tiling, cudaStream_t st) {
+                        DevScalars* sc, const Tables& tb, int tiling, int strip_h,
+                        cudaStream_t st) {
   if (DEV) {
     StateF32 s{(const float*)in, (float*)out};
-    launch_step_f32(p, s, solid, Kref, Kcur, colsum, sc, tb, st, false, tiling);
+    launch_step_f32(p, s, solid, Kref, Kcur, colsum, sc, tb, st, false, tiling, strip_h);
   } else {
     StateF64 s{(const double*)in, (double*)out};
-    launch_step_f64(p, s, solid, Kcur, colsum, sc, tb, st, false, tiling);
+    launch_step_f64(p, s, solid, Kcur, colsum, sc, tb, st, false, tiling, strip_h);
   }
 }
 
@@ -739,7 +740,7 @@ fv_status run_adjoint(fv_handle* h, const fv_adjoint_spec* spec, double* grad, i
                                cudaMemcpyDeviceToDevice, st));
     const int a = h->cur, b = 1 - h->cur;
     launch_replay_step<T, DEV>(p, (const T*)h->d_q[a], (T*)h->d_q[b], h->d_solid, h->d_Kref,
-                               h->d_Kcur, h->d_colsum, h->d_sc, tb, h->tiling, st);
+                               h->d_Kcur, h->d_colsum, h->d_sc, tb, h->tiling, h->strip_h, st);
     launch_finalize(p, h->d_Kref, h->d_Kcur, h->d_colsum, h->d_sc, 1, st);
     h->cur = b;
     adj_gauge_kernel<T, DEV><<<1, 128, 0, st>>>(nx, ny, (const T*)h->d_q[b], Kh + (size_t)n * nx,
@@ -803,7 +804,7 @@ fv_status run_adjoint(fv_handle* h, const fv_adjoint_spec* spec, double* grad, i
       launch_replay_step<T, DEV>(p, state(k, n - 1), state(k, n), h->d_solid,
                                  Kh + (size_t)(n - 1) * nx, Kh + (size_t)n * nx,
                                  rcol.as<unsigned long long>(), rsc.as<DevScalars>(), tb,
-                                 h->tiling, st2.s);
+                                 h->tiling, h->strip_h, st2.s);
       ++replayed;
     }
   };

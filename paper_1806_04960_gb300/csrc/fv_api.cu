@@ -71,7 +71,7 @@ static void launch_one_step(fv_handle* h, const StepParams& p, int a, int b) {
       launch_step_o1_f64(p, s, h->d_solid, h->d_Kcur, h->d_colsum, h->d_sc, tb, tq, h->stream, orx);
     else
       launch_step_f64(p, s, h->d_solid, h->d_Kcur, h->d_colsum, h->d_sc, tb, h->stream, orx,
-                      h->tiling);
+                      h->tiling, h->strip_h);
   } else {
     StateF32 s{(const float*)h->d_q[a], (float*)h->d_q[b]};
     if (h->order == 1)
@@ -79,7 +79,7 @@ static void launch_one_step(fv_handle* h, const StepParams& p, int a, int b) {
                          h->stream, orx);
     else
       launch_step_f32(p, s, h->d_solid, h->d_Kref, h->d_Kcur, h->d_colsum, h->d_sc, tb, h->stream,
-                      orx, h->tiling);
+                      orx, h->tiling, h->strip_h);
   }
 }
 
@@ -317,6 +317,63 @@ fv_status fv_set_tiling(fv_handle* h, int32_t tiling) {
   if (tiling != FV_TILING_AUTO && tiling != FV_TILING_TILE && tiling != FV_TILING_STRIP)
     return fail(FV_EINVAL, "fv_set_tiling: tiling must be FV_TILING_AUTO, _TILE or _STRIP");
   h->tiling = tiling;
+  return FV_OK;
+}
+
+fv_status fv_set_strip_height(fv_handle* h, int32_t rows) {
+  if (!h) return fail(FV_EINVAL, "fv_set_strip_height: null handle");
+  if (rows < 0 || rows % 8 != 0)
+    return fail(FV_EINVAL, "fv_set_strip_height: rows must be 0 or a positive multiple of 8");
+  h->strip_h = rows;
+  return FV_OK;
+}
+
+fv_status fv_tune(fv_handle* h, int32_t* rows_out) {
+  if (!h) return fail(FV_EINVAL, "fv_tune: null handle");
+  if (!h->has_state) return fail(FV_EINVAL, "fv_tune: no state (call fv_set_state first)");
+  if (h->order != 2 || h->tiling == FV_TILING_TILE) {
+    if (rows_out) *rows_out = h->strip_h;
+    return FV_OK;  // nothing to tune: the step does not stage by strips
+  }
+  // Trial launches read the current state and write the other buffer, which
+  // the next step overwrites; the accumulators they touch are put back.
+  DevScalars saved;
+  FV_CUDA(cudaMemcpyAsync(&saved, h->d_sc, sizeof(saved), cudaMemcpyDeviceToHost, h->stream));
+  FV_CUDA(cudaStreamSynchronize(h->stream));
+  const StepParams p = params_of(h, h->cfl > 0.0 ? h->cfl : 0.9);
+  const int hmax = ((h->grid.ny + 7) / 8) * 8;
+  static const int cand[] = {32, 48, 64, 96, 128, 160, 192, 256};
+  const int keep = h->strip_h;
+  int best = keep;
+  float best_ms = 1e30f;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t err = cudaEventCreate(&e0);
+  if (err == cudaSuccess) err = cudaEventCreate(&e1);
+  for (int c : cand) {
+    if (err != cudaSuccess) break;
+    if (c > hmax && c != cand[0]) continue;
+    h->strip_h = c;
+    const int a = h->cur, b = 1 - h->cur;
+    launch_one_step(h, p, a, b);  // warm-up
+    err = cudaEventRecord(e0, h->stream);
+    for (int k = 0; k < 3 && err == cudaSuccess; ++k) launch_one_step(h, p, a, b);
+    if (err == cudaSuccess) err = cudaEventRecord(e1, h->stream);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    if (err == cudaSuccess && ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  h->strip_h = err == cudaSuccess ? best : keep;
+  if (err == cudaSuccess) err = cudaMemsetAsync(h->d_colsum, 0, sizeof(unsigned long long) * h->grid.nx, h->stream);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(h->d_sc, &saved, sizeof(saved), cudaMemcpyHostToDevice, h->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(h->stream);
+  if (err != cudaSuccess) return cuda_fail(err, "fv_tune");
+  if (rows_out) *rows_out = h->strip_h;
   return FV_OK;
 }
 

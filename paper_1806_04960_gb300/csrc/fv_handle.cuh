@@ -30,6 +30,7 @@ struct fv_handle {
   int order = 2;                // scheme of fv_step: 2 (Eq. (Scheme)) or 1 (Sections 3.2-3.3)
   int xface = FV_XFACE_GL;      // x-face viscosity (fv_set_xface)
   int tiling = FV_TILING_AUTO;  // step-kernel staging (fv_set_tiling)
+  int strip_h = 0;              // strip height in rows, 0 = heuristic (fv_set_strip_height, fv_tune)
   void* d_q[2] = {nullptr, nullptr};
   int cur = 0;
   double* d_stage = nullptr;    // FP32 path: double staging buffer

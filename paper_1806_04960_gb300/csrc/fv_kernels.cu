@@ -465,23 +465,24 @@ void launch_batch_prepare(bool f64, const void* table, int ndom, double cfl, cud
 
 void launch_step_f64(const StepParams& p, const StateF64& s, const uint8_t* solid,
                      const int32_t* Kcur, unsigned long long* colsum, DevScalars* sc,
-                     const Tables& tb, cudaStream_t st, bool osher_romberg_x, int tiling) {
+                     const Tables& tb, cudaStream_t st, bool osher_romberg_x, int tiling,
+                     int strip_h) {
   if (tiling == TILING_TILE)
     launch_step_t<double, false>(p, s.in, s.out, solid, Kcur, Kcur, colsum, sc, tb.rhoE_d,
                                  tb.rhoE_d, osher_romberg_x, st);
   else
-    launch_strip_f64(p, s, solid, Kcur, colsum, sc, tb, st, osher_romberg_x);
+    launch_strip_f64(p, s, solid, Kcur, colsum, sc, tb, st, osher_romberg_x, strip_h);
 }
 
 void launch_step_f32(const StepParams& p, const StateF32& s, const uint8_t* solid,
                      const int32_t* Kref, const int32_t* Kcur, unsigned long long* colsum,
                      DevScalars* sc, const Tables& tb, cudaStream_t st, bool osher_romberg_x,
-                     int tiling) {
+                     int tiling, int strip_h) {
   if (tiling == TILING_TILE)
     launch_step_t<float, true>(p, s.in, s.out, solid, Kref, Kcur, colsum, sc, tb.rhoE_d,
                                tb.rhoE_f, osher_romberg_x, st);
   else
-    launch_strip_f32(p, s, solid, Kref, Kcur, colsum, sc, tb, st, osher_romberg_x);
+    launch_strip_f32(p, s, solid, Kref, Kcur, colsum, sc, tb, st, osher_romberg_x, strip_h);
 }
 
 void launch_finalize(const StepParams& p, int32_t* Kref, int32_t* Kcur,

@@ -62,21 +62,23 @@ struct StateF32 {
 // TILING_TILE = step_kernel, one CTA per 32 x 8 tile (csrc/fv_kernels.cu);
 // TILING_STRIP = strip_kernel, one CTA per 32-column strip (csrc/fv_strip.cu);
 // TILING_AUTO = the strip kernel.
+// strip_h: rows of a strip (a multiple of 8), 0 = chosen by strip_height.
 enum StepTiling { TILING_AUTO = 0, TILING_TILE = 1, TILING_STRIP = 2 };
 void launch_step_f64(const StepParams& p, const StateF64& s, const uint8_t* solid,
                      const int32_t* Kcur, unsigned long long* colsum, DevScalars* sc,
                      const Tables& tb, cudaStream_t st, bool osher_romberg_x = false,
-                     int tiling = TILING_AUTO);
+                     int tiling = TILING_AUTO, int strip_h = 0);
 void launch_step_f32(const StepParams& p, const StateF32& s, const uint8_t* solid,
                      const int32_t* Kref, const int32_t* Kcur, unsigned long long* colsum,
                      DevScalars* sc, const Tables& tb, cudaStream_t st,
-                     bool osher_romberg_x = false, int tiling = TILING_AUTO);
+                     bool osher_romberg_x = false, int tiling = TILING_AUTO, int strip_h = 0);
 void launch_strip_f64(const StepParams& p, const StateF64& s, const uint8_t* solid,
                       const int32_t* Kcur, unsigned long long* colsum, DevScalars* sc,
-                      const Tables& tb, cudaStream_t st, bool osher_romberg_x);
+                      const Tables& tb, cudaStream_t st, bool osher_romberg_x, int strip_h);
 void launch_strip_f32(const StepParams& p, const StateF32& s, const uint8_t* solid,
                       const int32_t* Kref, const int32_t* Kcur, unsigned long long* colsum,
-                      DevScalars* sc, const Tables& tb, cudaStream_t st, bool osher_romberg_x);
+                      DevScalars* sc, const Tables& tb, cudaStream_t st, bool osher_romberg_x,
+                      int strip_h);
 // Strip height (rows, a multiple of 8) for an nx x ny grid when `resident`
 // strip CTAs fit on the device at once.
 int strip_height(int nx, int ny, int resident);
@@ -122,7 +124,7 @@ size_t batch_table_bytes(int ndom, bool f64);
 void batch_fill_table(const BatchDomainDesc* descs, int ndom, bool f64, void* host_dst);
 // The batched step stages by strips (csrc/fv_strip.cu): work[k] = (domain,
 // strip column, strip row, strip height BATCH_STRIP_H, a multiple of 8).
-constexpr int BATCH_STRIP_H = 64;
+constexpr int BATCH_STRIP_H = 128;
 int batch_grid_size(bool f64);
 void launch_batch_step(bool f64, const void* table, const int4* work, int nwork, int parity,
                        cudaStream_t st);

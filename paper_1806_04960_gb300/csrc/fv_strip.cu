@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(strip_threads<T>(), (sizeof(T) == 8 ? 1 : 3))
 template <typename T, bool DEV, bool XOR>
 void launch_strip_xt(const StepParams& p, const T* in, T* out, const uint8_t* solid,
                      const int32_t* Kref, const int32_t* Kcur, unsigned long long* colsum,
-                     DevScalars* sc, const T* rt, cudaStream_t st) {
+                     DevScalars* sc, const T* rt, int strip_h, cudaStream_t st) {
   constexpr int NTS = strip_threads<T>();
   const size_t smem = sizeof(StripSmem<T>);
   static int resident = 0;
@@ -311,7 +311,7 @@ void launch_strip_xt(const StepParams& p, const T* in, T* out, const uint8_t* so
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     resident = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
   }
-  const int H = strip_height(p.nx, p.ny, resident);
+  const int H = strip_h > 0 ? strip_h : strip_height(p.nx, p.ny, resident);
   const dim3 grid((p.nx + SX - 1) / SX, (p.ny + H - 1) / H);
   strip_kernel<T, DEV, XOR><<<grid, NTS, smem, st>>>(p, make_consts<T>(p), in, out, solid, Kref,
                                                       Kcur, colsum, sc, rt, H);
@@ -379,20 +379,25 @@ int strip_height(int nx, int ny, int resident) {
 
 void launch_strip_f64(const StepParams& p, const StateF64& s, const uint8_t* solid,
                       const int32_t* Kcur, unsigned long long* colsum, DevScalars* sc,
-                      const Tables& tb, cudaStream_t st, bool osher_romberg_x) {
+                      const Tables& tb, cudaStream_t st, bool osher_romberg_x, int strip_h) {
   if (osher_romberg_x)
-    launch_strip_xt<double, false, true>(p, s.in, s.out, solid, Kcur, Kcur, colsum, sc, tb.rhoE_d, st);
+    launch_strip_xt<double, false, true>(p, s.in, s.out, solid, Kcur, Kcur, colsum, sc, tb.rhoE_d,
+                                         strip_h, st);
   else
-    launch_strip_xt<double, false, false>(p, s.in, s.out, solid, Kcur, Kcur, colsum, sc, tb.rhoE_d, st);
+    launch_strip_xt<double, false, false>(p, s.in, s.out, solid, Kcur, Kcur, colsum, sc,
+                                          tb.rhoE_d, strip_h, st);
 }
 
 void launch_strip_f32(const StepParams& p, const StateF32& s, const uint8_t* solid,
                       const int32_t* Kref, const int32_t* Kcur, unsigned long long* colsum,
-                      DevScalars* sc, const Tables& tb, cudaStream_t st, bool osher_romberg_x) {
+                      DevScalars* sc, const Tables& tb, cudaStream_t st, bool osher_romberg_x,
+                      int strip_h) {
   if (osher_romberg_x)
-    launch_strip_xt<float, true, true>(p, s.in, s.out, solid, Kref, Kcur, colsum, sc, tb.rhoE_f, st);
+    launch_strip_xt<float, true, true>(p, s.in, s.out, solid, Kref, Kcur, colsum, sc, tb.rhoE_f,
+                                       strip_h, st);
   else
-    launch_strip_xt<float, true, false>(p, s.in, s.out, solid, Kref, Kcur, colsum, sc, tb.rhoE_f, st);
+    launch_strip_xt<float, true, false>(p, s.in, s.out, solid, Kref, Kcur, colsum, sc,
+                                        tb.rhoE_f, strip_h, st);
 }
 
 }  // namespace fv

@@ -117,6 +117,10 @@ _lib.fv_set_xface.argtypes = [_H, C.c_int32]
 _lib.fv_set_xface.restype = C.c_int
 _lib.fv_host_face_f32.argtypes = [C.c_int, _D, _D, _D, C.c_int, _D, _D]
 _lib.fv_host_face_f32.restype = C.c_int
+_lib.fv_set_strip_height.argtypes = [_H, C.c_int32]
+_lib.fv_set_strip_height.restype = C.c_int
+_lib.fv_tune.argtypes = [_H, C.POINTER(C.c_int32)]
+_lib.fv_tune.restype = C.c_int
 _lib.fv_set_tiling.argtypes = [_H, C.c_int32]
 _lib.fv_set_tiling.restype = C.c_int
 _lib.fv_host_yface_o1.argtypes = [_D, _D, C.c_double, _D, C.c_double, C.c_double, C.c_double,
@@ -136,7 +140,8 @@ ABI_SYMBOLS = ("fv_create", "fv_set_state", "fv_step", "fv_step_timed", "fv_get_
                "fv_batch_set_state", "fv_batch_step", "fv_batch_step_timed", "fv_batch_get_state",
                "fv_batch_get_diag", "fv_batch_size", "fv_batch_destroy", "fv_adjoint",
                "fv_host_adjoint_step", "fv_set_order", "fv_host_yface_o1",
-               "fv_host_xface_or", "fv_set_xface", "fv_set_tiling", "fv_host_face_f32")
+               "fv_host_xface_or", "fv_set_xface", "fv_set_tiling", "fv_host_face_f32",
+               "fv_set_strip_height", "fv_tune")
 
 
 def _check(st):
@@ -252,6 +257,16 @@ def fv_set_xface(h, solver: int) -> None:
 
 def fv_set_tiling(h, tiling: int) -> None:
     _check(_lib.fv_set_tiling(h, int(tiling)))
+
+
+def fv_set_strip_height(h, rows: int) -> None:
+    _check(_lib.fv_set_strip_height(h, int(rows)))
+
+
+def fv_tune(h) -> int:
+    rows = C.c_int32(0)
+    _check(_lib.fv_tune(h, C.byref(rows)))
+    return rows.value
 
 
 def fv_host_cell_ops() -> dict:
@@ -371,6 +386,15 @@ class Solver:
         """Step-kernel staging: FV_TILING_AUTO (default), FV_TILING_TILE or
         FV_TILING_STRIP (fv_set_tiling); the results are bitwise the same."""
         fv_set_tiling(self.h, tiling)
+
+    def set_strip_height(self, rows: int) -> None:
+        """Rows per strip of the strip kernel, 0 = built-in choice (fv_set_strip_height)."""
+        fv_set_strip_height(self.h, rows)
+
+    def tune(self) -> int:
+        """Time the strip heights on the current state and keep the fastest
+        (fv_tune); returns the chosen height."""
+        return fv_tune(self.h)
 
     def step(self, n: int, cfl: float | None = None, want_time: bool = False):
         return fv_step(self.h, n, self.case.cfl if cfl is None else cfl, want_time)

@@ -120,3 +120,54 @@ def test_adjoint_strip_equals_tile(fv):
         out.append((grad, info.loss))
         s.close()
     assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
+
+
+@pytest.mark.parametrize("prec", ["FV_FP32_DEV", "FV_FP64"])
+def test_every_strip_height_gives_the_same_bits(fv, prec):
+    """Strip heights that do and do not divide the grid height, down to one
+    block and up to the whole grid."""
+    p = getattr(fv, prec)
+    c = ragged(257, 203, seed=7)
+    ref = run(fv, c, p, fv.FV_TILING_TILE, 40)
+    for rows in (8, 16, 24, 40, 64, 200, 256, 2048):
+        s = fv.Solver(c, p)
+        s.set_strip_height(rows)
+        s.set_state(c.q)
+        t = s.step(40, c.cfl, want_time=True)
+        got = (s.get_state(), t, s.levels(), s.diag().status, s.diag().steps)
+        s.close()
+        same(ref, got)
+
+
+def test_tune_keeps_state_and_results(fv):
+    c = cases.c2(512, 256)
+    a = fv.Solver(c, fv.FV_FP32_DEV)
+    a.set_state(c.q)
+    a.step(5, c.cfl)
+    q0, d0, K0 = a.get_state(), a.diag(), a.levels()
+    rows = a.tune()
+    assert rows in (32, 48, 64, 96, 128, 160, 192, 256)
+    q1, d1 = a.get_state(), a.diag()
+    assert np.array_equal(q0, q1) and d0.t == d1.t and d0.steps == d1.steps and d0.status == d1.status
+    assert np.array_equal(K0, a.levels())
+    t = a.step(20, c.cfl, want_time=True)
+    got = (a.get_state(), t, a.levels(), a.diag().status, a.diag().steps)
+    a.close()
+    b = fv.Solver(c, fv.FV_FP32_DEV)
+    b.set_state(c.q)
+    b.step(5, c.cfl)
+    t = b.step(20, c.cfl, want_time=True)
+    ref = (b.get_state(), t, b.levels(), b.diag().status, b.diag().steps)
+    b.close()
+    same(ref, got)
+
+
+def test_strip_height_errors(fv):
+    s = fv.Solver(ragged(45, 13), fv.FV_FP32_DEV)
+    for bad in (-8, 12, 7):
+        with pytest.raises(fv.FvError) as ei:
+            s.set_strip_height(bad)
+        assert ei.value.status == fv.FV_EINVAL
+    with pytest.raises(fv.FvError):
+        s.tune()   # no state yet
+    s.close()
