@@ -158,22 +158,15 @@ def test_fp64_mass_conservation(fv):
     assert abs(m1 - m0) <= 1e-13 * m0
 
 
-def test_fp64_full_size_sampled_step(fv):
-    """4096 x 2048 with 8 obstacles, the launch the benchmark times: run 20
-    steps, then one more; the oracle recomputes that last step at sampled
-    cells (tile borders, obstacle edges, the front, random cells)."""
-    c = cases.c2()
-    s = fv.Solver(c, fv.FV_FP64)
-    s.set_state(c.q)
-    s.step(20, c.cfl)
-    q20 = s.get_state()
-    s.step(1, c.cfl)
-    q21 = s.get_state()
-    s.close()
+def full_size_picks(c, q20, rows):
+    """Sampled cells of the 4096 x 2048 workload: random fluid cells, cells
+    next to solids, cells on the strips' column edges (x = 32 k - 1, 32 k), on
+    the 8-row block edges and on the strip-row edges (y = H k - 1, H k) of the
+    strip height H in use, and the moving front."""
     rng = np.random.Generator(np.random.PCG64(2048))
-    fluid = np.flatnonzero(c.solid.ravel() == 0)
+    fluid_mask = c.solid.ravel() == 0
+    fluid = np.flatnonzero(fluid_mask)
     picks = [rng.choice(fluid, 3000, replace=False)]
-    # cells next to solids and at tile corners
     sol = c.solid.astype(bool)
     edge = np.zeros_like(sol)
     edge[:, 1:] |= sol[:, :-1]
@@ -182,19 +175,65 @@ def test_fp64_full_size_sampled_step(fv):
     edge[:-1, :] |= sol[1:, :]
     edge &= ~sol
     picks.append(rng.choice(np.flatnonzero(edge.ravel()), 500, replace=False))
-    jj, ii = np.meshgrid(np.arange(0, c.ny, 8), np.arange(0, c.nx, 32), indexing="ij")
-    corner = (jj * c.nx + ii).ravel()
-    corner = corner[c.solid.ravel()[corner] == 0]
-    picks.append(rng.choice(corner, 500, replace=False))
-    front = np.flatnonzero((np.abs(q20[3] - c.q[3]) > 1e-6).ravel() & (c.solid.ravel() == 0))
+    cols = np.concatenate([np.arange(31, c.nx, 32), np.arange(0, c.nx, 32)])
+    rows_b = np.concatenate([np.arange(7, c.ny, 8), np.arange(0, c.ny, 8)])
+    rows_s = np.concatenate([np.arange(rows - 1, c.ny, rows), np.arange(0, c.ny, rows)])
+    for rr in (rows_b, rows_s):
+        jj, ii = np.meshgrid(rr, cols, indexing="ij")
+        cand = (jj * c.nx + ii).ravel()
+        cand = cand[fluid_mask[cand]]
+        picks.append(rng.choice(cand, min(500, cand.size), replace=False))
+    front = np.flatnonzero((np.abs(q20[3] - c.q[3]) > 1e-6).ravel() & fluid_mask)
     if front.size:
         picks.append(rng.choice(front, min(500, front.size), replace=False))
-    cells = np.unique(np.concatenate(picks))
+    return np.unique(np.concatenate(picks))
+
+
+def full_size_last_step(fv, prec):
+    """20 steps, the strip height tuned as the benchmark does (fv_tune), one
+    more step; returns the case, the state before and after the last step and
+    the strip height."""
+    c = cases.c2()
+    s = fv.Solver(c, prec)
+    s.set_state(c.q)
+    s.step(20, c.cfl)
+    rows = s.tune()
+    q20 = s.get_state()
+    s.step(1, c.cfl)
+    q21 = s.get_state()
+    s.close()
+    return c, q20, q21, rows
+
+
+def test_fp64_full_size_sampled_step(fv):
+    """4096 x 2048 with 8 obstacles in the launch configuration the benchmark
+    times (strip height from fv_tune): the oracle recomputes the last of 21
+    steps at sampled cells (random, next to solids, on strip and block edges,
+    at the front)."""
+    c, q20, q21, rows = full_size_last_step(fv, fv.FV_FP64)
+    cells = full_size_picks(c, q20, rows)
     ref, dt = O.step_cells(c, q20, cells)
     got = q21.reshape(4, -1)[:, cells].T
     for v in range(4):
         scale = np.abs(ref[:, v]).max()
         assert np.abs(got[:, v] - ref[:, v]).max() <= 1e-12 * (scale if scale > 0 else 1.0)
+
+
+def test_fp32_full_size_sampled_step(fv):
+    """The same for the FP32 deviation form, the benchmark's headline path:
+    the oracle steps from the FP32 state (widened to double) at the sampled
+    cells; the FP32 step agrees to its rounding (bounds relative to the
+    largest |value| of each component: alpha rho and alpha 1e-6, momenta
+    1e-4)."""
+    c, q20, q21, rows = full_size_last_step(fv, fv.FV_FP32_DEV)
+    cells = full_size_picks(c, q20, rows)
+    ref, dt = O.step_cells(c, q20, cells)
+    got = q21.reshape(4, -1)[:, cells].T
+    tol = [1e-6, 1e-4, 1e-4, 1e-6]
+    for v in range(4):
+        scale = np.abs(ref[:, v]).max()
+        err = np.abs(got[:, v] - ref[:, v]).max() / (scale if scale > 0 else 1.0)
+        assert err <= tol[v], (v, err)
 
 
 def test_invalid_inputs(fv):
