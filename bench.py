@@ -69,6 +69,23 @@ def dist_env():
     return rank, world, local
 
 
+def per_rank_max(x: float, dist=None, device: str = "cuda") -> float:
+    """Largest x over the ranks of the default process group (x itself
+    without one); the tensor lives on `device` (CUDA for NCCL, CPU for gloo)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(world: int, cells: int, ms_per_step: float) -> float:
+    """Whole-job MCUPS of `world` replicas, each advancing `cells` cells per
+    step, when the slowest rank takes ms_per_step per step."""
+    return world * cells / (ms_per_step * 1e-3) / 1e6
+
+
 # --------------------------------------------------------------------------- clocks
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during a region."""
@@ -396,22 +413,15 @@ def run_ours(args):
                                  args.strip_rows)
         res[name]["steps"] = k
 
-    def per_rank_max(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     cells = case.nx * case.ny
     traffic = recorded_traffic()
     line_paths = {}
     for name in res:
         r = res[name]
-        tot = per_rank_max(r["total_ms"])
-        ker = per_rank_max(r["kernel_ms"])
+        tot = per_rank_max(r["total_ms"], dist)
+        ker = per_rank_max(r["kernel_ms"], dist)
         ms_step = tot / r["steps"]
-        value = world * cells / (ms_step * 1e-3) / 1e6
+        value = weak_scaling_value(world, cells, ms_step)
         kms = ker / r["steps"]
         flops = ops["flops"] * cells
         achieved = flops / (kms * 1e-3) / 1e12
