@@ -300,6 +300,26 @@ def test_fp32_lake_at_rest_exact(fv):
         assert d.status == 0
 
 
+@pytest.mark.parametrize("prec", ["FV_FP32_DEV", "FV_FP64"])
+def test_full_size_lake_at_rest(fv, prec):
+    """The benchmark's grid and obstacles as a lake at rest (y0 = 1, air
+    above), in the benchmark's launch configuration (fv_tune): 100 steps leave
+    it at rest to roundoff (FP32 deviation form: exactly representable zeros
+    stay zero; bound 1e-9 rho0 as at the smaller sizes)."""
+    c = cases.c2_lake()
+    s = fv.Solver(c, getattr(fv, prec))
+    s.set_state(c.q)
+    s.tune()
+    s.step(100, c.cfl)
+    q, d = s.get_state(), s.diag()
+    s.close()
+    fl = c.solid == 0
+    tol = 1e-9 * c.rho0 if prec == "FV_FP32_DEV" else 1e-10 * c.rho0
+    assert d.status == 0
+    assert np.abs(q[1]).max() <= tol and np.abs(q[2]).max() <= tol
+    assert np.abs(q[0] - c.q[0])[fl].max() <= tol
+
+
 def test_fp32_dambreak_error_vs_oracle(fv):
     c = cases.c1()
     qo, to, _, _ = O.run(c, 200, cfl=0.45)
