@@ -1,27 +1,27 @@
-// One time step of Eq. (Scheme) (Gaburro, Castro, Dumbser) as a single fused
-// kernel per step plus a one-block finalize kernel:
+// One time step of Eq. (Scheme) (Gaburro, Castro, Dumbser) is one step
+// kernel plus a finalize kernel.  The default step kernel stages by column
+// strips (strip_kernel, fv_strip.cu); this file holds the tile staging
+// (fv_set_tiling(h, FV_TILING_TILE)) and the kernels around the step:
 //
-//   step_kernel   one CTA per TX x TY tile of cells.
-//     load      Q^n of the tile plus a 2-cell halo into shared memory (SoA,
-//               coalesced rows), with the solid/outside flags and the column
-//               levels K_i;
+//   step_kernel   one CTA per TX x TY tile of cells (the cell and face
+//                 arithmetic of fv_tile.cuh, shared with strip_kernel):
+//     load      Q^n of the tile plus a 2-cell halo into shared memory, with
+//               the solid/outside flags and the column levels K_i;
 //     recon     for the tile plus a 1-cell ring: fluctuations w.r.t. the
-//               cell's water-at-rest state Q^E_ij (alpha^E = alpha_ij,
-//               rho^E from the column level), central slopes, one
-//               Barth-Jespersen factor per cell, order switch, half-step
-//               predictor dQ/dt = -(A1 dQ/dx + A2 dQ/dy) in deviation form,
-//               the four face-midpoint states at t^{n+1/2} (Section 3.4);
+//               cell's water-at-rest state, slopes, Barth-Jespersen factor,
+//               order switch, half-step predictor, face-midpoint states at
+//               t^{n+1/2} (Section 3.4);
 //     faces     every x face (Osher, Gauss-Legendre) and y face (well-balanced
 //               Osher-Romberg) of the tile solved once into shared memory;
-//               walls and solid neighbours see the mirror state;
-//     update    Q^{n+1} = Q^n - dt/dx (D+_W + D-_E + I_x) - dt/dy (D+_S + D-_N + I_y)
-//               with the interior integral of Eq. (b^y_3_final_integral) plus
-//               the conservative part f(q_E) - f(q_W), g(q_N) - g(q_S);
-//     epilogue  max signal rate for the next dt (one atomicMax per CTA) and
-//               the free-surface detector's column sums of Eq.
-//               (Free_surf_detector) in exact 2^-32 fixed point (one atomicAdd
-//               per column per CTA), non-admissible-state flag.
-//   finalize      K_i = round(column sum), dt bookkeeping, accumulator reset.
+//     update    Q^{n+1} with the interior integral of Eq.
+//               (b^y_3_final_integral) plus the conservative part;
+//     epilogue  max signal rate for the next dt, the free-surface detector's
+//               column sums of Eq. (Free_surf_detector) in exact 2^-32 fixed
+//               point, non-admissible-state flag.
+//   finalize_kernel   K_i = round(column sum), dt bookkeeping, accumulator
+//                     reset (one thread per column over the grid);
+//   prepare_kernel, prologue_kernel, to_dev/from_dev, mass and the batch's
+//   per-domain finalize and prepare.
 //
 // The FP64 instantiation stores the full state; the FP32 instantiation stores
 // the deviation m^f = m - alpha rho^E(y; K_i) so that a state at rest is
