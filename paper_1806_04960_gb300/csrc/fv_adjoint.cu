@@ -595,19 +595,29 @@ __global__ void adj_record_kernel(int nx, const int32_t* Kcur, int32_t* Krow, co
   if (blockIdx.x == 0 && threadIdx.x == 0) *dt_slot = sc->dt_cur;
 }
 
-// alpha rho at the gauges of a state stored relative to the levels K (double).
+// After step n of the forward sweep, one launch: alpha rho at the gauges of
+// Q^n, stored relative to the levels Kq it was computed with (double), and
+// the levels and dt step n + 1 will use (Krow null after the last step).
 template <typename T, bool DEV>
-__global__ void adj_gauge_kernel(int nx, int ny, const T* q, const int32_t* K, const double* rhoE,
-                                 const int64_t* gauges, int ng, double* out) {
+__global__ void adj_after_step_kernel(int nx, int ny, const T* q, const int32_t* Kq,
+                                      const double* rhoE, const int64_t* gauges, int ng,
+                                      double* out, const int32_t* Kcur, int32_t* Krow,
+                                      const DevScalars* sc, double* dt_slot) {
   const size_t N = (size_t)nx * ny;
-  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
-    const int64_t c = gauges[g];
-    if (DEV) {
-      const int i = (int)(c % nx), j = (int)(c / nx);
-      out[g] = (double)q[3 * N + c] * rhoE[2 * (j - K[i]) + 1 + 2 * ny] + (double)q[c];
-    } else {
-      out[g] = (double)q[c];
+  if (blockIdx.x == 0)
+    for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+      const int64_t c = gauges[g];
+      if (DEV) {
+        const int i = (int)(c % nx), j = (int)(c / nx);
+        out[g] = (double)q[3 * N + c] * rhoE[2 * (j - Kq[i]) + 1 + 2 * ny] + (double)q[c];
+      } else {
+        out[g] = (double)q[c];
+      }
     }
+  if (Krow) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nx; i += gridDim.x * blockDim.x)
+      Krow[i] = Kcur[i];
+    if (blockIdx.x == 0 && threadIdx.x == 0) *dt_slot = sc->dt_cur;
   }
 }
 
@@ -754,8 +764,8 @@ fv_status run_adjoint(fv_handle* h, const fv_adjoint_spec* spec, double* grad, i
   launch_prepare(spec->cfl, h->d_sc, st);
   h->cfl = spec->cfl;
   const int rb = std::max(1, std::min(1024, (nx + 255) / 256));
+  adj_record_kernel<<<rb, 256, 0, st>>>(nx, h->d_Kcur, Kh + (size_t)nx, h->d_sc, dth + 1);
   for (int n = 1; n <= Nst; ++n) {
-    adj_record_kernel<<<rb, 256, 0, st>>>(nx, h->d_Kcur, Kh + (size_t)n * nx, h->d_sc, dth + n);
     if ((n - 1) % s == 0)
       ADJ_CUDA(cudaMemcpyAsync(ckpt.as<char>() + qbytes * ((n - 1) / s), h->d_q[h->cur], qbytes,
                                cudaMemcpyDeviceToDevice, st));
@@ -764,9 +774,10 @@ fv_status run_adjoint(fv_handle* h, const fv_adjoint_spec* spec, double* grad, i
                                h->d_Kcur, h->d_colsum, h->d_sc, tb, h->tiling, h->strip_h, st);
     launch_finalize(p, h->d_Kref, h->d_Kcur, h->d_colsum, h->d_sc, 1, st);
     h->cur = b;
-    adj_gauge_kernel<T, DEV><<<1, 128, 0, st>>>(nx, ny, (const T*)h->d_q[b], Kh + (size_t)n * nx,
-                                                h->d_rhoE, gidx.as<int64_t>(), ng,
-                                                gval.as<double>() + (size_t)(n - 1) * ng);
+    adj_after_step_kernel<T, DEV><<<rb, 256, 0, st>>>(
+        nx, ny, (const T*)h->d_q[b], Kh + (size_t)n * nx, h->d_rhoE, gidx.as<int64_t>(), ng,
+        gval.as<double>() + (size_t)(n - 1) * ng, h->d_Kcur,
+        n < Nst ? Kh + (size_t)(n + 1) * nx : nullptr, h->d_sc, dth + n + 1);
   }
   ADJ_CUDA(cudaGetLastError());
   ADJ_CUDA(cudaEventRecord(evf.b, st));
