@@ -548,7 +548,7 @@ def run_drop(args):
 
 
 def run_paper_setup(args):
-    """The paper's own set-ups as extra workloads (Sections 5.5 and 5.6), both
+    """The paper's own set-ups as extra workloads (Sections 5.5 and 5.7), both
     precisions at CFL 0.45, advanced in chunks of fv_step_timed to the end
     time: the dam break with impact against a vertical wall (1000 x 500, to
     t = 1) and the sharp-crested weir (800 x 250, to t = 0.18: at t = 0.19-0.21

@@ -9,7 +9,7 @@ Physical set-ups follow the paper's test problems (Section 5):
   * liquid at rest in hydrostatic balance, rho = rho0 exp(-g rho0 (y - y0) / k0)
     (Eq. BNs_eq3 and the dam-break initial density, Section 5.5);
   * gas at p = 0, rho = rho0, u = 0 with volume fraction eps (Section 5 preamble);
-  * obstacles are cells removed from the domain (Section 5.1, 5.4);
+  * obstacles are cells removed from the domain (Sections 5.1 and 5.5);
   * k0 from the Mach-0.3 rule k0 = rho0 (2 sqrt(g H) / 0.3)^2, which reproduces
     the paper's 6.54e5 (H = 1.5), 6.37e5 (H = 1.4618) and 2.62e5 (H = 0.6).
 
@@ -288,7 +288,7 @@ def weir_e5(nx: int = 800, ny: int = 250, cfl: float = 0.45) -> Case:
 
 
 def impact_e11(nx: int = 1000, ny: int = 500, cfl: float = 0.45) -> Case:
-    """Dam break and impact against a vertical wall (Section 5.6): [0,3.2] x
+    """Dam break and impact against a vertical wall (Section 5.7): [0,3.2] x
     [0,1.8], water [0,1.2] x [0,0.6] in hydrostatic balance, k0 = 2.62e5,
     walls on three sides and a transmissive top; the paper runs 1000 x 500
     to t = 1 (efficiency) and shows t = 0.6 .. 1.7."""

@@ -1,5 +1,5 @@
 """The paper's own set-ups as workloads: the dam break with impact against a
-vertical wall (Section 5.6; transmissive top) and the flow over a
+vertical wall (Section 5.7; transmissive top) and the flow over a
 sharp-crested weir (Section 5.5; a one-cell weir).
 
 On coarse grids the GPU path follows the oracle step for step (FP64 relative
