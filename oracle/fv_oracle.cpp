@@ -836,7 +836,8 @@ O1Node o1_node(const Model& M, const double fa[4], double aEa, const double fb[4
   return n;
 }
 
-// Primitive fluctuations at a node (reading G24 of the survey): rho^f, alpha^f.
+// Primitive fluctuations at a path node: rho^f, alpha^f.  The path is linear
+// in the conserved fluctuations; the primitive ones are derived at each node.
 double o1_rhof(const O1Node& n) { return (n.f[0] - n.rhoE * n.f[3]) / n.q[3]; }
 
 // B_Phi (b - a) on the segment a -> b: (0, 0, b3, b4, 0).
