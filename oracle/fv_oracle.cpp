@@ -79,9 +79,22 @@
 //   R-orx   the conservative Osher-Romberg x faces (Eq. (OR_cons)) complete
 //           each sub-segment's flux difference with b4x = u(Psi(s_k)) Delta
 //           alpha and use the Romberg average of u for the face's b4x.
+//   R-h     (an extension: the paper removes whole cells, so an obstacle's
+//           height has no derivative there) a fluid cell may carry a capacity
+//           c in (0, 1], the fluid part of a cell whose bottom theta = 1 - c
+//           is taken by the obstacle below it.  Its update is Eq. (Scheme) for
+//           a cell of height c dy holding the same reconstruction: an x face
+//           is open over min(c_left, c_right) dy (solid and outside count as
+//           0) and a cell sees the rest of its own part of that face as a
+//           wall; the x interior integral is unchanged; the y fluctuations and
+//           the y jump terms of the interior integral are divided by c, the
+//           gravity integral (proportional to the height) is not.  The
+//           levels and the CFL rate do not see c.  c = 1 everywhere is the
+//           paper's scheme, bit for bit.
 //
 // Parity-pinned by the tests listed next to each C entry point.
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -411,6 +424,7 @@ struct Ctx {
   double dt;
   int xsolver = 0;           // x faces: 0 Gauss-Legendre Osher (Eq. (OsherMatrixFormal_approx)),
                              // 1 conservative Osher-Romberg (Eq. (OR_cons))
+  const double* cap = nullptr;  // ny*nx fluid capacities of reading R-h; null = all 1
 };
 
 inline size_t at(const Grid& G, int i, int j) { return (size_t)j * G.nx + i; }
@@ -421,6 +435,12 @@ bool is_fluid(const Ctx& C, int i, int j) {
 }
 
 double kappa(const Model& M) { return M.g * M.rho0 / M.k0; }
+
+// Capacity of cell (i, j) under reading R-h: 0 when solid or outside the grid.
+double capacity(const Ctx& C, int i, int j) {
+  if (!is_fluid(C, i, j)) return 0.0;
+  return C.cap ? C.cap[at(C.G, i, j)] : 1.0;
+}
 
 // Equilibrium density at height y_L + h * dy / 2 above the bottom, relative to level K
 // (h counts half cells: faces are even, centres odd).
@@ -693,9 +713,11 @@ void yface(const Ctx& C, const Rec* B, const Rec* T, int jface, double Dm[4], do
   dfluct_y(C.M, fm, aEm, fp, aEp, rhoE, Dm, Dp);
 }
 
-// Eq. (Scheme) for one fluid cell with the interior integral of reading R-int.
+// Eq. (Scheme) for one fluid cell with the interior integral of reading R-int;
+// c_own < 1: the partial cell of reading R-h (DpW, DmE already weighted by the
+// open parts of its x faces).
 void update_cell(const Ctx& C, const Rec& r, int i, int j, const double DpW[4], const double DmE[4],
-                 const double DpS[4], const double DmN[4], double out[4]) {
+                 const double DpS[4], const double DmN[4], double out[4], double c_own = 1.0) {
   const Grid& G = C.G;
   const Model& M = C.M;
   const size_t n = (size_t)G.nx * G.ny;
@@ -724,11 +746,23 @@ void update_cell(const Ctx& C, const Rec& r, int i, int j, const double DpW[4], 
   const double af = fc[3];
   const double rhof = (fc[0] - r.rhoEc * af) / r.qc[3];
   const double gravity_part = (r.aE * rhof + af * r.rhoEc + af * rhof) * M.g * G.dy;
-  Iy[2] += pressure_part + gravity_part;
+  if (c_own == 1.0) {
+    Iy[2] += pressure_part + gravity_part;
+    Iy[3] += G.dy * wc.v * r.day;
+    for (int v = 0; v < 4; ++v) {
+      const double q0 = C.Q[v * n + at(G, i, j)];
+      out[v] = q0 - C.dt / G.dx * (DpW[v] + DmE[v] + Ix[v]) - C.dt / G.dy * (DpS[v] + DmN[v] + Iy[v]);
+    }
+    return;
+  }
+  // Reading R-h: a cell of height c_own dy; the jumps across it are those of
+  // the full cell, the gravity integral scales with its height.
+  Iy[2] += pressure_part;
   Iy[3] += G.dy * wc.v * r.day;
   for (int v = 0; v < 4; ++v) {
     const double q0 = C.Q[v * n + at(G, i, j)];
-    out[v] = q0 - C.dt / G.dx * (DpW[v] + DmE[v] + Ix[v]) - C.dt / G.dy * (DpS[v] + DmN[v] + Iy[v]);
+    const double ys = (DpS[v] + DmN[v] + Iy[v]) / c_own + (v == 2 ? gravity_part : 0.0);
+    out[v] = q0 - C.dt / G.dx * (DpW[v] + DmE[v] + Ix[v]) - C.dt / G.dy * ys;
   }
 }
 
@@ -787,7 +821,32 @@ int advance(Ctx& C, double* q_out) {
       if (fl[c]) {
         const size_t kw = (size_t)j * (G.nx + 1) + i, ke = kw + 1;
         const size_t ks = (size_t)j * G.nx + i, kn = (size_t)(j + 1) * G.nx + i;
-        update_cell(C, rec[c], i, j, &xp[4 * kw], &xm[4 * ke], &yp[4 * ks], &ym[4 * kn], out);
+        const double ci = capacity(C, i, j);
+        const double cw = capacity(C, i - 1, j), ce = capacity(C, i + 1, j);
+        const bool partial = ci != 1.0 || (cw != 0.0 && cw != 1.0) || (ce != 0.0 && ce != 1.0);
+        if (partial) {
+          // Reading R-h: x faces open over min(c, c_neighbour); the rest of the
+          // cell's own part of the face is a wall.
+          double DpW[4], DmE[4], wm[4], wp[4];
+          const double oW = std::min(ci, cw), oE = std::min(ci, ce);
+          const Rec* self = &rec[c];
+          double wallW[4] = {0, 0, 0, 0}, wallE[4] = {0, 0, 0, 0};
+          if (oW < ci) {
+            xface(C, nullptr, self, i, wm, wp);
+            std::memcpy(wallW, wp, sizeof wallW);
+          }
+          if (oE < ci) {
+            xface(C, self, nullptr, i + 1, wm, wp);
+            std::memcpy(wallE, wm, sizeof wallE);
+          }
+          for (int v = 0; v < 4; ++v) {
+            DpW[v] = (oW * xp[4 * kw + v] + (ci - oW) * wallW[v]) / ci;
+            DmE[v] = (oE * xm[4 * ke + v] + (ci - oE) * wallE[v]) / ci;
+          }
+          update_cell(C, rec[c], i, j, DpW, DmE, &yp[4 * ks], &ym[4 * kn], out, ci);
+        } else {
+          update_cell(C, rec[c], i, j, &xp[4 * kw], &xm[4 * ke], &yp[4 * ks], &ym[4 * kn], out);
+        }
         if (!admissible(out)) bad = 1;
       }
       for (int v = 0; v < 4; ++v) q_out[v * n + c] = out[v];
@@ -1079,18 +1138,25 @@ int orc_run(const int32_t* gi, const double* gd, const double* eos, const int32_
 // it (m_hist, nsteps*ngauges, nullable).  With dt_fix and K_fix (both given),
 // step s uses dt_fix[s] and the levels K_fix[s*nx ..] instead of those of its
 // state: the map whose derivative the gradient checks take by finite
-// differences.
+// differences.  cap (nullable, ny*nx): the fluid capacities of reading R-h
+// (second order only; each fluid cell's in (0, 1]).
 int orc_run_record(const int32_t* gi, const double* gd, const double* eos, const int32_t* sides,
                    const uint8_t* solid, const double* q_in, double* q_out, int nsteps,
                    double cfl, const double* dt_fix, const int32_t* K_fix, double* dt_hist,
                    int32_t* K_hist, const int64_t* gauges, int ngauges, double* m_hist,
-                   int scheme) {
+                   int scheme, const double* cap) {
   Ctx C = make_ctx(gi, gd, eos, sides, solid, q_in);
   if (!valid(C) || nsteps < 0 || !(cfl > 0.0) || (!dt_fix) != (!K_fix)) return 1;
   const int order = scheme & 15;
   C.xsolver = (scheme >> 4) & 1;
   if ((order != 1 && order != 2) || (scheme >> 5) != 0) return 1;
   const size_t n1 = (size_t)C.G.nx * C.G.ny, n4 = 4 * n1;
+  if (cap) {
+    if (order != 2) return 1;
+    for (size_t c = 0; c < n1; ++c)
+      if (!solid[c] && !(cap[c] > 0.0 && cap[c] <= 1.0)) return 1;
+    C.cap = cap;
+  }
   for (int g = 0; g < ngauges; ++g)
     if (gauges[g] < 0 || gauges[g] >= (int64_t)n1) return 1;
   std::vector<double> a(q_in, q_in + n4), b(n4);

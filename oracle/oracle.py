@@ -52,7 +52,7 @@ def lib():
                                          _D, _D]
             L.orc_step_cells.restype = C.c_int
             L.orc_run_record.argtypes = [_I32, _D, _D, _I32, _U8, _D, _D, C.c_int, C.c_double,
-                                         _D, _I32, _D, _I32, _I64, C.c_int, _D, C.c_int]
+                                         _D, _I32, _D, _I32, _I64, C.c_int, _D, C.c_int, _D]
             L.orc_dfluct_x_or.argtypes = [_D, _D, _D, _D, _D]
             L.orc_sign_A1_apply.argtypes = [_D, _D, _D, _D]
             L.orc_dfluct_y_o1.argtypes = [_D, _D, C.c_double, _D, C.c_double, C.c_double,
@@ -118,15 +118,16 @@ def run(case, nsteps: int, q=None, cfl: float | None = None):
 
 
 def run_record(case, nsteps: int, gauges, q=None, cfl: float | None = None, dt_fix=None,
-               K_fix=None, order: int = 2, xsolver: int = 0):
+               K_fix=None, order: int = 2, xsolver: int = 0, cap=None):
     """Advance ``nsteps`` steps of the scheme of ``order`` (2: Eq. (Scheme);
     1: the first-order scheme of Sections 3.2-3.3) with x faces by
     ``xsolver`` (0: Gauss-Legendre Osher; 1: conservative Osher-Romberg,
     Eq. (OR_cons)), recording each step's dt,
     levels and the alpha rho at the flat gauge cells after it.  With
     ``dt_fix`` (nsteps) and ``K_fix`` (nsteps, nx) the steps use those instead
-    of their own.  Returns (q_out, dt (nsteps), K (nsteps, nx), m (nsteps,
-    ngauges))."""
+    of their own.  ``cap`` (ny, nx), second order only: the fluid capacities
+    of reading R-h (a partial cell on top of an obstacle; 1 = a whole cell).
+    Returns (q_out, dt (nsteps), K (nsteps, nx), m (nsteps, ngauges))."""
     L = lib()
     gi, gd, eos, sides, solid = _case_args(case)
     qin = np.ascontiguousarray(case.q if q is None else q, dtype=np.float64)
@@ -140,11 +141,15 @@ def run_record(case, nsteps: int, gauges, q=None, cfl: float | None = None, dt_f
         raise ValueError("give both dt_fix and K_fix or neither")
     dfix = None if dt_fix is None else np.ascontiguousarray(dt_fix, dtype=np.float64)
     kfix = None if K_fix is None else np.ascontiguousarray(K_fix, dtype=np.int32)
+    cp = None if cap is None else np.ascontiguousarray(cap, dtype=np.float64)
+    if cp is not None and cp.shape != (case.ny, case.nx):
+        raise ValueError("cap must be (ny, nx)")
     rc = L.orc_run_record(_p(gi, _I32), _p(gd), _p(eos), _p(sides, _I32), _p(solid, _U8),
                           _p(qin), _p(qout), int(nsteps), float(case.cfl if cfl is None else cfl),
                           None if dfix is None else _p(dfix),
                           None if kfix is None else _p(kfix, _I32), _p(dts), _p(Ks, _I32),
-                          _p(g, _I64), int(g.size), _p(ms), int(order) | (int(xsolver) << 4))
+                          _p(g, _I64), int(g.size), _p(ms), int(order) | (int(xsolver) << 4),
+                          None if cp is None else _p(cp))
     if rc == 1:
         raise OracleError("invalid input")
     if rc == 2:

@@ -198,6 +198,37 @@ def c5_directions(c: Case, count: int = 32, seed: int = 32) -> np.ndarray:
     return d
 
 
+H_RECT = (0.7, 0.9, 0.0, 0.2)
+
+
+def heights(nx: int = 48, ny: int = 24, steps: int = 60, cfl: float = 0.45) -> Case:
+    """Obstacle-height gradient workload: a 2 x 1 box, water column [0, 1] x
+    [0, 0.6] with the 0.2 x 0.2 obstacle H_RECT inside it (k0 = 4.36e5), so
+    that the water over the obstacle's top moves from the first step."""
+    return dambreak(nx, ny, lx=2.0, ly=1.0, x_col=1.0, h_col=0.6, rects=[H_RECT], k0=4.36e5,
+                    cfl=cfl, steps=steps, name=f"heights_{nx}x{ny}")
+
+
+def height_ids(c: Case, rects=None) -> np.ndarray:
+    """Height parameters of obstacles: an int32 (ny, nx) map holding k at the
+    fluid cells that sit directly on the top solid cell of rectangle k's
+    columns (rects default to the case's own, ``meta['rects']``), -1 elsewhere.
+    Raising obstacle k by theta dy turns those cells into the partial cells
+    of reading R-h."""
+    rects = c.meta.get("rects", []) if rects is None else rects
+    out = np.full((c.ny, c.nx), -1, dtype=np.int32)
+    xc, yc = c.xc(), c.yc()
+    for k, (xl, xr, yb, yt) in enumerate(rects):
+        for i in np.flatnonzero((xc >= xl) & (xc <= xr)):
+            rows = np.flatnonzero((yc >= yb) & (yc <= yt) & (c.solid[:, i] == 1))
+            if rows.size == 0:
+                continue
+            j = int(rows.max()) + 1
+            if j < c.ny and c.solid[j, i] == 0:
+                out[j, i] = k
+    return out
+
+
 def generic(c: Case, seed: int, scale: float = 1e-3) -> Case:
     """``perturbed`` plus a seeded perturbation of the volume fraction
     (liquid alpha = 1 - scale U(0,1), gas alpha = eps (1 + 0.1 N(0,1)) clipped
