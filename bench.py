@@ -325,14 +325,15 @@ def measure_e2e(fv, case, prec, steps):
 def measure_adjoint(fv, cases_mod, prec, nsteps, stream_sync):
     """Config 5: the dam break of config 1 at 512 x 256 (k0 = 4.36e5, CFL 0.45),
     gauge loss over `nsteps` steps at 16 seeded gauges, gradient with respect to
-    the initial state by fv_adjoint (sqrt(N) checkpoints, one replay of the
-    forward sweep).  The target record is the gauges' initial alpha rho held
-    constant (the cost does not depend on it).  Cost ratio = device time of
-    fv_adjoint (forward sweep + reverse sweep) / device time of fv_step over
-    the same steps."""
+    the initial state and the obstacle's height by fv_adjoint (sqrt(N)
+    checkpoints, one replay of the forward sweep).  The target record is the
+    gauges' initial alpha rho held constant (the cost does not depend on it).
+    Cost ratio = device time of fv_adjoint (forward sweep + reverse sweep) /
+    device time of fv_step over the same steps."""
     import numpy as np
     c = cases_mod.c5(512, 256)
     g = cases_mod.c5_gauges(c)
+    hid = cases_mod.height_ids(c)
     target = np.repeat(c.q[0].ravel()[g][None, :], nsteps, axis=0)
     s = fv.Solver(c, prec)
     s.set_state(c.q)
@@ -340,11 +341,11 @@ def measure_adjoint(fv, cases_mod, prec, nsteps, stream_sync):
     s.set_state(c.q)
     _, fwd_ms = s.step_timed(nsteps, c.cfl)
     s.set_state(c.q)
-    s.adjoint(min(nsteps, 20), g, target[:min(nsteps, 20)], cfl=c.cfl)   # warm the path
+    s.adjoint_heights(min(nsteps, 20), g, target[:min(nsteps, 20)], hid, cfl=c.cfl)   # warm the path
     s.set_state(c.q)
     stream_sync()
     t0 = time.perf_counter()
-    grad, info, _ = s.adjoint(nsteps, g, target, cfl=c.cfl)
+    grad, dh, info, _ = s.adjoint_heights(nsteps, g, target, hid, cfl=c.cfl)
     wall = time.perf_counter() - t0
     s.close()
     adj_ms = info.forward_ms + info.reverse_ms
@@ -355,7 +356,8 @@ def measure_adjoint(fv, cases_mod, prec, nsteps, stream_sync):
             "replayed_steps": info.recomputed_steps,
             "mcups_forward": cells * nsteps / (fwd_ms * 1e-3) / 1e6,
             "mcups_gradient": cells * nsteps / (adj_ms * 1e-3) / 1e6,
-            "finite_fraction": float(np.isfinite(grad).mean()), "loss": info.loss}
+            "finite_fraction": float(np.isfinite(grad).mean()), "loss": info.loss,
+            "dL_dh": float(dh[0]), "height_cells": int((hid >= 0).sum())}
 
 
 def adjoint_block(fv, cases_mod, na, stream_sync):

@@ -206,6 +206,22 @@ typedef struct {
   const double* target;     /* host, N*ngauges: T_g^n at [(n-1)*ngauges + g] */
   int32_t checkpoint_every; /* >= 0; 0 = ceil(sqrt(N)) */
   double* m_series;         /* nullable host, N*ngauges: receives m_g^n */
+  /* Obstacle heights (optional; nheights = 0 for none).  The paper removes
+   * whole cells for an obstacle, so its height has no derivative in the
+   * scheme; the derivative returned is that of the extension in which
+   * raising obstacle k by theta dy leaves the fluid cell on each of its top
+   * cells a capacity 1 - theta: its x faces open over min(c_left, c_right) dy
+   * (a neighbour sees the closed part as a wall), its y fluctuations and the
+   * y jump terms of the interior integral divided by the capacity, the
+   * gravity integral not.  theta = 0 is the scheme of Eq. (Scheme), and the
+   * value is the one-sided derivative d/dh_k at the grid-aligned heights
+   * (raising), with dt_n and K_i^n held as for dL_dq0. */
+  int32_t nheights;         /* >= 0 */
+  const int32_t* height_id; /* host, ny*nx, null iff nheights = 0: k in [0, nheights) at the
+                               fluid cells resting on obstacle k (the cell below is solid),
+                               -1 elsewhere */
+  double* dL_dh;            /* host, nheights, null iff nheights = 0: receives dL/dh_k (per
+                               metre of height; 0 for a k with no cells) */
 } fv_adjoint_spec;
 
 typedef struct {
@@ -221,7 +237,8 @@ typedef struct {
  * doubles, layout of fv_set_state, zero in solid cells; host (on_device = 0)
  * or device memory (1).  info: nullable.  Synchronises.  FV_EINVAL on bad
  * arguments (a gauge outside the grid or in a solid cell, a non-finite
- * target), FV_ENONFINITE if a forward step produced a non-admissible state,
+ * target, a height_id entry out of range or on a cell that is not a fluid
+ * cell resting on a solid one), FV_ENONFINITE if a forward step produced a non-admissible state,
  * FV_ENOMEM if the workspace (about (2 sqrt(N) + 20) state-sized buffers)
  * cannot be allocated. */
 fv_status fv_adjoint(fv_handle* h, const fv_adjoint_spec* spec, double* dL_dq0, int on_device,

@@ -89,6 +89,20 @@ int fv_host_adjoint_step(const fv_grid* grid, const fv_eos* eos, const int32_t s
                          const uint8_t* solid, const double* q, const int32_t* K, double dt,
                          const double* lam, double* lam_out, int prec);
 
+/* Obstacle-height part of one reverse step on the host, through the same
+ * per-cell code as fv_adjoint's kernel: out[k] = lam . dQ^{n+1}/dtheta_k at
+ * theta = 0+, where raising obstacle k by theta dy gives its top cells
+ * (height_id as in fv_adjoint_spec) the capacity 1 - theta (the extension
+ * documented with fv_adjoint_spec).  Arguments as fv_host_adjoint_step; lam is
+ * the adjoint of Q^{n+1} in the storage form of prec (FV_FP64: the full
+ * state; FV_FP32_DEV: (alpha rho - alpha rho^E, alpha rho u, alpha rho v,
+ * alpha) with rho^E from the levels K); out: nheights doubles.  Returns 0, or
+ * 1 on a bad argument. */
+int fv_host_height_step(const fv_grid* grid, const fv_eos* eos, const int32_t side[4],
+                        const uint8_t* solid, const double* q, const int32_t* K, double dt,
+                        const double* lam, const int32_t* height_id, int nheights, double* out,
+                        int prec);
+
 #ifdef __cplusplus
 }
 #endif

@@ -579,6 +579,166 @@ __global__ void __launch_bounds__(BX * BY) adj_gather_kernel(AdjArgs<T> A) {
   if (i < A.nx && j < A.ny) gather_body<T>(A, i, j);
 }
 
+// ------------------------------------------------------------------ heights
+// Derivative of one step with respect to obstacle heights, at theta = 0+ of
+// the extension in which raising obstacle k by theta dy leaves each of its
+// top fluid cells P the capacity c = 1 - theta.  With every face value of the
+// step fixed, only the update's weights move:
+//   P:  x terms (open length c dy over volume c dx dy) unchanged; y terms
+//       D+_S + D-_N + (y jumps of the interior integral) divided by c; the
+//       gravity integral (proportional to the height) unchanged, so
+//       dQ_P/dtheta = -dt/dy (D+_S + D-_N + jumps);
+//   F:  a fluid x neighbour of P that is not a top cell of the same obstacle
+//       sees its face open over c dy and closed (a wall) over theta dy:
+//       dQ_F/dtheta = dt/dx (D_F(face) - D_F(wall)).
+// The contribution of P to dL/dtheta_k at step n is lambda^n . dQ^n/dtheta
+// in storage form.
+
+// The y terms of the interior integral (interior_terms) without the gravity
+// integral g dy (alpha rho)^f.
+template <typename T>
+__host__ __device__ __forceinline__ void y_jumps(const T fS[4], const T fN[4], const T base[4],
+                                                 T mEc, T mES, T mEN, T day, T dy,
+                                                 const Phys<T>& P, T Iy[4]) {
+  const Vel<T> vN = velocity(mEN + fN[0], fN[1], fN[2]);
+  const Vel<T> vS = velocity(mES + fS[0], fS[1], fS[2]);
+  const Vel<T> vc = velocity(mEc + base[0], base[1], base[2]);
+  Iy[0] = fN[2] - fS[2];
+  Iy[1] = fN[1] * vN.v - fS[1] * vS.v;
+  Iy[2] = (fN[2] * vN.v - fS[2] * vS.v) + P.c2 * ((fN[0] - fS[0]) - P.rho0 * (fN[3] - fS[3]));
+  Iy[3] = dy * vc.v * day;
+}
+
+// lambda . dq for a storage-form derivative (the deviation form stores
+// alpha rho - alpha rho^E_c, so da also moves the first component).
+template <typename T, bool DEV>
+__host__ __device__ __forceinline__ double lam_dot(const AdjArgs<T>& A, size_t c, const T d[4], T rEc) {
+  const size_t N = (size_t)A.nx * A.ny;
+  const T d0 = DEV ? d[0] - rEc * d[3] : d[0];
+  return A.lam[c] * (double)d0 + A.lam[N + c] * (double)d[1] + A.lam[2 * N + c] * (double)d[2] +
+         A.lam[3 * N + c] * (double)d[3];
+}
+
+// Contribution of top cell c (hid[c] = k >= 0) to dL/dtheta_k at this step;
+// A.rec holds the step's records, A.lam the adjoint of Q^n.
+template <typename T, bool DEV>
+__host__ __device__ double height_body(const AdjArgs<T>& A, const int32_t* hid, int64_t c) {
+  const int nx = A.nx, ny = A.ny;
+  const size_t N = (size_t)nx * ny;
+  const int i = (int)(c % nx), j = (int)(c / nx);
+  const int k = hid[c];
+  const Phys<T>& P = A.kc.P;
+  const T rdx = A.dt / A.kc.dx, rdy = A.dt / A.kc.dy;
+  CellRec<T> C;
+  recon_cell<T, DEV>(A, i, j, C);
+  T Dm[4], Dp[4], qm[4], qp[4], dq[4];
+  // south face: the obstacle's top, a wall below P
+  const T* fs = C.fo[2];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) qp[v] = fs[v];
+  qp[0] += C.mES;
+  qp[3] += C.aE;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) qm[v] = qp[v];
+  qm[2] = -qp[2];
+  dq[0] = T(0);
+  dq[1] = T(0);
+  dq[2] = qp[2] - qm[2];
+  dq[3] = T(0);
+  yface(qm, qp, dq, T(0), P, Dm, Dp);
+  T ys[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) ys[v] = Dp[v];
+  // north face
+  const T* fb = C.fo[3];
+  if (fluid_at(A, i, j + 1)) {
+    const size_t cT = (size_t)c + nx;
+    const T mET = A.rec[R_MES * N + cT], aT = A.rec[R_AE * N + cT];
+    T ft[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) ft[v] = A.rec[(R_FS + v) * N + cT];
+    qm[0] = C.mEN + fb[0]; qm[1] = fb[1]; qm[2] = fb[2]; qm[3] = C.aE + fb[3];
+    qp[0] = mET + ft[0]; qp[1] = ft[1]; qp[2] = ft[2]; qp[3] = aT + ft[3];
+    dq[0] = (mET - C.mEN) + (ft[0] - fb[0]);
+    dq[1] = ft[1] - fb[1];
+    dq[2] = ft[2] - fb[2];
+    dq[3] = (aT - C.aE) + (ft[3] - fb[3]);
+    const T rEf = tab(A.rt, 2 * (j + 1 - A.Kcur[i]), ny);
+    const T dap = P.c2 * ((rEf - P.rho0) * (aT - C.aE) + ((ft[0] - fb[0]) - P.rho0 * (ft[3] - fb[3])));
+    yface(qm, qp, dq, dap, P, Dm, Dp);
+  } else {
+    qm[0] = C.mEN + fb[0]; qm[1] = fb[1]; qm[2] = fb[2]; qm[3] = C.aE + fb[3];
+    const bool tr = j + 1 == ny && A.side[3] == 1;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) qp[v] = qm[v];
+    if (!tr) qp[2] = -qm[2];
+    dq[0] = T(0);
+    dq[1] = T(0);
+    dq[2] = qp[2] - qm[2];
+    dq[3] = T(0);
+    yface(qm, qp, dq, T(0), P, Dm, Dp);
+  }
+  T Iy[4], d[4];
+  y_jumps(C.fo[2], C.fo[3], C.base, C.mEc, C.mES, C.mEN, C.ga[1], A.kc.dy, P, Iy);
+#pragma unroll
+  for (int v = 0; v < 4; ++v) d[v] = -rdy * (ys[v] + Dm[v] + Iy[v]);
+  double acc = lam_dot<T, DEV>(A, (size_t)c, d, C.rEc);
+  // x neighbours: west (side 0) and east (side 1)
+#pragma unroll
+  for (int sd = 0; sd < 2; ++sd) {
+    const int fi = sd == 0 ? i - 1 : i + 1;
+    if (!fluid_at(A, fi, j)) continue;
+    const size_t cF = (size_t)j * nx + fi;
+    if (hid[cF] == k) continue;
+    const T mEF = A.rec[R_MEC * N + cF], aF = A.rec[R_AE * N + cF];
+    T fF[4];
+    const int bs = sd == 0 ? R_FE : R_FW;  // F's face state toward P
+#pragma unroll
+    for (int v = 0; v < 4; ++v) fF[v] = A.rec[(bs + v) * N + cF];
+    const T* fP = C.fo[sd == 0 ? 0 : 1];   // P's face state toward F
+    T qF[4] = {mEF + fF[0], fF[1], fF[2], aF + fF[3]};
+    T qP[4] = {C.mEc + fP[0], fP[1], fP[2], C.aE + fP[3]};
+    const T* ql = sd == 0 ? qF : qP;
+    const T* qr = sd == 0 ? qP : qF;
+    const T* fl = sd == 0 ? fF : fP;
+    const T* fr = sd == 0 ? fP : fF;
+    const T mEl = sd == 0 ? mEF : C.mEc, mEr = sd == 0 ? C.mEc : mEF;
+    const T al = sd == 0 ? aF : C.aE, ar = sd == 0 ? C.aE : aF;
+    dq[0] = (mEr - mEl) + (fr[0] - fl[0]);
+    dq[1] = fr[1] - fl[1];
+    dq[2] = fr[2] - fl[2];
+    dq[3] = (ar - al) + (fr[3] - fl[3]);
+    xface(ql, qr, dq, P, Dm, Dp);
+    T DF[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) DF[v] = sd == 0 ? Dm[v] : Dp[v];
+    // the same face closed, seen from F
+    T g[4] = {qF[0], -qF[1], qF[2], qF[3]};
+    const T* wl = sd == 0 ? qF : g;
+    const T* wr = sd == 0 ? g : qF;
+    dq[0] = T(0);
+    dq[1] = wr[1] - wl[1];
+    dq[2] = T(0);
+    dq[3] = T(0);
+    xface(wl, wr, dq, P, Dm, Dp);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) d[v] = rdx * (DF[v] - (sd == 0 ? Dm[v] : Dp[v]));
+    const T rEcF = tab(A.rt, 2 * (j - A.Kcur[fi]) + 1, ny);
+    acc += lam_dot<T, DEV>(A, cF, d, rEcF);
+  }
+  return acc;
+}
+
+// hacc[p] += the contribution of top cell hcell[p] at this step (one writer
+// per entry; the per-obstacle sums are taken on the host in list order).
+template <typename T, bool DEV>
+__global__ void __launch_bounds__(128) adj_height_kernel(AdjArgs<T> A, const int64_t* hcell,
+                                                         int nh, const int32_t* hid,
+                                                         double* hacc) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < nh) hacc[p] += height_body<T, DEV>(A, hid, hcell[p]);
+}
+
 // ------------------------------------------------------------------ small kernels
 // Loss source of step n: d/dm_g of dt_n (m_g - T_g)^2, gauges in order.
 __global__ void adj_source_kernel(double* lam, const int64_t* gauges, int ng, const double* m,
@@ -691,7 +851,7 @@ void launch_replay_step(const StepParams& p, const T* in, T* out, const uint8_t*
 
 template <typename T, bool DEV>
 fv_status run_adjoint(fv_handle* h, const fv_adjoint_spec* spec, double* grad, int on_device,
-                      fv_adjoint_info* info) {
+                      fv_adjoint_info* info, const std::vector<int64_t>& hcell_h) {
   const int nx = h->grid.nx, ny = h->grid.ny, Nst = spec->nsteps, ng = spec->ngauges;
   const size_t N = h->ncell;
   const size_t qbytes = 4 * N * sizeof(T);
@@ -716,7 +876,11 @@ fv_status run_adjoint(fv_handle* h, const fv_adjoint_spec* spec, double* grad, i
       contrib.alloc(sizeof(T) * NCONTRIB * N) && rsc.alloc(sizeof(DevScalars)) &&
       rcol.alloc(sizeof(unsigned long long) * nx) && gmark.alloc(sizeof(int32_t) * N) &&
       gord.alloc(sizeof(int32_t) * ng);
-  if (!ok) {
+  const int nh = (int)hcell_h.size();
+  DevBuf hcell, hid, hacc;
+  const bool okh = nh == 0 || (hcell.alloc(sizeof(int64_t) * nh) &&
+                               hid.alloc(sizeof(int32_t) * N) && hacc.alloc(sizeof(double) * nh));
+  if (!ok || !okh) {
     set_last_error("fv_adjoint: device allocation failed");
     return FV_ENOMEM;
   }
@@ -740,6 +904,11 @@ fv_status run_adjoint(fv_handle* h, const fv_adjoint_spec* spec, double* grad, i
   for (int k = ng - 1; k >= 0; --k) mark_h[spec->gauges[ord_h[k]]] = k;
   ADJ_CUDA(cudaMemcpyAsync(gord.p, ord_h.data(), sizeof(int32_t) * ng, cudaMemcpyHostToDevice, st));
   ADJ_CUDA(cudaMemcpyAsync(gmark.p, mark_h.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, st));
+  if (nh > 0) {
+    ADJ_CUDA(cudaMemcpyAsync(hcell.p, hcell_h.data(), sizeof(int64_t) * nh, cudaMemcpyHostToDevice, st));
+    ADJ_CUDA(cudaMemcpyAsync(hid.p, spec->height_id, sizeof(int32_t) * N, cudaMemcpyHostToDevice, st));
+    ADJ_CUDA(cudaMemsetAsync(hacc.p, 0, sizeof(double) * nh, st));
+  }
   ADJ_CUDA(cudaMemsetAsync(rsc.p, 0, sizeof(DevScalars), st));
   ADJ_CUDA(cudaMemsetAsync(rcol.p, 0, sizeof(unsigned long long) * nx, st));
   int32_t* Kh = Khist.as<int32_t>();
@@ -870,6 +1039,9 @@ fv_status run_adjoint(fv_handle* h, const fv_adjoint_spec* spec, double* grad, i
       A.lam = lam;
       A.lam_out = lam2;
       launch_reverse_step<T, DEV>(A, st);
+      if (nh > 0)  // reads the step's records and the adjoint of Q^n
+        adj_height_kernel<T, DEV><<<(nh + 127) / 128, 128, 0, st>>>(
+            A, hcell.as<int64_t>(), nh, hid.as<int32_t>(), hacc.as<double>());
       std::swap(lam, lam2);
     }
     ADJ_CUDA(cudaEventRecord(ev_rev[k % 2].e, st));
@@ -878,7 +1050,16 @@ fv_status run_adjoint(fv_handle* h, const fv_adjoint_spec* spec, double* grad, i
   ADJ_CUDA(cudaEventRecord(evr.b, st));
   ADJ_CUDA(cudaMemcpyAsync(grad, lam, sizeof(double) * 4 * N,
                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  std::vector<double> hacc_h(nh);
+  if (nh > 0)
+    ADJ_CUDA(cudaMemcpyAsync(hacc_h.data(), hacc.p, sizeof(double) * nh, cudaMemcpyDeviceToHost, st));
   ADJ_CUDA(cudaStreamSynchronize(st));
+  if (spec->nheights > 0) {
+    // dL/dh_k = (1/dy) sum of the top cells' dL/dtheta_k, in list order
+    for (int k = 0; k < spec->nheights; ++k) spec->dL_dh[k] = 0.0;
+    for (int q = 0; q < nh; ++q) spec->dL_dh[spec->height_id[hcell_h[q]]] += hacc_h[q];
+    for (int k = 0; k < spec->nheights; ++k) spec->dL_dh[k] /= h->grid.dy;
+  }
   if (info) {
     float fms = 0.f, rms = 0.f;
     ADJ_CUDA(cudaEventElapsedTime(&fms, evf.a, evf.b));
@@ -900,50 +1081,87 @@ fv_status run_adjoint(fv_handle* h, const fv_adjoint_spec* spec, double* grad, i
 namespace fv {
 namespace {
 
+// Top cells named by height_id, in cell order; false on an invalid map.
+bool height_cells(int nx, int ny, const uint8_t* solid, int nheights, const int32_t* height_id,
+                  const double* dL_dh, std::vector<int64_t>& out) {
+  out.clear();
+  if (nheights < 0 || (nheights > 0) != (height_id != nullptr) ||
+      (nheights > 0) != (dL_dh != nullptr))
+    return false;
+  if (nheights == 0) return true;
+  const size_t N = (size_t)nx * ny;
+  for (size_t c = 0; c < N; ++c) {
+    const int32_t k = height_id[c];
+    if (k == -1) continue;
+    if (k < -1 || k >= nheights) return false;
+    if (solid[c] || c < (size_t)nx || !solid[c - nx]) return false;
+    out.push_back((int64_t)c);
+  }
+  return true;
+}
+
+// Buffers and arguments of one reverse step on the host.
+template <typename T, bool DEV>
+struct HostStep {
+  std::vector<double> rtd;
+  std::vector<T> rt, qs, rec, slot, contrib;
+  AdjArgs<T> A;
+  HostStep(const StepParams& p, const int32_t* side, const uint8_t* solid, const double* q,
+           const int32_t* K, double dt, const double* lam) {
+    const int nx = p.nx, ny = p.ny;
+    const size_t N = (size_t)nx * ny;
+    rtd.resize(4 * (size_t)ny + 1);
+    for (long h2 = -2L * ny; h2 <= 2L * ny; ++h2)
+      rtd[h2 + 2L * ny] = p.rho0 * std::exp(-p.kappa * (0.5 * (double)h2) * p.dy);
+    rt.resize(rtd.size());
+    qs.resize(4 * N);
+    rec.assign(NREC * N, T(0));
+    slot.assign(NSLOT * N, T(0));
+    contrib.assign(NCONTRIB * N, T(0));
+    for (size_t k = 0; k < rtd.size(); ++k) rt[k] = (T)rtd[k];
+    // storage form: the full state (FP64) or m^f = m - alpha rho^E relative to K (deviation form)
+    for (size_t c = 0; c < N; ++c) {
+      const int i = (int)(c % nx), j = (int)(c / nx);
+      const double m =
+          solid[c] ? 0.0 : q[c] - (DEV ? q[3 * N + c] * rtd[2 * (j - K[i]) + 1 + 2 * ny] : 0.0);
+      qs[c] = (T)m;
+      for (int v = 1; v < 4; ++v) qs[v * N + c] = (T)q[v * N + c];
+    }
+    A.nx = nx;
+    A.ny = ny;
+    for (int k = 0; k < 4; ++k) A.side[k] = side[k];
+    A.kc = make_consts<T>(p);
+    A.dt = (T)dt;
+    A.kc.R.half_dt = T(0.5) * A.dt;
+    A.q = qs.data();
+    A.solid = solid;
+    A.Kref = K;
+    A.Kcur = K;
+    A.rt = rt.data();
+    A.lam = lam;
+    A.rec = rec.data();
+    A.slot = slot.data();
+    A.contrib = contrib.data();
+    A.lam_out = nullptr;
+    A.gmark = nullptr;
+    A.gord = nullptr;
+    A.gauges = nullptr;
+    A.ng = 0;
+    A.src_m = A.src_t = nullptr;
+    A.src_dt = 0.0;
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) rec_body<T, DEV>(A, i, j);
+  }
+};
+
 template <typename T, bool DEV>
 void host_reverse_step(const StepParams& p, const int32_t* side, const uint8_t* solid,
                        const double* q, const int32_t* K, double dt, const double* lam,
                        double* lam_out) {
-  const int nx = p.nx, ny = p.ny;
-  const size_t N = (size_t)nx * ny;
-  std::vector<double> rtd(4 * (size_t)ny + 1);
-  for (long h2 = -2L * ny; h2 <= 2L * ny; ++h2)
-    rtd[h2 + 2L * ny] = p.rho0 * std::exp(-p.kappa * (0.5 * (double)h2) * p.dy);
-  std::vector<T> rt(rtd.size()), qs(4 * N), rec(NREC * N, T(0)), slot(NSLOT * N, T(0)),
-      contrib(NCONTRIB * N, T(0));
-  for (size_t k = 0; k < rtd.size(); ++k) rt[k] = (T)rtd[k];
-  // storage form: the full state (FP64) or m^f = m - alpha rho^E relative to K (deviation form)
-  for (size_t c = 0; c < N; ++c) {
-    const int i = (int)(c % nx), j = (int)(c / nx);
-    const double m = solid[c] ? 0.0 : q[c] - (DEV ? q[3 * N + c] * rtd[2 * (j - K[i]) + 1 + 2 * ny] : 0.0);
-    qs[c] = (T)m;
-    for (int v = 1; v < 4; ++v) qs[v * N + c] = (T)q[v * N + c];
-  }
-  AdjArgs<T> A;
-  A.nx = nx;
-  A.ny = ny;
-  for (int k = 0; k < 4; ++k) A.side[k] = side[k];
-  A.kc = make_consts<T>(p);
-  A.dt = (T)dt;
-  A.kc.R.half_dt = T(0.5) * A.dt;
-  A.q = qs.data();
-  A.solid = solid;
-  A.Kref = K;
-  A.Kcur = K;
-  A.rt = rt.data();
-  A.lam = lam;
-  A.rec = rec.data();
-  A.slot = slot.data();
-  A.contrib = contrib.data();
+  HostStep<T, DEV> H(p, side, solid, q, K, dt, lam);
+  AdjArgs<T>& A = H.A;
   A.lam_out = lam_out;
-  A.gmark = nullptr;
-  A.gord = nullptr;
-  A.gauges = nullptr;
-  A.ng = 0;
-  A.src_m = A.src_t = nullptr;
-  A.src_dt = 0.0;
-  for (int j = 0; j < ny; ++j)
-    for (int i = 0; i < nx; ++i) rec_body<T, DEV>(A, i, j);
+  const int nx = p.nx, ny = p.ny;
   const long long nf = (long long)(nx + 1) * ny + (long long)nx * (ny + 1);
   for (long long f = 0; f < nf; ++f) face_body<T>(A, f);
   for (int j = 0; j < ny; ++j)
@@ -952,18 +1170,7 @@ void host_reverse_step(const StepParams& p, const int32_t* side, const uint8_t* 
     for (int i = 0; i < nx; ++i) gather_body<T>(A, i, j);
 }
 
-}  // namespace
-}  // namespace fv
-
-// One reverse step on the host through the same per-cell and per-face bodies
-// as the kernels; see fv_model_host.h.
-extern "C" int fv_host_adjoint_step(const fv_grid* grid, const fv_eos* eos, const int32_t side[4],
-                                    const uint8_t* solid, const double* q, const int32_t* K,
-                                    double dt, const double* lam, double* lam_out, int prec) {
-  using namespace fv;
-  if (!grid || !eos || !side || !solid || !q || !K || !lam || !lam_out) return 1;
-  if (grid->nx < 1 || grid->ny < 1 || eos->gamma != 1.0) return 1;
-  if (prec != FV_FP64 && prec != FV_FP32_DEV) return 1;
+StepParams host_params(const fv_grid* grid, const fv_eos* eos, const int32_t side[4]) {
   StepParams p;
   p.nx = grid->nx;
   p.ny = grid->ny;
@@ -978,8 +1185,52 @@ extern "C" int fv_host_adjoint_step(const fv_grid* grid, const fv_eos* eos, cons
   p.kappa = eos->g * eos->rho0 / eos->k0;
   for (int s = 0; s < 4; ++s) p.side[s] = side[s];
   p.cfl = 0.0;
+  return p;
+}
+
+template <typename T, bool DEV>
+void host_height_step(const StepParams& p, const int32_t* side, const uint8_t* solid,
+                      const double* q, const int32_t* K, double dt, const double* lam,
+                      const int32_t* hid, const std::vector<int64_t>& hcell, int nheights,
+                      double* out) {
+  HostStep<T, DEV> H(p, side, solid, q, K, dt, lam);
+  for (int k = 0; k < nheights; ++k) out[k] = 0.0;
+  for (int64_t c : hcell) out[hid[c]] += height_body<T, DEV>(H.A, hid, c);
+}
+
+}  // namespace
+}  // namespace fv
+
+// One reverse step on the host through the same per-cell and per-face bodies
+// as the kernels; see fv_model_host.h.
+extern "C" int fv_host_adjoint_step(const fv_grid* grid, const fv_eos* eos, const int32_t side[4],
+                                    const uint8_t* solid, const double* q, const int32_t* K,
+                                    double dt, const double* lam, double* lam_out, int prec) {
+  using namespace fv;
+  if (!grid || !eos || !side || !solid || !q || !K || !lam || !lam_out) return 1;
+  if (grid->nx < 1 || grid->ny < 1 || eos->gamma != 1.0) return 1;
+  if (prec != FV_FP64 && prec != FV_FP32_DEV) return 1;
+  const StepParams p = host_params(grid, eos, side);
   if (prec == FV_FP64) host_reverse_step<double, false>(p, side, solid, q, K, dt, lam, lam_out);
   else host_reverse_step<float, true>(p, side, solid, q, K, dt, lam, lam_out);
+  return 0;
+}
+
+extern "C" int fv_host_height_step(const fv_grid* grid, const fv_eos* eos, const int32_t side[4],
+                                   const uint8_t* solid, const double* q, const int32_t* K,
+                                   double dt, const double* lam, const int32_t* height_id,
+                                   int nheights, double* out, int prec) {
+  using namespace fv;
+  if (!grid || !eos || !side || !solid || !q || !K || !lam || !height_id || !out) return 1;
+  if (grid->nx < 1 || grid->ny < 1 || eos->gamma != 1.0 || nheights < 1) return 1;
+  if (prec != FV_FP64 && prec != FV_FP32_DEV) return 1;
+  std::vector<int64_t> hcell;
+  if (!height_cells(grid->nx, grid->ny, solid, nheights, height_id, out, hcell)) return 1;
+  const StepParams p = host_params(grid, eos, side);
+  if (prec == FV_FP64)
+    host_height_step<double, false>(p, side, solid, q, K, dt, lam, height_id, hcell, nheights, out);
+  else
+    host_height_step<float, true>(p, side, solid, q, K, dt, lam, height_id, hcell, nheights, out);
   return 0;
 }
 
@@ -1024,6 +1275,14 @@ extern "C" fv_status fv_adjoint(fv_handle* h, const fv_adjoint_spec* spec, doubl
       set_last_error("fv_adjoint: target values must be finite");
       return FV_EINVAL;
     }
-  if (h->prec == FV_FP64) return run_adjoint<double, false>(h, spec, dL_dq0, on_device, info);
-  return run_adjoint<float, true>(h, spec, dL_dq0, on_device, info);
+  std::vector<int64_t> hcell;
+  if (!height_cells(h->grid.nx, h->grid.ny, solid.data(), spec->nheights, spec->height_id,
+                    spec->dL_dh, hcell)) {
+    set_last_error("fv_adjoint: nheights >= 0; height_id and dL_dh given iff nheights > 0; "
+                   "height_id entries in [-1, nheights), >= 0 only on a fluid cell whose lower "
+                   "neighbour is solid");
+    return FV_EINVAL;
+  }
+  if (h->prec == FV_FP64) return run_adjoint<double, false>(h, spec, dL_dq0, on_device, info, hcell);
+  return run_adjoint<float, true>(h, spec, dL_dq0, on_device, info, hcell);
 }

@@ -46,7 +46,9 @@ class fv_diag(C.Structure):
 class fv_adjoint_spec(C.Structure):
     _fields_ = [("nsteps", C.c_int32), ("cfl", C.c_double), ("ngauges", C.c_int32),
                 ("gauges", C.POINTER(C.c_int64)), ("target", C.POINTER(C.c_double)),
-                ("checkpoint_every", C.c_int32), ("m_series", C.POINTER(C.c_double))]
+                ("checkpoint_every", C.c_int32), ("m_series", C.POINTER(C.c_double)),
+                ("nheights", C.c_int32), ("height_id", C.POINTER(C.c_int32)),
+                ("dL_dh", C.POINTER(C.c_double))]
 
 
 class fv_adjoint_info(C.Structure):
@@ -130,6 +132,10 @@ _lib.fv_host_adjoint_step.argtypes = [C.POINTER(fv_grid), C.POINTER(fv_eos), C.P
                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p,
                                       C.c_void_p, C.c_int]
 _lib.fv_host_adjoint_step.restype = C.c_int
+_lib.fv_host_height_step.argtypes = [C.POINTER(fv_grid), C.POINTER(fv_eos), C.POINTER(C.c_int32),
+                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p,
+                                     C.c_void_p, C.c_int, C.c_void_p, C.c_int]
+_lib.fv_host_height_step.restype = C.c_int
 _lib.fv_host_adj_check.argtypes = [C.c_int, _D, _D, _D, _D, _D, _D]
 _lib.fv_host_adj_check.restype = C.c_int
 
@@ -141,7 +147,7 @@ ABI_SYMBOLS = ("fv_create", "fv_set_state", "fv_step", "fv_step_timed", "fv_get_
                "fv_batch_get_diag", "fv_batch_size", "fv_batch_destroy", "fv_adjoint",
                "fv_host_adjoint_step", "fv_set_order", "fv_host_yface_o1",
                "fv_host_xface_or", "fv_set_xface", "fv_set_tiling", "fv_host_face_f32",
-               "fv_set_strip_height", "fv_tune")
+               "fv_set_strip_height", "fv_tune", "fv_host_height_step")
 
 
 def _check(st):
@@ -325,24 +331,33 @@ def fv_get_diag(h) -> fv_diag:
 
 
 def fv_adjoint(h, nsteps: int, cfl: float, gauges, target, grad_out, checkpoint_every: int = 0,
-               want_series: bool = False):
+               want_series: bool = False, height_id=None, nheights: int | None = None):
     """Gradient of the gauge loss (see fv.h) after ``nsteps`` steps with respect
     to the handle's current state, written to ``grad_out`` (4, ny, nx) float64
-    (numpy or CUDA tensor).  Returns (fv_adjoint_info, m series (nsteps,
-    ngauges) or None)."""
+    (numpy or CUDA tensor), and with ``height_id`` ((ny, nx) int32, see
+    ``cases.height_ids``) with respect to the obstacle heights.  Returns
+    (fv_adjoint_info, m series (nsteps, ngauges) or None, dL/dh (nheights) or
+    None)."""
     g = np.ascontiguousarray(gauges, dtype=np.int64)
     t = np.ascontiguousarray(target, dtype=np.float64)
     if t.size != int(nsteps) * g.size:
         raise ValueError("target must hold nsteps x ngauges values")
     series = np.zeros((int(nsteps), g.size)) if want_series else None
+    hid, dh, nh = None, None, 0
+    if height_id is not None:
+        hid = np.ascontiguousarray(height_id, dtype=np.int32)
+        nh = int(hid.max()) + 1 if nheights is None else int(nheights)
+        dh = np.zeros(max(nh, 1))
     spec = fv_adjoint_spec(int(nsteps), float(cfl), int(g.size),
                            g.ctypes.data_as(C.POINTER(C.c_int64)), t.ctypes.data_as(_D),
                            int(checkpoint_every),
-                           series.ctypes.data_as(_D) if want_series else None)
+                           series.ctypes.data_as(_D) if want_series else None, nh,
+                           hid.ctypes.data_as(C.POINTER(C.c_int32)) if nh > 0 else None,
+                           dh.ctypes.data_as(_D) if nh > 0 else None)
     info = fv_adjoint_info()
     p, dev = _ptr(grad_out)
     _check(_lib.fv_adjoint(h, C.byref(spec), C.c_void_p(p), dev, C.byref(info)))
-    return info, series
+    return info, series, (dh[:nh] if height_id is not None else None)
 
 
 def fv_destroy(h) -> None:
@@ -417,9 +432,21 @@ class Solver:
         the handle advances by ``nsteps``.  Returns (grad, info, series)."""
         if grad is None:
             grad = np.empty((4, self.case.ny, self.case.nx), dtype=np.float64)
-        info, series = fv_adjoint(self.h, nsteps, self.case.cfl if cfl is None else cfl, gauges,
-                                  target, grad, checkpoint_every, want_series)
+        info, series, _ = fv_adjoint(self.h, nsteps, self.case.cfl if cfl is None else cfl,
+                                     gauges, target, grad, checkpoint_every, want_series)
         return grad, info, series
+
+    def adjoint_heights(self, nsteps: int, gauges, target, height_id, cfl: float | None = None,
+                        checkpoint_every: int = 0, grad=None, want_series: bool = False):
+        """``adjoint`` plus the derivative with respect to the obstacle heights
+        named by ``height_id`` (``cases.height_ids``; raising the obstacles, see
+        fv.h).  Returns (grad, dL/dh (nheights), info, series)."""
+        if grad is None:
+            grad = np.empty((4, self.case.ny, self.case.nx), dtype=np.float64)
+        info, series, dh = fv_adjoint(self.h, nsteps, self.case.cfl if cfl is None else cfl,
+                                      gauges, target, grad, checkpoint_every, want_series,
+                                      height_id=height_id)
+        return grad, dh, info, series
 
     def diag(self) -> fv_diag:
         return fv_get_diag(self.h)
@@ -515,7 +542,7 @@ def gauge_loss_function():
             q0c = q0.detach().contiguous()
             solver.set_state(q0c)
             grad = torch.empty_like(q0c)
-            info, _ = fv_adjoint(solver.h, nsteps, cfl, gauges, target, grad)
+            info, _, _ = fv_adjoint(solver.h, nsteps, cfl, gauges, target, grad)
             ctx.save_for_backward(grad)
             return torch.tensor(info.loss, dtype=q0.dtype, device=q0.device)
 

@@ -256,3 +256,67 @@ def test_host_osher_romberg_x_face_matches_oracle():
         ref = O.dfluct_x_or(qm, qp, rho0=MODEL[0], k0=MODEL[1], g=MODEL[3])
         for a, b in zip(got, ref):
             assert np.allclose(a, b, rtol=1e-11, atol=1e-9 * np.abs(b).max())
+
+
+def _host_height_step(c, q, K, dt, lam, hid, prec):
+    import ctypes as C
+    grid = fv.fv_grid(c.nx, c.ny, c.x0, c.y0, c.dx, c.dy)
+    eos = fv.fv_eos(c.rho0, c.k0, c.gamma, c.g, c.eps)
+    side = (C.c_int32 * 4)(*c.sides)
+    solid = np.ascontiguousarray(c.solid, dtype=np.uint8)
+    q = np.ascontiguousarray(q)
+    K = np.ascontiguousarray(K, dtype=np.int32)
+    lam = np.ascontiguousarray(lam)
+    hid = np.ascontiguousarray(hid, dtype=np.int32)
+    nh = int(hid.max()) + 1
+    out = np.zeros(nh)
+    assert fv._lib.fv_host_height_step(C.byref(grid), C.byref(eos), side, solid.ctypes.data,
+                                       q.ctypes.data, K.ctypes.data, float(dt), lam.ctypes.data,
+                                       hid.ctypes.data, nh, out.ctypes.data, prec) == 0
+    return out
+
+
+def test_host_height_step_matches_oracle_differences():
+    """The obstacle-height part of one reverse step (fv_host_height_step, the
+    kernel's per-cell code on the host) against the one-sided difference in
+    theta of lam . Q^{n+1} from the oracle's partial cells (reading R-h), with
+    the step's dt and levels held fixed; Richardson-extrapolated, so the
+    difference's own error is O(e^2).  Two obstacles of different heights
+    side by side, so that a top cell's neighbour is another obstacle's top
+    cell.  Then the float instantiation (FP32 deviation form, lam mapped to
+    its storage form) against double."""
+    from oracle import oracle as O
+    from paper_1806_04960_gb300 import cases
+    rects = [cases.H_RECT, (0.92, 1.05, 0.0, 0.3)]
+    c0 = cases.dambreak(48, 24, lx=2.0, ly=1.0, x_col=1.2, h_col=0.6, rects=rects, k0=4.36e5,
+                        cfl=0.45)
+    c = cases.generic(c0, 7)
+    hid = cases.height_ids(c)
+    assert set(np.unique(hid)) == {-1, 0, 1}
+    g = np.array([5], dtype=np.int64)
+    q, _, _, _ = O.run_record(c, 6, g, cfl=0.45)     # a state with the water moving
+    dt, K = O.dt_levels(c, q=q, cfl=0.45)
+    rng = np.random.Generator(np.random.PCG64(41))
+    lam = rng.standard_normal(q.shape) * (c.solid == 0)
+
+    def lam_q1(theta, k):
+        cap = np.ones((c.ny, c.nx))
+        cap[hid == k] = 1.0 - theta
+        q1, _, _, _ = O.run_record(c, 1, g, q=q, cfl=0.45, dt_fix=[dt], K_fix=[K], cap=cap)
+        return float(np.sum(lam * q1))
+
+    host = _host_height_step(c, q, K, dt, lam, hid, fv.FV_FP64)
+    for k in (0, 1):
+        base = lam_q1(0.0, k)
+        e = 1e-5
+        d1 = (lam_q1(e, k) - base) / e
+        d2 = (lam_q1(2 * e, k) - base) / (2 * e)
+        ref = 2 * d1 - d2
+        assert abs(host[k] - ref) < 1e-6 * abs(ref), (k, host[k], ref)
+    # float (deviation form): lam on the storage form (m - a rho^E, mu, mv, a)
+    rhoE = c.rho0 * np.exp(-c.g * c.rho0 / c.k0 *
+                           ((np.arange(c.ny)[:, None] + 0.5) - K[None, :]) * c.dy)
+    lam_s = lam.copy()
+    lam_s[3] += rhoE * lam[0]
+    host32 = _host_height_step(c, q, K, dt, lam_s, hid, fv.FV_FP32_DEV)
+    assert np.all(np.abs(host32 - host) < 1e-3 * np.abs(host)), (host32, host)
