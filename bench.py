@@ -69,6 +69,21 @@ def dist_env():
     return rank, world, local
 
 
+def _finite(obj):
+    """obj with every non-finite float replaced by None (strict JSON)."""
+    if isinstance(obj, float):
+        return obj if math.isfinite(obj) else None
+    if isinstance(obj, dict):
+        return {k: _finite(v) for k, v in obj.items()}
+    if isinstance(obj, (list, tuple)):
+        return [_finite(v) for v in obj]
+    return obj
+
+
+def dumps_finite(obj) -> str:
+    return json.dumps(_finite(obj), allow_nan=False)
+
+
 def per_rank_max(x: float, dist=None, device: str = "cuda") -> float:
     """Largest x over the ranks of the default process group (x itself
     without one); the tensor lives on `device` (CUDA for NCCL, CPU for gloo)."""
@@ -247,7 +262,7 @@ def run_reference(args):
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
-    print(json.dumps(line), flush=True)
+    print(dumps_finite(line), flush=True)
 
 
 # --------------------------------------------------------------------------- our arm
@@ -357,7 +372,8 @@ def measure_adjoint(fv, cases_mod, prec, nsteps, stream_sync):
             "mcups_forward": cells * nsteps / (fwd_ms * 1e-3) / 1e6,
             "mcups_gradient": cells * nsteps / (adj_ms * 1e-3) / 1e6,
             "finite_fraction": float(np.isfinite(grad).mean()), "loss": info.loss,
-            "dL_dh": float(dh[0]), "height_cells": int((hid >= 0).sum())}
+            "dL_dh": float(dh[0]) if np.isfinite(dh[0]) else None,
+            "height_cells": int((hid >= 0).sum())}
 
 
 def adjoint_block(fv, cases_mod, na, stream_sync):
@@ -377,7 +393,7 @@ def run_adjoint(args):
     build.build()
     from paper_1806_04960_gb300 import cases, fv
     blk = adjoint_block(fv, cases, max(1, args.adjoint_steps), torch.cuda.synchronize)
-    print(json.dumps({"metric": "adjoint/forward cost ratio", "value": blk["f32"]["ratio"],
+    print(dumps_finite({"metric": "adjoint/forward cost ratio", "value": blk["f32"]["ratio"],
                       "unit": "ratio", "n_gpus": 1, "higher_is_better": False, "dtype": "f32",
                       "data": "synthetic", "config": {"workload": blk["workload"]},
                       "adjoint": blk}), flush=True)
@@ -458,7 +474,7 @@ def run_ours(args):
                    "sample": f"failed: {e}"}
     if rank == 0 and args.only:
         r = line_paths[args.only]
-        print(json.dumps({"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world,
+        print(dumps_finite({"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world,
                           "steps": r["steps"], "warmup": warmup, "ms_per_step": r["ms_per_step"],
                           "kernel_ms_per_step": r["kernel_ms_per_step"],
                           "dtype": args.only, "roofline": r["roofline"], "clocks": r["clocks"],
@@ -492,7 +508,7 @@ def run_ours(args):
             "adjoint": adjoint,
             "status": {"f32": f32["status"], "f64": f64["status"]},
         }
-        print(json.dumps(line), flush=True)
+        print(dumps_finite(line), flush=True)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
@@ -543,7 +559,7 @@ def run_drop(args):
     torch.cuda.synchronize()
     db = max(abs(p["b"] - q["b"]) / q["b"] for p, q in zip(hist["f32"], hist["f64"]))
     da = max(abs(p["a"] - q["a"]) / q["a"] for p, q in zip(hist["f32"], hist["f64"]))
-    print(json.dumps({"workload": "drop_2048x2048", "steps": 2000, "cfl": case.cfl,
+    print(dumps_finite({"workload": "drop_2048x2048", "steps": 2000, "cfl": case.cfl,
                       "mcups": rates, "max_rel_diff_f32_vs_f64": {"a": da, "b": db},
                       "final": {"f64": hist["f64"][-1], "f32": hist["f32"][-1]},
                       "history": hist}), flush=True)
@@ -585,7 +601,7 @@ def run_paper_setup(args):
                      "device_s": ms * 1e-3}
         s.close()
     torch.cuda.synchronize()
-    print(json.dumps({"workload": case.name, "nx": case.nx, "ny": case.ny, "cfl": case.cfl,
+    print(dumps_finite({"workload": case.name, "nx": case.nx, "ny": case.ny, "cfl": case.cfl,
                       "t_end": t_end, "paper_cell_updates_per_s": paper,
                       "paper_note": "the paper's own run of this set-up, FP64 on its GPU",
                       "ratio_f64_vs_paper": res["f64"]["mcups"] * 1e6 / paper, **res}), flush=True)

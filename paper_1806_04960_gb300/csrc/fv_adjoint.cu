@@ -824,10 +824,29 @@ struct EventPair {
   }
 };
 
+// Obstacle-height work of a reverse step, run on its own stream between the
+// step's rec kernel and the next step's (which overwrites the records).
+struct HeightWork {
+  int nh = 0;
+  const int64_t* hcell = nullptr;
+  const int32_t* hid = nullptr;
+  double* hacc = nullptr;
+  cudaStream_t st = nullptr;
+  cudaEvent_t rec_done = nullptr, done = nullptr;
+};
+
 template <typename T, bool DEV>
-void launch_reverse_step(AdjArgs<T> A, cudaStream_t st) {
+void launch_reverse_step(AdjArgs<T> A, cudaStream_t st, const HeightWork& H) {
   const dim3 b2(BX, BY), g2((A.nx + BX - 1) / BX, (A.ny + BY - 1) / BY);
+  if (H.nh > 0) cudaStreamWaitEvent(st, H.done, 0);  // the previous step's height kernel
   adj_rec_kernel<T, DEV><<<g2, b2, 0, st>>>(A);
+  if (H.nh > 0) {
+    // reads the records and the adjoint of Q^n while faces, cells and gather run
+    cudaEventRecord(H.rec_done, st);
+    cudaStreamWaitEvent(H.st, H.rec_done, 0);
+    adj_height_kernel<T, DEV><<<(H.nh + 127) / 128, 128, 0, H.st>>>(A, H.hcell, H.nh, H.hid, H.hacc);
+    cudaEventRecord(H.done, H.st);
+  }
   const long long nf = (long long)(A.nx + 1) * A.ny + (long long)A.nx * (A.ny + 1);
   adj_face_kernel<T><<<(unsigned)((nf + 255) / 256), 256, 0, st>>>(A);
   const dim3 g3((A.nx + 31) / 32, (A.ny + 3) / 4);
@@ -921,6 +940,21 @@ fv_status run_adjoint(fv_handle* h, const fv_adjoint_spec* spec, double* grad, i
   for (int k = 0; k < 2; ++k) {
     ADJ_CUDA(cudaEventCreateWithFlags(&ev_rep[k].e, cudaEventDisableTiming));
     ADJ_CUDA(cudaEventCreateWithFlags(&ev_rev[k].e, cudaEventDisableTiming));
+  }
+  OwnedStream st3;
+  OwnedEvent ev_hrec, ev_hdone;
+  HeightWork hw;
+  if (nh > 0) {
+    ADJ_CUDA(cudaStreamCreateWithFlags(&st3.s, cudaStreamNonBlocking));
+    ADJ_CUDA(cudaEventCreateWithFlags(&ev_hrec.e, cudaEventDisableTiming));
+    ADJ_CUDA(cudaEventCreateWithFlags(&ev_hdone.e, cudaEventDisableTiming));
+    hw.nh = nh;
+    hw.hcell = hcell.as<int64_t>();
+    hw.hid = hid.as<int32_t>();
+    hw.hacc = hacc.as<double>();
+    hw.st = st3.s;
+    hw.rec_done = ev_hrec.e;
+    hw.done = ev_hdone.e;
   }
   ADJ_CUDA(cudaEventCreate(&evf.a));
   ADJ_CUDA(cudaEventCreate(&evf.b));
@@ -1038,14 +1072,12 @@ fv_status run_adjoint(fv_handle* h, const fv_adjoint_spec* spec, double* grad, i
       A.Kcur = Kh + (size_t)n * nx;
       A.lam = lam;
       A.lam_out = lam2;
-      launch_reverse_step<T, DEV>(A, st);
-      if (nh > 0)  // reads the step's records and the adjoint of Q^n
-        adj_height_kernel<T, DEV><<<(nh + 127) / 128, 128, 0, st>>>(
-            A, hcell.as<int64_t>(), nh, hid.as<int32_t>(), hacc.as<double>());
+      launch_reverse_step<T, DEV>(A, st, hw);
       std::swap(lam, lam2);
     }
     ADJ_CUDA(cudaEventRecord(ev_rev[k % 2].e, st));
   }
+  if (nh > 0) ADJ_CUDA(cudaStreamWaitEvent(st, hw.done, 0));
   ADJ_CUDA(cudaGetLastError());
   ADJ_CUDA(cudaEventRecord(evr.b, st));
   ADJ_CUDA(cudaMemcpyAsync(grad, lam, sizeof(double) * 4 * N,
