@@ -272,6 +272,20 @@ fv_status fv_batch_step(fv_batch* b, int32_t n, double cfl);
  * events on the internal stream).  Synchronises. */
 fv_status fv_batch_step_timed(fv_batch* b, int32_t n, double cfl, double* total_ms);
 
+/* Autotuner of the batch's work list: times the persistent step kernel from
+ * the current states with strips of 32, 48, 64, 96, 128, 160, 192 and 256 rows,
+ * each in two orders (domain by domain; longest strips first, which balances
+ * the kernel's round-robin assignment over uneven domains), three launches
+ * each after one warm-up at the given cfl, and keeps the fastest (default
+ * before tuning: 128 rows, domain order).  Results do not depend on the
+ * choice; speed does.  States, times, levels and accumulators are left as
+ * they were (the trial launches write only the other state buffers, which the
+ * next step overwrites); cached step graphs are dropped when the list
+ * changes.  rows_out, order_out (nullable) receive the choice.  Synchronises.
+ * FV_EINVAL if a domain has no state or cfl is outside (0, 1]; FV_ECUDA on a
+ * CUDA error (the previous list is kept). */
+fv_status fv_batch_tune(fv_batch* b, double cfl, int32_t* rows_out, int32_t* order_out);
+
 /* State, diagnostics and domain count (as the single-domain calls). */
 fv_status fv_batch_get_state(fv_batch* b, int32_t dom, double* q, int on_device);
 fv_status fv_batch_get_diag(fv_batch* b, int32_t dom, fv_diag* d);

@@ -7,6 +7,7 @@
 // captured once into a CUDA graph on an internal stream and replayed.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <map>
 #include <new>
@@ -53,6 +54,8 @@ struct fv_batch {
   double* d_partial = nullptr;
   double* d_mass = nullptr;
   int cur = 0;
+  int strip_h = BATCH_STRIP_H;     // rows per strip of the work list
+  int order = 0;                   // work order (batch_work)
   std::vector<char> has_state;
   std::map<std::tuple<int, double, int>, cudaGraphExec_t> graphs;
 };
@@ -70,6 +73,24 @@ static void batch_release(fv_batch* b) {
   if (b->ev_out) cudaEventDestroy(b->ev_out);
   if (b->inner) cudaStreamDestroy(b->inner);
   delete b;
+}
+
+// Work list of the persistent batch kernel: every domain cut into strips of
+// 32 columns x H rows (the last strip of a column shorter).  order 0: domain
+// by domain; order 1: longest strips first (stable), which balances the
+// kernel's round-robin assignment when the domains are uneven.
+static std::vector<int4> batch_work(const std::vector<fv_grid>& grids, int H, int order) {
+  std::vector<int4> w;
+  for (int k = 0; k < (int)grids.size(); ++k) {
+    const int sx = (grids[k].nx + 31) / 32, sy = (grids[k].ny + H - 1) / H;
+    for (int j = 0; j < sy; ++j)
+      for (int i = 0; i < sx; ++i) w.push_back(make_int4(k, i, j, H));
+  }
+  if (order == 1) {
+    auto rows = [&](const int4& t) { return std::min(t.w, grids[t.x].ny - t.z * t.w); };
+    std::stable_sort(w.begin(), w.end(), [&](const int4& a, const int4& b) { return rows(a) > rows(b); });
+  }
+  return w;
 }
 
 static StepParams bparams(const fv_grid& g, const fv_eos& e, const int32_t side[4], double cfl) {
@@ -186,10 +207,8 @@ fv_status fv_batch_create(int32_t ndom, const fv_grid* grids, const fv_eos* eos,
       batch_release(b);
       return bfail(FV_ECUDA, std::string("fv_batch_create: ") + cudaGetErrorString(e));
     }
-    const int sx = (g.nx + 31) / 32, sy = (g.ny + BATCH_STRIP_H - 1) / BATCH_STRIP_H;
-    for (int j = 0; j < sy; ++j)
-      for (int i = 0; i < sx; ++i) tiles.push_back(make_int4(k, i, j, BATCH_STRIP_H));
   }
+  tiles = batch_work(b->grids, b->strip_h, b->order);
   std::vector<unsigned char> table(batch_table_bytes(ndom, f64));
   batch_fill_table(b->desc.data(), ndom, f64, table.data());
   b->ntiles = (int)tiles.size();
@@ -302,6 +321,89 @@ fv_status fv_batch_step(fv_batch* b, int32_t n, double cfl) { return batch_run(b
 fv_status fv_batch_step_timed(fv_batch* b, int32_t n, double cfl, double* total_ms) {
   if (!total_ms) return bfail(FV_EINVAL, "fv_batch_step_timed: null total_ms");
   return batch_run(b, n, cfl, total_ms);
+}
+
+fv_status fv_batch_tune(fv_batch* b, double cfl, int32_t* rows_out, int32_t* order_out) {
+  if (!b) return bfail(FV_EINVAL, "fv_batch_tune: null batch");
+  if (!(cfl > 0.0) || !(cfl <= 1.0)) return bfail(FV_EINVAL, "fv_batch_tune: cfl must be in (0, 1]");
+  for (int k = 0; k < b->ndom; ++k)
+    if (!b->has_state[k]) return bfail(FV_EINVAL, "fv_batch_tune: domain " + std::to_string(k) + " has no state");
+  const bool f64 = b->prec == FV_FP64;
+  cudaStream_t st = b->inner;
+  BV_CUDA(cudaEventRecord(b->ev_in, b->user));
+  BV_CUDA(cudaStreamWaitEvent(st, b->ev_in, 0));
+  // the trial launches accumulate into each domain's scalars and column sums:
+  // keep the scalars, zero the sums afterwards (they are zero between steps)
+  std::vector<DevScalars> saved(b->ndom);
+  for (int k = 0; k < b->ndom; ++k)
+    BV_CUDA(cudaMemcpyAsync(&saved[k], b->desc[k].sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
+  BV_CUDA(cudaStreamSynchronize(st));
+  const int cand_h[] = {32, 48, 64, 96, 128, 160, 192, 256};
+  size_t most = 0;
+  for (int H : cand_h) most = std::max(most, batch_work(b->grids, H, 0).size());
+  int4* d_try = nullptr;
+  BV_CUDA(cudaMalloc((void**)&d_try, most * sizeof(int4)));
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  cudaError_t e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  float best = 3.4e38f;
+  int best_h = b->strip_h, best_o = b->order;
+  launch_batch_prepare(f64, b->d_table, b->ndom, cfl, st);
+  for (int H : cand_h) {
+    for (int order = 0; order < 2 && e == cudaSuccess; ++order) {
+      const std::vector<int4> w = batch_work(b->grids, H, order);
+      e = cudaMemcpyAsync(d_try, w.data(), w.size() * sizeof(int4), cudaMemcpyHostToDevice, st);
+      if (e != cudaSuccess) break;
+      launch_batch_step(f64, b->d_table, d_try, (int)w.size(), b->cur, st);   // warm-up
+      e = cudaEventRecord(t0, st);
+      for (int r = 0; r < 3 && e == cudaSuccess; ++r)
+        launch_batch_step(f64, b->d_table, d_try, (int)w.size(), b->cur, st);
+      if (e == cudaSuccess) e = cudaEventRecord(t1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+      if (e == cudaSuccess) e = cudaGetLastError();
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+      if (e == cudaSuccess && ms < best) {
+        best = ms;
+        best_h = H;
+        best_o = order;
+      }
+    }
+  }
+  // restore: scalars as they were, column sums zero
+  for (int k = 0; k < b->ndom && e == cudaSuccess; ++k) {
+    e = cudaMemcpyAsync(b->desc[k].sc, &saved[k], sizeof(DevScalars), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemsetAsync(b->desc[k].colsum, 0, b->desc[k].p.nx * sizeof(unsigned long long), st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  cudaFree(d_try);
+  if (e != cudaSuccess) return bfail(FV_ECUDA, std::string("fv_batch_tune: ") + cudaGetErrorString(e));
+  if (best_h != b->strip_h || best_o != b->order) {
+    const std::vector<int4> w = batch_work(b->grids, best_h, best_o);
+    int4* d_new = nullptr;
+    BV_CUDA(cudaMalloc((void**)&d_new, w.size() * sizeof(int4)));
+    e = cudaMemcpy(d_new, w.data(), w.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(d_new);
+      return bfail(FV_ECUDA, std::string("fv_batch_tune: ") + cudaGetErrorString(e));
+    }
+    // the cached graphs hold the old work list
+    for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    b->graphs.clear();
+    cudaFree(b->d_tiles);
+    b->d_tiles = d_new;
+    b->ntiles = (int)w.size();
+    b->strip_h = best_h;
+    b->order = best_o;
+  }
+  if (rows_out) *rows_out = b->strip_h;
+  if (order_out) *order_out = b->order;
+  BV_CUDA(cudaEventRecord(b->ev_out, st));
+  BV_CUDA(cudaStreamWaitEvent(b->user, b->ev_out, 0));
+  return FV_OK;
 }
 
 fv_status fv_batch_get_state(fv_batch* b, int32_t dom, double* q, int on_device) {

@@ -83,3 +83,44 @@ def test_batch_rejects_bad_input(fv):
     with pytest.raises(fv.FvError):
         b.set_state(5, doms[0].q)
     b.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batch_tune_keeps_state_and_results(fv, prec):
+    """fv_batch_tune leaves every domain's state, time and levels as they were,
+    and the tuned batch steps to the same bits as an untuned one (the work
+    list changes the speed only)."""
+    doms = small_ensemble()
+    a, b = fv.Batch(doms, prec), fv.Batch(doms, prec)
+    for k, c in enumerate(doms):
+        a.set_state(k, c.q)
+        b.set_state(k, c.q)
+    a.step(3, 0.45)
+    b.step(3, 0.45)
+    before = [a.get_state(k) for k in range(len(doms))]
+    t_before = [a.diag(k).t for k in range(len(doms))]
+    rows, order = a.tune(0.45)
+    assert rows in (32, 48, 64, 96, 128, 160, 192, 256) and order in (0, 1)
+    for k in range(len(doms)):
+        assert np.array_equal(a.get_state(k), before[k])
+        assert a.diag(k).t == t_before[k] and a.diag(k).steps == 3
+    a.step(5, 0.45)
+    b.step(5, 0.45)
+    for k in range(len(doms)):
+        assert np.array_equal(a.get_state(k), b.get_state(k)), k
+        assert a.diag(k).t == b.diag(k).t
+    a.close()
+    b.close()
+
+
+def test_batch_tune_needs_states(fv):
+    doms = small_ensemble()
+    b = fv.Batch(doms, 1)
+    b.set_state(0, doms[0].q)
+    with pytest.raises(fv.FvError):
+        b.tune(0.45)
+    for k, c in enumerate(doms):
+        b.set_state(k, c.q)
+    with pytest.raises(fv.FvError):
+        b.tune(1.5)
+    b.close()
