@@ -214,15 +214,39 @@ def oracle_band(case, rows: int):
 
 
 def time_oracle(case, rows: int, steps: int, warm: int = 1):
+    """Oracle throughput on the bottom `rows` rows; also returns the band and
+    its state after the warm + timed steps."""
     from oracle import oracle
     band = oracle_band(case, rows)
     q = band.q
     if warm:
         q, _, _, _ = oracle.run(band, warm, q=q)
     t0 = time.perf_counter()
-    oracle.run(band, steps, q=q)
+    q_end, _, _, _ = oracle.run(band, steps, q=q)
     dt = time.perf_counter() - t0
-    return band.nx * band.ny * steps / dt / 1e6, dt, oracle.max_threads(), band
+    return band.nx * band.ny * steps / dt / 1e6, dt, oracle.max_threads(), band, q_end
+
+
+def errors_vs_oracle(fv, band, q_oracle, steps):
+    """Relative L1 (sum |a - b| / sum |b|) and L-infinity (max |a - b| / max |b|)
+    errors per component of both GPU paths against the oracle's state after the
+    same `steps` steps from the same input; fluid cells."""
+    import numpy as np
+    fluid = band.solid == 0
+    out = {"steps": steps, "components": ["alpha rho", "alpha rho u", "alpha rho v", "alpha"]}
+    for name, prec in (("f64", fv.FV_FP64), ("f32", fv.FV_FP32_DEV)):
+        s = fv.Solver(band, prec)
+        s.set_state(band.q)
+        s.step(steps, band.cfl)
+        q = s.get_state()
+        s.close()
+        l1, linf = [], []
+        for v in range(4):
+            a, b = q[v][fluid], q_oracle[v][fluid]
+            l1.append(float(np.sum(np.abs(a - b)) / max(np.sum(np.abs(b)), 1e-300)))
+            linf.append(float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)))
+        out[name] = {"l1": l1, "linf": linf}
+    return out
 
 
 # --------------------------------------------------------------------------- reference arm
@@ -237,7 +261,7 @@ def run_reference(args):
     budget_s = 150.0
     # size the sample so that warmup + steps fit the budget
     probe_rows = 128
-    mc, dt, cores, _ = time_oracle(case, probe_rows, 1, warm=0)
+    mc, dt, cores, _, _ = time_oracle(case, probe_rows, 1, warm=0)
     per_cell_s = dt / (case.nx * probe_rows)
     total = max(1, args.steps + args.warmup)
     rows = int(budget_s / total / per_cell_s / case.nx)
@@ -465,12 +489,17 @@ def run_ours(args):
     if not args.only and not args.no_adjoint:
         adjoint = adjoint_block(fv, cases, args.adjoint_steps, torch.cuda.synchronize)
     cpu = None
+    err = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
-            mc, dt, cores, band = time_oracle(case, case.ny, 2, warm=1)
+            mc, dt, cores, band, q_or = time_oracle(case, case.ny, 10, warm=1)
             cpu = {"value": mc, "unit": UNIT, "cores": cores, "kind": "oracle",
-                   "sample": f"the full 4096 x 2048 workload, 2 timed steps after 1 warm-up "
+                   "sample": f"the full 4096 x 2048 workload, 10 timed steps after 1 warm-up "
                              f"({dt:.1f} s wall on {cores} threads)"}
+            err = errors_vs_oracle(fv, band, q_or, 11)
+            err["note"] = ("the oracle's 11 steps of the cpu_baseline run; the tests bound 200 steps "
+                           "of the 128 x 64 dam break: FP64 relative L-inf <= 1e-10, FP32 relative "
+                           "L1 <= 1e-4 (alpha rho, alpha) and <= 1e-3 (momenta)")
         except Exception as e:  # pragma: no cover
             cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle",
                    "sample": f"failed: {e}"}
@@ -502,6 +531,7 @@ def run_ours(args):
             "gpu_launches": 2 * f32["steps"] + 1,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "error_vs_oracle": err,
             "fp64": {"value": f64["value"], "unit": UNIT, "ms_per_step": f64["ms_per_step"],
                      "kernel_ms_per_step": f64["kernel_ms_per_step"],
                      "steps": f64["steps"], "dtype": "f64", "roofline": f64["roofline"],
