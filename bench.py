@@ -485,6 +485,12 @@ def run_ours(args):
     batch = None
     if not args.only and not args.no_batch:
         batch = measure_batch(fv, cases, min(steps, 100), warmup, torch.cuda.synchronize, barrier)
+        # the same per-cell work as the single-domain step; the time includes the
+        # per-domain finalize launches of each ensemble step
+        b_tf = ops["flops"] * batch["cells"] / (batch["ms_per_step"] * 1e-3) / 1e12
+        batch["roofline"] = {"bound": "alu", "achieved": b_tf, "peak": pk["fp32_tflops"],
+                             "unit": "TFLOP/s", "frac": b_tf / pk["fp32_tflops"],
+                             "flops_per_cell": ops["flops"], "timed": "whole ensemble step"}
     adjoint = None
     if not args.only and not args.no_adjoint:
         adjoint = adjoint_block(fv, cases, args.adjoint_steps, torch.cuda.synchronize)

@@ -123,7 +123,8 @@ struct BatchDomainDesc {
 size_t batch_table_bytes(int ndom, bool f64);
 void batch_fill_table(const BatchDomainDesc* descs, int ndom, bool f64, void* host_dst);
 // The batched step stages by strips (csrc/fv_strip.cu): work[k] = (domain,
-// strip column, strip row, strip height BATCH_STRIP_H, a multiple of 8).
+// strip column, strip row, strip height, a multiple of 8).  BATCH_STRIP_H is
+// the height of a new batch's work list, until fv_batch_tune picks another.
 constexpr int BATCH_STRIP_H = 128;
 int batch_grid_size(bool f64);
 void launch_batch_step(bool f64, const void* table, const int4* work, int nwork, int parity,

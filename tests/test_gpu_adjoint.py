@@ -85,13 +85,13 @@ def gpu_grad(fv, pb, prec, every=0, target=None):
 
 @pytest.fixture(scope="module")
 def fd_dirs(problem):
-    d = cases.c5_directions(problem["case"], count=32)[:6]
+    d = cases.c5_directions(problem["case"], count=32)[:16]
     return d, np.array([oracle_dir_deriv(problem, dk, H) for dk in d])
 
 
 @pytest.fixture(scope="module")
 def fd_dirs_far(problem):
-    d = cases.c5_directions(problem["case"], count=32)[6:12]
+    d = cases.c5_directions(problem["case"], count=32)[16:32]
     return d, np.array([oracle_dir_deriv(problem, dk, H, problem["far"]) for dk in d])
 
 
