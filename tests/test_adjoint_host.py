@@ -320,3 +320,35 @@ def test_host_height_step_matches_oracle_differences():
     lam_s[3] += rhoE * lam[0]
     host32 = _host_height_step(c, q, K, dt, lam_s, hid, fv.FV_FP32_DEV)
     assert np.all(np.abs(host32 - host) < 1e-3 * np.abs(host)), (host32, host)
+
+
+def test_host_height_step_rejects_bad_maps():
+    """The height map is validated as in fv_adjoint: an id outside [-1,
+    nheights) or on a cell that is not a fluid cell resting on a solid one."""
+    from paper_1806_04960_gb300 import cases
+    c = cases.heights()
+    hid = cases.height_ids(c)
+    lam = np.ones_like(c.q)
+    K = np.full(c.nx, 14, dtype=np.int32)
+    import ctypes as C
+    grid = fv.fv_grid(c.nx, c.ny, c.x0, c.y0, c.dx, c.dy)
+    eos = fv.fv_eos(c.rho0, c.k0, c.gamma, c.g, c.eps)
+    side = (C.c_int32 * 4)(*c.sides)
+    solid = np.ascontiguousarray(c.solid, dtype=np.uint8)
+    out = np.zeros(4)
+
+    def call(h, nh):
+        h = np.ascontiguousarray(h, dtype=np.int32)
+        return fv._lib.fv_host_height_step(C.byref(grid), C.byref(eos), side, solid.ctypes.data,
+                                           c.q.ctypes.data, K.ctypes.data, 1e-4, lam.ctypes.data,
+                                           h.ctypes.data, nh, out.ctypes.data, fv.FV_FP64)
+    assert call(hid, 1) == 0
+    bad = hid.copy(); bad[10, 3] = 0          # fluid below
+    assert call(bad, 1) == 1
+    bad = hid.copy(); bad[0, 20] = 0          # a solid cell
+    assert call(bad, 1) == 1
+    bad = hid.copy(); bad[bad == 0] = 1       # id >= nheights
+    assert call(bad, 1) == 1
+    bad = hid.copy(); bad[0, 0] = -2          # id < -1
+    assert call(bad, 1) == 1
+    assert call(hid, 0) == 1
