@@ -124,3 +124,53 @@ def test_batch_tune_needs_states(fv):
     with pytest.raises(fv.FvError):
         b.tune(1.5)
     b.close()
+
+
+def test_batch_full_size_sampled_step(fv):
+    """The benchmark's ensemble at full size (256 weir domains, 77.8 M cells,
+    FP32) in the launch configuration it times (work list from
+    fv_batch_tune): 5 ensemble steps, tune, one more step; for 8 seeded
+    domains the oracle recomputes that step at sampled cells (random, next to
+    the weir, on strip column and block row edges) from the GPU's state, with
+    the domain's own dt.  Bounds as for the single-domain FP32 full-size
+    check: 1e-6 (alpha rho, alpha), 1e-4 (momenta) of each component's
+    largest value."""
+    doms = cases.weir_domains()
+    b = fv.Batch(doms, fv.FV_FP32_DEV)
+    for k, c in enumerate(doms):
+        b.set_state(k, c.q)
+    b.step(5, 0.9)
+    b.tune(0.9)
+    rng = np.random.Generator(np.random.PCG64(4961))
+    ks = rng.choice(len(doms), 8, replace=False)
+    before = {int(k): b.get_state(int(k)) for k in ks}
+    b.step(1, 0.9)
+    after = {int(k): b.get_state(int(k)) for k in ks}
+    b.close()
+    tol = [1e-6, 1e-4, 1e-4, 1e-6]
+    for k in ks:
+        k = int(k)
+        c = doms[k]
+        fl = c.solid.ravel() == 0
+        fluid = np.flatnonzero(fl)
+        picks = [rng.choice(fluid, min(400, fluid.size), replace=False)]
+        sol = c.solid.astype(bool)
+        near = np.zeros_like(sol)
+        near[:, 1:] |= sol[:, :-1]
+        near[:, :-1] |= sol[:, 1:]
+        near[1:, :] |= sol[:-1, :]
+        near &= ~sol
+        picks.append(np.flatnonzero(near.ravel()))
+        cols = np.concatenate([np.arange(31, c.nx, 32), np.arange(0, c.nx, 32)])
+        rows = np.concatenate([np.arange(7, c.ny, 8), np.arange(0, c.ny, 8)])
+        jj, ii = np.meshgrid(rows, cols, indexing="ij")
+        cand = (jj * c.nx + ii).ravel()
+        cand = cand[fl[cand]]
+        picks.append(rng.choice(cand, min(300, cand.size), replace=False))
+        cells = np.unique(np.concatenate(picks))
+        ref, _ = O.step_cells(c, before[k], cells, cfl=0.9)
+        got = after[k].reshape(4, -1)[:, cells].T
+        for v in range(4):
+            scale = np.abs(ref[:, v]).max()
+            err = np.abs(got[:, v] - ref[:, v]).max() / (scale if scale > 0 else 1.0)
+            assert err <= tol[v], (k, v, err)

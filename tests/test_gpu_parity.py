@@ -363,3 +363,37 @@ def test_drop_fp32_follows_fp64_and_exact_solution(fv):
     assert abs(b32 - b64) <= 5e-3 * b64 and abs(a32 - a64) <= 5e-3 * a64
     a_ex, b_ex = drop_semi_axes(t64, nsub=4000)
     assert abs(b64 - b_ex) <= 0.02 * b_ex and abs(a64 - a_ex) <= 0.02 * a_ex
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_drop_full_size_sampled_step(fv, prec):
+    """The elliptical drop at its full 2048 x 2048 (g = 0), in the launch
+    configuration its benchmark times (the built-in strip height): 20 steps,
+    then the oracle recomputes the 21st at sampled cells (random, on strip
+    column and block row edges, on the interface 0.01 < alpha < 0.99) from the
+    GPU's state.  Bounds as for the dam break's full-size checks."""
+    c = cases.drop(2048)
+    s = fv.Solver(c, prec)
+    s.set_state(c.q)
+    s.step(20, c.cfl)
+    q20 = s.get_state()
+    s.step(1, c.cfl)
+    q21 = s.get_state()
+    s.close()
+    rng = np.random.Generator(np.random.PCG64(2049))
+    n = c.nx * c.ny
+    picks = [rng.choice(n, 3000, replace=False)]
+    cols = np.concatenate([np.arange(31, c.nx, 32), np.arange(0, c.nx, 32)])
+    rows = np.concatenate([np.arange(7, c.ny, 8), np.arange(0, c.ny, 8)])
+    jj, ii = np.meshgrid(rows, cols, indexing="ij")
+    picks.append(rng.choice((jj * c.nx + ii).ravel(), 1000, replace=False))
+    iface = np.flatnonzero(((q20[3] > 0.01) & (q20[3] < 0.99)).ravel())
+    picks.append(rng.choice(iface, min(1000, iface.size), replace=False))
+    cells = np.unique(np.concatenate(picks))
+    ref, _ = O.step_cells(c, q20, cells)
+    got = q21.reshape(4, -1)[:, cells].T
+    tol = [1e-12] * 4 if prec == fv.FV_FP64 else [1e-6, 1e-4, 1e-4, 1e-6]
+    for v in range(4):
+        scale = np.abs(ref[:, v]).max()
+        err = np.abs(got[:, v] - ref[:, v]).max() / (scale if scale > 0 else 1.0)
+        assert err <= tol[v], (v, err)
