@@ -502,8 +502,11 @@ __host__ __device__ void cell_body(const AdjArgs<T>& A, int i, int j) {
     for (int v = 0; v < 4; ++v) A.contrib[(size_t)(4 * p + v) * N + c] = out[p][v];
 }
 
+// Float: at most 128 registers, so that four CTAs fit per SM (unbounded it
+// takes 167 and three fit, and the 1024 CTAs of a 512 x 256 grid run in 2.25
+// waves at 31 % issue activity).  Double needs about 250 and is left alone.
 template <typename T, bool DEV>
-__global__ void __launch_bounds__(128) adj_cell_kernel(AdjArgs<T> A) {
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1) adj_cell_kernel(AdjArgs<T> A) {
   const int i = blockIdx.x * 32 + (threadIdx.x & 31), j = blockIdx.y * 4 + (threadIdx.x >> 5);
   if (i < A.nx && j < A.ny) cell_body<T, DEV>(A, i, j);
 }
