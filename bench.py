@@ -320,7 +320,7 @@ def measure_batch(fv, cases_mod, steps, warmup, stream_sync, barrier):
     for k, c in enumerate(doms):
         b.set_state(k, c.q)
     b.step(warmup, 0.9)
-    rows, order = b.tune(0.9)
+    rows, order, pers = b.tune(0.9)
     b.step_timed(steps, 0.9)   # capture the graph for this step count once
     stream_sync()
     barrier()
@@ -332,8 +332,10 @@ def measure_batch(fv, cases_mod, steps, warmup, stream_sync, barrier):
     b.close()
     return {"value": cells * steps / (total_ms * 1e-3) / 1e6, "unit": UNIT,
             "ms_per_step": total_ms / steps, "steps": steps, "domains": len(doms), "cells": cells,
-            "dtype": "f32", "launch": "persistent strip kernel + per-domain finalize per step, "
-                                      "CUDA graph of all steps",
+            "dtype": "f32", "launch": ("persistent grid" if pers else "one CTA per strip") +
+                                      " of the strip kernel + per-domain finalize per step, "
+                                      "CUDA graph of all steps (form, strip height and order "
+                                      "from fv_batch_tune)",
             "strip_rows": rows, "work_order": "longest strips first" if order else "by domain",
             "bad_domains": int(bad), "t_min": min(t), "t_max": max(t)}
 

@@ -248,7 +248,8 @@ fv_status fv_adjoint(fv_handle* h, const fv_adjoint_spec* spec, double* dL_dq0, 
  * parameter sweeps).  Each domain has its own grid, equation of state,
  * boundaries, free-surface levels, dt (its own CFL condition) and time; one
  * ensemble step advances every domain by one of its own steps.  A step is one
- * persistent launch over the tiles of all domains plus one per-domain finalize
+ * launch over the strips of all domains (a persistent grid, or one CTA per
+ * strip after fv_batch_tune finds that faster) plus one per-domain finalize
  * launch; fv_batch_step captures n steps into a CUDA graph on an internal
  * stream (ordered after and before the stream given at create) and replays it.
  * The paper runs one domain at a time; the per-domain arithmetic is the same as
@@ -272,19 +273,28 @@ fv_status fv_batch_step(fv_batch* b, int32_t n, double cfl);
  * events on the internal stream).  Synchronises. */
 fv_status fv_batch_step_timed(fv_batch* b, int32_t n, double cfl, double* total_ms);
 
-/* Autotuner of the batch's work list: times the persistent step kernel from
- * the current states with strips of 32, 48, 64, 96, 128, 160, 192 and 256 rows,
- * each in two orders (domain by domain; longest strips first, which balances
- * the kernel's round-robin assignment over uneven domains), three launches
- * each after one warm-up at the given cfl, and keeps the fastest (default
- * before tuning: 128 rows, domain order).  Results do not depend on the
- * choice; speed does.  States, times, levels and accumulators are left as
- * they were (the trial launches write only the other state buffers, which the
- * next step overwrites); cached step graphs are dropped when the list
- * changes.  rows_out, order_out (nullable) receive the choice.  Synchronises.
- * FV_EINVAL if a domain has no state or cfl is outside (0, 1]; FV_ECUDA on a
- * CUDA error (the previous list is kept). */
-fv_status fv_batch_tune(fv_batch* b, double cfl, int32_t* rows_out, int32_t* order_out);
+/* Autotuner of the batch's step launch: times the step kernel from the
+ * current states with strips of 32, 48, 64, 96, 128, 160, 192 and 256 rows,
+ * each in two work orders (0: domain by domain; 1: longest strips first) and
+ * two launch forms (1: a persistent grid of the resident CTAs taking the strips
+ * round-robin; 0: one CTA per strip, handed out by the block scheduler as CTAs
+ * finish), three launches each after one warm-up at the given cfl, and keeps
+ * the fastest (default before tuning: 128 rows, domain order, persistent).
+ * Results do not depend on the choice; speed does.  States, times, levels and
+ * accumulators are left as they were (the trial launches write only the other
+ * state buffers, which the next step overwrites); cached step graphs are
+ * dropped when the choice changes.  rows_out, order_out, persistent_out
+ * (nullable) receive it.  Synchronises.  FV_EINVAL if a domain has no state or
+ * cfl is outside (0, 1]; FV_ECUDA on a CUDA error (the previous choice is
+ * kept). */
+fv_status fv_batch_tune(fv_batch* b, double cfl, int32_t* rows_out, int32_t* order_out,
+                        int32_t* persistent_out);
+
+/* Sets the batch's step launch as fv_batch_tune would: strips of `rows` rows (a
+ * positive multiple of 8), work order 0 or 1, persistent 1 or 0 (meanings as
+ * above).  Results do not depend on it.  FV_EINVAL on another value; FV_ECUDA
+ * if the new work list cannot be placed (the previous launch is kept). */
+fv_status fv_batch_set_launch(fv_batch* b, int32_t rows, int32_t order, int32_t persistent);
 
 /* State, diagnostics and domain count (as the single-domain calls). */
 fv_status fv_batch_get_state(fv_batch* b, int32_t dom, double* q, int on_device);

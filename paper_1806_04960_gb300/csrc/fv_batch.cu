@@ -1,10 +1,12 @@
 // Batched ensemble of independent domains (C ABI declared in include/fv.h).
 //
 // Every domain has its own grid, equation of state, boundaries, level
-// detector, dt and time.  One step of the ensemble is one persistent launch of
-// batch_strip_kernel over the column strips of all domains (round-robin over
-// a grid of a few CTAs per SM) followed by one per-domain finalize launch.  n steps are
-// captured once into a CUDA graph on an internal stream and replayed.
+// detector, dt and time.  One step of the ensemble is one launch of
+// batch_strip_kernel over the column strips of all domains (a persistent grid
+// of the resident CTAs striding over them, or one CTA per strip, as
+// fv_batch_tune measures fastest) followed by one per-domain finalize launch.
+// n steps are captured once into a CUDA graph on an internal stream and
+// replayed.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -56,6 +58,7 @@ struct fv_batch {
   int cur = 0;
   int strip_h = BATCH_STRIP_H;     // rows per strip of the work list
   int order = 0;                   // work order (batch_work)
+  bool persistent = true;          // launch form of the step kernel
   std::vector<char> has_state;
   std::map<std::tuple<int, double, int>, cudaGraphExec_t> graphs;
 };
@@ -91,6 +94,33 @@ static std::vector<int4> batch_work(const std::vector<fv_grid>& grids, int H, in
     std::stable_sort(w.begin(), w.end(), [&](const int4& a, const int4& b) { return rows(a) > rows(b); });
   }
   return w;
+}
+
+// Make (H, order, persistent) the batch's step launch: a new work list when H
+// or the order changes; the cached step graphs are dropped on any change.
+static fv_status batch_apply(fv_batch* b, int H, int order, bool persistent, const char* who) {
+  if (H == b->strip_h && order == b->order && persistent == b->persistent) return FV_OK;
+  if (H != b->strip_h || order != b->order) {
+    const std::vector<int4> w = batch_work(b->grids, H, order);
+    int4* d_new = nullptr;
+    cudaError_t e = cudaMalloc((void**)&d_new, w.size() * sizeof(int4));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(d_new, w.data(), w.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(d_new);
+      return bfail(FV_ECUDA, std::string(who) + ": " + cudaGetErrorString(e));
+    }
+    cudaFree(b->d_tiles);
+    b->d_tiles = d_new;
+    b->ntiles = (int)w.size();
+    b->strip_h = H;
+    b->order = order;
+  }
+  b->persistent = persistent;
+  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  b->graphs.clear();
+  return FV_OK;
 }
 
 static StepParams bparams(const fv_grid& g, const fv_eos& e, const int32_t side[4], double cfl) {
@@ -277,7 +307,7 @@ static fv_status batch_run(fv_batch* b, int32_t n, double cfl, double* total_ms)
     launch_batch_prepare(f64, b->d_table, b->ndom, cfl, b->inner);
     int par = b->cur;
     for (int32_t k = 0; k < n; ++k) {
-      launch_batch_step(f64, b->d_table, b->d_tiles, b->ntiles, par, b->inner);
+      launch_batch_step(f64, b->d_table, b->d_tiles, b->ntiles, par, b->persistent, b->inner);
       launch_batch_finalize(f64, b->d_table, b->ndom, cfl, 1, b->inner);
       par ^= 1;
     }
@@ -323,7 +353,17 @@ fv_status fv_batch_step_timed(fv_batch* b, int32_t n, double cfl, double* total_
   return batch_run(b, n, cfl, total_ms);
 }
 
-fv_status fv_batch_tune(fv_batch* b, double cfl, int32_t* rows_out, int32_t* order_out) {
+fv_status fv_batch_set_launch(fv_batch* b, int32_t rows, int32_t order, int32_t persistent) {
+  if (!b) return bfail(FV_EINVAL, "fv_batch_set_launch: null batch");
+  if (rows < 8 || rows % 8 != 0 || rows > (1 << 20) || (order != 0 && order != 1) ||
+      (persistent != 0 && persistent != 1))
+    return bfail(FV_EINVAL, "fv_batch_set_launch: rows a positive multiple of 8, order and "
+                            "persistent 0 or 1");
+  return batch_apply(b, rows, order, persistent == 1, "fv_batch_set_launch");
+}
+
+fv_status fv_batch_tune(fv_batch* b, double cfl, int32_t* rows_out, int32_t* order_out,
+                        int32_t* persistent_out) {
   if (!b) return bfail(FV_EINVAL, "fv_batch_tune: null batch");
   if (!(cfl > 0.0) || !(cfl <= 1.0)) return bfail(FV_EINVAL, "fv_batch_tune: cfl must be in (0, 1]");
   for (int k = 0; k < b->ndom; ++k)
@@ -348,25 +388,29 @@ fv_status fv_batch_tune(fv_batch* b, double cfl, int32_t* rows_out, int32_t* ord
   if (e == cudaSuccess) e = cudaEventCreate(&t1);
   float best = 3.4e38f;
   int best_h = b->strip_h, best_o = b->order;
+  bool best_p = b->persistent;
   launch_batch_prepare(f64, b->d_table, b->ndom, cfl, st);
   for (int H : cand_h) {
     for (int order = 0; order < 2 && e == cudaSuccess; ++order) {
       const std::vector<int4> w = batch_work(b->grids, H, order);
       e = cudaMemcpyAsync(d_try, w.data(), w.size() * sizeof(int4), cudaMemcpyHostToDevice, st);
-      if (e != cudaSuccess) break;
-      launch_batch_step(f64, b->d_table, d_try, (int)w.size(), b->cur, st);   // warm-up
-      e = cudaEventRecord(t0, st);
-      for (int r = 0; r < 3 && e == cudaSuccess; ++r)
-        launch_batch_step(f64, b->d_table, d_try, (int)w.size(), b->cur, st);
-      if (e == cudaSuccess) e = cudaEventRecord(t1, st);
-      if (e == cudaSuccess) e = cudaEventSynchronize(t1);
-      if (e == cudaSuccess) e = cudaGetLastError();
-      float ms = 0.f;
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
-      if (e == cudaSuccess && ms < best) {
-        best = ms;
-        best_h = H;
-        best_o = order;
+      for (int form = 0; form < 2 && e == cudaSuccess; ++form) {
+        const bool pers = form == 0;
+        launch_batch_step(f64, b->d_table, d_try, (int)w.size(), b->cur, pers, st);   // warm-up
+        e = cudaEventRecord(t0, st);
+        for (int r = 0; r < 3 && e == cudaSuccess; ++r)
+          launch_batch_step(f64, b->d_table, d_try, (int)w.size(), b->cur, pers, st);
+        if (e == cudaSuccess) e = cudaEventRecord(t1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+        if (e == cudaSuccess && ms < best) {
+          best = ms;
+          best_h = H;
+          best_o = order;
+          best_p = pers;
+        }
       }
     }
   }
@@ -381,26 +425,11 @@ fv_status fv_batch_tune(fv_batch* b, double cfl, int32_t* rows_out, int32_t* ord
   if (t1) cudaEventDestroy(t1);
   cudaFree(d_try);
   if (e != cudaSuccess) return bfail(FV_ECUDA, std::string("fv_batch_tune: ") + cudaGetErrorString(e));
-  if (best_h != b->strip_h || best_o != b->order) {
-    const std::vector<int4> w = batch_work(b->grids, best_h, best_o);
-    int4* d_new = nullptr;
-    BV_CUDA(cudaMalloc((void**)&d_new, w.size() * sizeof(int4)));
-    e = cudaMemcpy(d_new, w.data(), w.size() * sizeof(int4), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) {
-      cudaFree(d_new);
-      return bfail(FV_ECUDA, std::string("fv_batch_tune: ") + cudaGetErrorString(e));
-    }
-    // the cached graphs hold the old work list
-    for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
-    b->graphs.clear();
-    cudaFree(b->d_tiles);
-    b->d_tiles = d_new;
-    b->ntiles = (int)w.size();
-    b->strip_h = best_h;
-    b->order = best_o;
-  }
+  const fv_status st_apply = batch_apply(b, best_h, best_o, best_p, "fv_batch_tune");
+  if (st_apply != FV_OK) return st_apply;
   if (rows_out) *rows_out = b->strip_h;
   if (order_out) *order_out = b->order;
+  if (persistent_out) *persistent_out = b->persistent ? 1 : 0;
   BV_CUDA(cudaEventRecord(b->ev_out, st));
   BV_CUDA(cudaStreamWaitEvent(b->user, b->ev_out, 0));
   return FV_OK;

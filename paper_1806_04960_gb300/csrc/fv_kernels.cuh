@@ -127,8 +127,10 @@ void batch_fill_table(const BatchDomainDesc* descs, int ndom, bool f64, void* ho
 // the height of a new batch's work list, until fv_batch_tune picks another.
 constexpr int BATCH_STRIP_H = 128;
 int batch_grid_size(bool f64);
+// persistent: a grid of the resident CTAs striding over the work list;
+// otherwise one CTA per strip.
 void launch_batch_step(bool f64, const void* table, const int4* work, int nwork, int parity,
-                       cudaStream_t st);
+                       bool persistent, cudaStream_t st);
 void launch_batch_finalize(bool f64, const void* table, int ndom, double cfl, int count_step,
                            cudaStream_t st);
 void launch_batch_prepare(bool f64, const void* table, int ndom, double cfl, cudaStream_t st);

@@ -277,9 +277,11 @@ __global__ void __launch_bounds__(strip_threads<T>(), (sizeof(T) == 8 ? 1 : 3))
                           blockIdx.y, H, S);
 }
 
-// Batched step: every strip (domain, sx, sy, H) of an ensemble, distributed
-// round-robin over a persistent grid; each domain uses its own parameters,
-// dt, levels and accumulators.  parity selects the state buffer read.
+// Batched step: every strip (domain, sx, sy, H) of an ensemble, either one
+// CTA per strip (the block scheduler hands strips out as CTAs finish) or
+// round-robin over a persistent grid of the resident CTAs; each domain uses
+// its own parameters, dt, levels and accumulators.  parity selects the state
+// buffer read.
 template <typename T, bool DEV>
 __global__ void __launch_bounds__(strip_threads<T>(), (sizeof(T) == 8 ? 1 : 3))
     batch_strip_kernel(const BatchDomain<T>* __restrict__ doms, const int4* __restrict__ work,
@@ -341,17 +343,17 @@ int batch_grid_size(bool f64) {
 }
 
 void launch_batch_step(bool f64, const void* table, const int4* work, int nwork, int parity,
-                       cudaStream_t st) {
+                       bool persistent, cudaStream_t st) {
   if (f64) {
-    const int grid = batch_grid_t<double, false>();
-    batch_strip_kernel<double, false>
-        <<<grid < nwork ? grid : nwork, strip_threads<double>(), sizeof(StripSmem<double>), st>>>(
-            static_cast<const BatchDomain<double>*>(table), work, nwork, parity);
+    const int res = batch_grid_t<double, false>();
+    const int grid = persistent && res < nwork ? res : nwork;
+    batch_strip_kernel<double, false><<<grid, strip_threads<double>(), sizeof(StripSmem<double>), st>>>(
+        static_cast<const BatchDomain<double>*>(table), work, nwork, parity);
   } else {
-    const int grid = batch_grid_t<float, true>();
-    batch_strip_kernel<float, true>
-        <<<grid < nwork ? grid : nwork, strip_threads<float>(), sizeof(StripSmem<float>), st>>>(
-            static_cast<const BatchDomain<float>*>(table), work, nwork, parity);
+    const int res = batch_grid_t<float, true>();
+    const int grid = persistent && res < nwork ? res : nwork;
+    batch_strip_kernel<float, true><<<grid, strip_threads<float>(), sizeof(StripSmem<float>), st>>>(
+        static_cast<const BatchDomain<float>*>(table), work, nwork, parity);
   }
 }
 

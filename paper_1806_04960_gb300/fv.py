@@ -99,7 +99,9 @@ _lib.fv_batch_create.argtypes = [C.c_int32, C.POINTER(fv_grid), C.POINTER(fv_eos
 _lib.fv_batch_set_state.argtypes = [_B, C.c_int32, C.c_void_p, C.c_int]
 _lib.fv_batch_step.argtypes = [_B, C.c_int32, C.c_double]
 _lib.fv_batch_step_timed.argtypes = [_B, C.c_int32, C.c_double, _D]
-_lib.fv_batch_tune.argtypes = [_B, C.c_double, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+_lib.fv_batch_tune.argtypes = [_B, C.c_double, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                               C.POINTER(C.c_int32)]
+_lib.fv_batch_set_launch.argtypes = [_B, C.c_int32, C.c_int32, C.c_int32]
 _lib.fv_batch_get_state.argtypes = [_B, C.c_int32, C.c_void_p, C.c_int]
 _lib.fv_batch_get_diag.argtypes = [_B, C.c_int32, C.POINTER(fv_diag)]
 _lib.fv_batch_size.argtypes = [_B]
@@ -107,7 +109,7 @@ _lib.fv_batch_size.restype = C.c_int32
 _lib.fv_batch_destroy.argtypes = [_B]
 _lib.fv_batch_destroy.restype = None
 for _f in ("fv_batch_create", "fv_batch_set_state", "fv_batch_step", "fv_batch_step_timed",
-           "fv_batch_get_state", "fv_batch_get_diag", "fv_batch_tune"):
+           "fv_batch_get_state", "fv_batch_get_diag", "fv_batch_tune", "fv_batch_set_launch"):
     getattr(_lib, _f).restype = C.c_int
 _lib.fv_host_cell_ops.restype = C.c_int
 _lib.fv_host_yface.restype = C.c_int
@@ -148,7 +150,8 @@ ABI_SYMBOLS = ("fv_create", "fv_set_state", "fv_step", "fv_step_timed", "fv_get_
                "fv_batch_get_diag", "fv_batch_size", "fv_batch_destroy", "fv_adjoint",
                "fv_host_adjoint_step", "fv_set_order", "fv_host_yface_o1",
                "fv_host_xface_or", "fv_set_xface", "fv_set_tiling", "fv_host_face_f32",
-               "fv_set_strip_height", "fv_tune", "fv_host_height_step", "fv_batch_tune")
+               "fv_set_strip_height", "fv_tune", "fv_host_height_step", "fv_batch_tune",
+               "fv_batch_set_launch")
 
 
 def _check(st):
@@ -499,11 +502,17 @@ class Batch:
         _check(_lib.fv_batch_step_timed(self.b, int(n), float(cfl), C.byref(t)))
         return t.value
 
+    def set_launch(self, rows: int, order: int, persistent: int) -> None:
+        """Fix the strip height, work order and launch form (fv_batch_set_launch)."""
+        _check(_lib.fv_batch_set_launch(self.b, int(rows), int(order), int(persistent)))
+
     def tune(self, cfl: float) -> tuple:
-        """Pick the fastest work list (fv_batch_tune); returns (rows, order)."""
-        rows, order = C.c_int32(0), C.c_int32(0)
-        _check(_lib.fv_batch_tune(self.b, float(cfl), C.byref(rows), C.byref(order)))
-        return rows.value, order.value
+        """Pick the fastest strip height, work order and launch form
+        (fv_batch_tune); returns (rows, order, persistent)."""
+        rows, order, pers = C.c_int32(0), C.c_int32(0), C.c_int32(0)
+        _check(_lib.fv_batch_tune(self.b, float(cfl), C.byref(rows), C.byref(order),
+                                  C.byref(pers)))
+        return rows.value, order.value, pers.value
 
     def get_state(self, dom: int, out=None):
         c = self.cases[dom]

@@ -99,8 +99,8 @@ def test_batch_tune_keeps_state_and_results(fv, prec):
     b.step(3, 0.45)
     before = [a.get_state(k) for k in range(len(doms))]
     t_before = [a.diag(k).t for k in range(len(doms))]
-    rows, order = a.tune(0.45)
-    assert rows in (32, 48, 64, 96, 128, 160, 192, 256) and order in (0, 1)
+    rows, order, pers = a.tune(0.45)
+    assert rows in (32, 48, 64, 96, 128, 160, 192, 256) and order in (0, 1) and pers in (0, 1)
     for k in range(len(doms)):
         assert np.array_equal(a.get_state(k), before[k])
         assert a.diag(k).t == t_before[k] and a.diag(k).steps == 3
@@ -174,3 +174,29 @@ def test_batch_full_size_sampled_step(fv):
             scale = np.abs(ref[:, v]).max()
             err = np.abs(got[:, v] - ref[:, v]).max() / (scale if scale > 0 else 1.0)
             assert err <= tol[v], (k, v, err)
+
+
+def test_batch_launch_forms_give_the_same_bits(fv):
+    """Every strip height, work order and launch form (fv_batch_set_launch)
+    steps the ensemble to the same bits: the per-cell arithmetic does not
+    depend on which CTA takes a strip."""
+    doms = small_ensemble()
+    ref = None
+    for rows, order, pers in ((128, 0, 1), (128, 0, 0), (32, 1, 0), (256, 1, 1), (48, 0, 0)):
+        b = fv.Batch(doms, 1)
+        b.set_launch(rows, order, pers)
+        for k, c in enumerate(doms):
+            b.set_state(k, c.q)
+        b.step(6, 0.45)
+        got = [b.get_state(k) for k in range(len(doms))]
+        b.close()
+        if ref is None:
+            ref = got
+        else:
+            for k in range(len(doms)):
+                assert np.array_equal(got[k], ref[k]), (rows, order, pers, k)
+    b = fv.Batch(doms, 1)
+    for bad in ((0, 0, 1), (12, 0, 1), (32, 2, 1), (32, 0, 2)):
+        with pytest.raises(fv.FvError):
+            b.set_launch(*bad)
+    b.close()
