@@ -78,10 +78,11 @@ static void batch_release(fv_batch* b) {
   delete b;
 }
 
-// Work list of the persistent batch kernel: every domain cut into strips of
-// 32 columns x H rows (the last strip of a column shorter).  order 0: domain
-// by domain; order 1: longest strips first (stable), which balances the
-// kernel's round-robin assignment when the domains are uneven.
+// Work list of the batch kernel: every domain cut into strips of 32 columns x
+// H rows (the last strip of a column shorter).  order 0: domain by domain;
+// order 1: longest strips first (stable), which balances uneven domains in
+// both launch forms (round-robin over a persistent grid; CTAs handed out by
+// the block scheduler).
 static std::vector<int4> batch_work(const std::vector<fv_grid>& grids, int H, int order) {
   std::vector<int4> w;
   for (int k = 0; k < (int)grids.size(); ++k) {
