@@ -59,7 +59,9 @@
 //           average of u(Phi(s_k)) in x; in y, v(Phi(s_k)) on each Romberg
 //           sub-interval and the Romberg combination on the whole face (the
 //           printed sqrt(rho)-weighted Roe average loses the upwinding of
-//           alpha at the liquid-gas interface);
+//           alpha at the liquid-gas interface; it is kept behind the `roe`
+//           switch of orc_run_record, off by default, so that the tests can
+//           show the 128 x 64 dam break failing with it);
 //   R-pos   a cell whose reconstructed states at t^{n+1/2} (four face midpoints
 //           and barycentre) are not admissible (alpha <= 0 or alpha rho <= 0)
 //           is advanced at first order, like the alpha <= 10 eps switch;
@@ -112,6 +114,10 @@ namespace {
 // ---------------------------------------------------------------------------
 struct Model {
   double rho0, k0, gamma, g, eps;
+  // 1: the velocity averages of b4x and b4y are the printed sqrt(rho)-weighted
+  // Roe averages of the two states (Eqs. (b_4^x), (b_4^y)) instead of reading
+  // R-vel; off by default, kept so that the tests can show why R-vel is taken
+  int roe = 0;
 };
 
 // Tait equation of state, Eq. (TaitLaw), with gamma = 1.
@@ -134,6 +140,16 @@ Prim prim(const Model& M, const double q[4]) {
   w.c2 = sound2(M, w.rho);
   w.c = std::sqrt(w.c2);
   return w;
+}
+
+// Printed Roe average of one velocity component, Eqs. (b_4^x) and (b_4^y):
+// (w_a sqrt(rho_a) + w_b sqrt(rho_b)) / (sqrt(rho_a) + sqrt(rho_b)), rho = m / alpha;
+// comp 0 averages u, 1 averages v.
+double roe_average(const Model& M, const double qa[4], const double qb[4], int comp) {
+  const Prim a = prim(M, qa), b = prim(M, qb);
+  const double ra = std::sqrt(qa[0] / qa[3]), rb = std::sqrt(qb[0] / qb[3]);
+  const double wa = comp == 0 ? a.u : a.v, wb = comp == 0 ? b.u : b.v;
+  return (wa * ra + wb * rb) / (ra + rb);
 }
 
 // Physical fluxes of Eq. (BNsimplified_genForm); the 5th (potential y) entry is 0.
@@ -282,6 +298,7 @@ void dfluct_x(const Model& M, const double qm[4], const double qp[4], double Dm[
     for (int v = 0; v < 5; ++v) V[v] += w_gl[k] * t[v];
     ubar += w_gl[k] * prim(M, phi).u;
   }
+  if (M.roe) ubar = roe_average(M, qm, qp, 0);
   double B[5] = {0.0, 0.0, 0.0, ubar * dq[3], 0.0};
   for (int v = 0; v < 4; ++v) {
     Dm[v] = 0.5 * (fp[v] - fm[v] + B[v] - V[v]);
@@ -386,6 +403,7 @@ void dfluct_y(const Model& M, const double fm[4], double aEm, const double fp[4]
   flux_g(M, n1.q, g1);
   double vbar01 = 0.0;   // Romberg quadrature of the path velocity over [0, 1]
   for (int k = 0; k < 3; ++k) vbar01 += wk[k] * prim(M, ynode(fm, aEm, fp, aEp, rhoE, sk[k]).q).v;
+  if (M.roe) vbar01 = roe_average(M, n0.q, n1.q, 1);
   bterm_y(M, n0, n1, rhoE, vbar01, B01);
   double V[5] = {0, 0, 0, 0, 0};
   for (int k = 0; k < 3; ++k) {
@@ -395,7 +413,7 @@ void dfluct_y(const Model& M, const double fm[4], double aEm, const double fp[4]
     double ga[5], gb[5], Bab[5], Rk[5], t[5];
     flux_g(M, na.q, ga);
     flux_g(M, nb.q, gb);
-    bterm_y(M, na, nb, rhoE, prim(M, nc.q).v, Bab);
+    bterm_y(M, na, nb, rhoE, M.roe ? roe_average(M, na.q, nb.q, 1) : prim(M, nc.q).v, Bab);
     for (int v = 0; v < 5; ++v) Rk[v] = gb[v] - ga[v] + Bab[v];
     sign_A2_apply(M, nc.q, Rk, t);
     for (int v = 0; v < 5; ++v) V[v] += wk[k] * t[v] / (2.0 * ek[k]);
@@ -1133,7 +1151,9 @@ int orc_run(const int32_t* gi, const double* gd, const double* eos, const int32_
 // n time steps of the scheme (bits 0-3: order 2 = Eq. (Scheme) with the
 // reconstruction of Section 3.4, order 1 = the first-order scheme of Sections
 // 3.2-3.3, reading R-o1; bit 4: x faces by the conservative Osher-Romberg
-// viscosity of Eq. (OR_cons) instead of Gauss-Legendre) recording, for each step, its levels (K_hist, nsteps*nx,
+// viscosity of Eq. (OR_cons) instead of Gauss-Legendre; bit 5, second order
+// with Gauss-Legendre x faces only: the printed Roe averages in b4x and b4y
+// instead of reading R-vel) recording, for each step, its levels (K_hist, nsteps*nx,
 // nullable), its dt (dt_hist, nullable) and alpha rho at the gauge cells after
 // it (m_hist, nsteps*ngauges, nullable).  With dt_fix and K_fix (both given),
 // step s uses dt_fix[s] and the levels K_fix[s*nx ..] instead of those of its
@@ -1149,7 +1169,9 @@ int orc_run_record(const int32_t* gi, const double* gd, const double* eos, const
   if (!valid(C) || nsteps < 0 || !(cfl > 0.0) || (!dt_fix) != (!K_fix)) return 1;
   const int order = scheme & 15;
   C.xsolver = (scheme >> 4) & 1;
-  if ((order != 1 && order != 2) || (scheme >> 5) != 0) return 1;
+  C.M.roe = (scheme >> 5) & 1;
+  if ((order != 1 && order != 2) || (scheme >> 6) != 0) return 1;
+  if (C.M.roe && (order != 2 || C.xsolver != 0)) return 1;
   const size_t n1 = (size_t)C.G.nx * C.G.ny, n4 = 4 * n1;
   if (cap) {
     if (order != 2) return 1;

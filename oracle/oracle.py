@@ -118,7 +118,7 @@ def run(case, nsteps: int, q=None, cfl: float | None = None):
 
 
 def run_record(case, nsteps: int, gauges, q=None, cfl: float | None = None, dt_fix=None,
-               K_fix=None, order: int = 2, xsolver: int = 0, cap=None):
+               K_fix=None, order: int = 2, xsolver: int = 0, cap=None, roe: bool = False):
     """Advance ``nsteps`` steps of the scheme of ``order`` (2: Eq. (Scheme);
     1: the first-order scheme of Sections 3.2-3.3) with x faces by
     ``xsolver`` (0: Gauss-Legendre Osher; 1: conservative Osher-Romberg,
@@ -127,6 +127,8 @@ def run_record(case, nsteps: int, gauges, q=None, cfl: float | None = None, dt_f
     ``dt_fix`` (nsteps) and ``K_fix`` (nsteps, nx) the steps use those instead
     of their own.  ``cap`` (ny, nx), second order only: the fluid capacities
     of reading R-h (a partial cell on top of an obstacle; 1 = a whole cell).
+    ``roe`` (second order, Gauss-Legendre x faces): the printed sqrt(rho)-
+    weighted Roe averages of Eqs. (b_4^x), (b_4^y) in place of reading R-vel.
     Returns (q_out, dt (nsteps), K (nsteps, nx), m (nsteps, ngauges))."""
     L = lib()
     gi, gd, eos, sides, solid = _case_args(case)
@@ -148,7 +150,7 @@ def run_record(case, nsteps: int, gauges, q=None, cfl: float | None = None, dt_f
                           _p(qin), _p(qout), int(nsteps), float(case.cfl if cfl is None else cfl),
                           None if dfix is None else _p(dfix),
                           None if kfix is None else _p(kfix, _I32), _p(dts), _p(Ks, _I32),
-                          _p(g, _I64), int(g.size), _p(ms), int(order) | (int(xsolver) << 4),
+                          _p(g, _I64), int(g.size), _p(ms), int(order) | (int(xsolver) << 4) | (int(bool(roe)) << 5),
                           None if cp is None else _p(cp))
     if rc == 1:
         raise OracleError("invalid input")

@@ -146,6 +146,48 @@ def test_linear_case_y_equals_abs_matrix(scale):
         assert np.allclose(Dp + Dm, (A2 @ dq)[:4], rtol=1e-9, atol=1e-7)
 
 
+def _abs_A1_numpy(q):
+    A1, _ = O.jacobians(q)   # pinned to the flux derivatives above
+    return np_abs_sign(A1)[0]
+
+
+def _viscosity_x_reference(qm, qp, nodes=48):
+    """Integral over s in [0, 1] of |A1(qm + s dq)| dq by a 48-node
+    Gauss-Legendre rule with |A1| from numpy's eigendecomposition."""
+    x, w = np.polynomial.legendre.leggauss(nodes)
+    dq = np.append(qp - qm, 0.0)
+    V = np.zeros(5)
+    for sk, wk in zip(0.5 * (x + 1.0), 0.5 * w):
+        V += wk * (_abs_A1_numpy(qm + sk * (qp - qm)) @ dq)
+    return V[:4]
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_x_viscosity_is_three_point_gauss_legendre_on_nonlinear_paths(seed):
+    """Eq. (OsherMatrixFormal_approx): the x-face viscosity is the 3-point
+    Gauss-Legendre rule for the integral of |A1(Psi(s))| dq along the segment.
+    On a segment whose velocity varies nonlinearly (u, u +- c keep their signs,
+    so the integrand is smooth) the rule is exact to degree 5: its error
+    relative to |V| falls like h^6 as the jump shrinks by h; the error of a
+    3-node rule with other weights summing to 1 (e.g. equal weights) falls like
+    h^2 and is 1e-4 at h = 1/8."""
+    rng = np.random.Generator(np.random.PCG64(4242 + seed))
+    m1, m2 = rng.uniform(400.0, 600.0), rng.uniform(800.0, 1000.0)
+    u1, u2 = rng.uniform(2.0, 5.0), rng.uniform(6.0, 9.0)
+    v1, v2 = rng.uniform(-3.0, 3.0, 2)
+    a1, a2 = rng.uniform(0.4, 0.6), rng.uniform(0.8, 1.0)
+    qm = np.array([m1, m1 * u1, m1 * v1, a1])
+    qe = np.array([m2, m2 * u2, m2 * v2, a2])
+    errs = []
+    for h in (0.125, 0.0625):
+        qp = qm + h * (qe - qm)
+        Dm, Dp = O.dfluct_x(qm, qp)
+        ref = _viscosity_x_reference(qm, qp)
+        errs.append(np.abs((Dp - Dm) - ref).max() / np.abs(ref).max())
+    assert errs[1] <= 1e-9, errs
+    assert errs[0] / errs[1] >= 32.0, errs
+
+
 def test_alpha_transport_is_upwind():
     """Path-consistent velocity: with u > 0 at every quadrature node the upwind
     cell receives no alpha fluctuation (D-_4 = 0), and vice versa."""
@@ -216,19 +258,42 @@ def test_detector_rounds_half_away_from_zero():
     assert K[0] == 4 and K[1] == 2 and K[2] == 0
 
 
+def test_detector_normalises_the_gas_fraction_on_2048_rows():
+    """Eq. (Free_surf_detector) with reading R-det on the benchmark's 4096 x
+    2048 grid and its 8 obstacles: a lake with its surface at y = 1.0 = 1024 dy
+    has K = 1024 in every column (solid cells count 1, gas cells 0).  Summing
+    alpha itself would add 1024 x 1e-3 of gas above the surface and give 1025.
+    A column with a partly filled cell: 1000 liquid rows, alpha = 0.6 in row
+    1000, gas above: K = round(1000 + (0.6 - eps)/(1 - eps)) = 1001 (the
+    un-normalised sum, 1001.647, gives 1002)."""
+    c = cases.dambreak(4096, 2048, rects=cases.c2_rects(), lake_level=1.0)
+    _, K = O.dt_levels(c)
+    assert np.all(K == 1024)
+    c2 = cases.dambreak(4, 2048, lx=4.0 / 1024, x_col=10.0, h_col=1.0)
+    q = c2.q.copy()
+    q[3][:, :] = c2.eps
+    q[3][:1000, 0] = 1.0
+    q[3][1000, 0] = 0.6
+    q[0] = q[3] * RHO0
+    _, K2 = O.dt_levels(c2, q=q)
+    assert K2[0] == 1001 and np.all(K2[1:] == 0)
+
+
 # ---------------------------------------------------------------- well balance
 
 def test_table1_lake_at_rest_within_paper_errors():
-    """Section 5.1: water at rest with and without the obstacle keeps the exact
-    profile; errors after t = 0.1 stay below the paper's t = 1 maxima."""
+    """Section 5.1, Table 1: water at rest with and without the obstacle, run
+    to t = 1 (about 3700 steps at CFL 0.9), keeps the exact profile within the
+    paper's maximum errors at t = 1."""
     gold = {(r[0], float(r[1])): [float(x) for x in r[2:]] for r in read_golden("table1_lake_at_rest.txt")}
     for obstacle in (True, False):
         c = cases.lake_box(100, obstacle=obstacle)
         fl = c.solid == 0
         t = 0.0
         q = c.q
-        while t < 0.1:
-            q, tt, _, _ = O.run(c, 50, q=q)
+        while t < 1.0:
+            dt, _ = O.dt_levels(c, q=q)
+            q, tt, _, _ = O.run(c, max(1, min(500, int((1.0 - t) / dt))), q=q)
             t += tt
         rho = q[0][fl] / q[3][fl]
         rho_ex = c.q[0][fl] / c.q[3][fl]
@@ -237,10 +302,10 @@ def test_table1_lake_at_rest_within_paper_errors():
         E_v = np.abs(q[2][fl] / q[0][fl]).max()
         E_p = np.abs(c.k0 * (rho - rho_ex) / RHO0).max()
         ref = gold[("obstacle" if obstacle else "flat", 1.0)]
-        assert E_rho <= max(ref[0], 1e-12), E_rho
-        assert E_u <= max(ref[1], 1e-13), E_u
-        assert E_v <= max(ref[2], 1e-13), E_v
-        assert E_p <= max(ref[3], 1e-9), E_p
+        assert E_rho <= ref[0], E_rho
+        assert E_u <= max(ref[1], 1e-15), E_u
+        assert E_v <= ref[2], E_v
+        assert E_p <= ref[3], E_p
 
 
 def test_lake_with_air_and_obstacle_stays_at_rest():
@@ -347,7 +412,8 @@ def test_alpha_contact_translates_exactly_in_velocity():
         t_end = 0.2
         q = run_to(c, t_end)
         u = q[1] / q[0]
-        assert np.abs(u - 1.0).max() < 1e-10
+        # roundoff of ~1000 steps (measured 1.1e-12 at 200 cells)
+        assert np.abs(u - 1.0).max() < 5e-12
         assert np.abs(q[0] / q[3] - RHO0).max() < 1e-9
         X = np.meshgrid(c.xc(), c.yc())[0]
         a_ex = 0.5 + 0.4 * np.exp(-((X - 0.3 - t_end) / 0.08) ** 2)
@@ -590,3 +656,24 @@ def test_osher_romberg_x_lake_mass_and_riemann():
         rho_ex, _ = isothermal_riemann(1010.0, 0.5, 1000.0, -0.5, c_s, xi)
         errs.append(np.abs(qq[0][1] / qq[3][1] - rho_ex).mean())
     assert errs[2] < errs[1] < errs[0] and errs[2] < 0.3
+
+
+# ---------------------------------------------------------------- reading R-vel
+
+def test_printed_roe_average_breaks_the_dam_break():
+    """Eqs. (b_4^x), (b_4^y) print u_bar, v_bar as sqrt(rho)-weighted Roe
+    averages of the two face states.  With them (the oracle's `roe` switch) the
+    nonconservative alpha transport is not upwind at the liquid-gas interface:
+    alpha rises above 1 by 2-9 % within two to five steps and the 128 x 64 dam
+    break becomes non-admissible by step 6 at CFL 0.9, 0.45 and 0.2.  Reading
+    R-vel (the path average of the velocity with the viscosity's quadrature)
+    advances the same 10 steps with alpha <= 1 + 2^-20."""
+    c = cases.c1()
+    fl = c.solid == 0
+    for cfl in (0.9, 0.45, 0.2):
+        q, _, _, _ = O.run_record(c, 10, [0], cfl=cfl)
+        assert q[3][fl].max() <= 1.0 + 2.0 ** -20 and q[0][fl].min() > 0.0
+        q2, _, _, _ = O.run_record(c, 2, [0], cfl=cfl, roe=True)
+        assert q2[3][fl].max() > 1.01
+        with pytest.raises(O.OracleError):
+            O.run_record(c, 6, [0], cfl=cfl, roe=True)
