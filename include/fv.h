@@ -323,12 +323,16 @@ void fv_batch_destroy(fv_batch* b);
  *   q_in, q_out: device pointers to the 4-plane double state (layout above);
  *     they must not alias.  Solid cells of q_out are written as 0.
  *   cfl in (0, 1]; cuda_stream: the stream for all work (NULL = default).
- *   dt_out: nullable host pointer; if given, the stream is synchronised and
- *     *dt_out receives the step's dt (FV_ENONFINITE if q_out is not
- *     admissible); otherwise the call is asynchronous.
+ *   dt_out: nullable host pointer; if given, the stream is synchronised,
+ *     *dt_out receives the step's dt and the states are checked: FV_EINVAL if
+ *     q_in has a fluid cell with alpha <= 0, alpha*rho <= 0 or a non-finite
+ *     value (as fv_set_state), else FV_ENONFINITE if q_out is not admissible.
+ *     Without dt_out the call is asynchronous and neither state is checked.
  * Calls no allocating routine.  The first call on a device looks up the
  * array's device address with that device current; make that first call
- * before any stream capture.  Every call reuses the same array, which keeps
+ * before any stream capture.  The equilibrium table in the array is copied
+ * from a host buffer when ny, dy, rho0 or the gravity constant differ from the
+ * previous call's on that device.  Every call reuses the same array, which keeps
  * the previous call's contents (the accumulators are cleared at the start of
  * each call), so calls whose work overlaps on a GPU (other streams, other host
  * threads) race and must be serialised by the caller. */

@@ -29,6 +29,9 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "fv_consts.cuh"
 #include "fv_kernels.cuh"
@@ -269,7 +272,7 @@ __global__ void prepare_kernel(double cfl, DevScalars* sc) {
 
 __global__ void prologue_kernel(StepParams p, const double* __restrict__ q,
                                 const uint8_t* __restrict__ solid, unsigned long long* colsum,
-                                DevScalars* sc) {
+                                DevScalars* sc, int status_bits) {
   const size_t N = (size_t)p.nx * p.ny;
   double my_rate = 0.0;
   bool bad = false;
@@ -290,7 +293,7 @@ __global__ void prologue_kernel(StepParams p, const double* __restrict__ q,
     const unsigned long long qw = (unsigned long long)__double2ll_rn(w * 4294967296.0);
     if (qw) atomicAdd(&colsum[i], qw);
   }
-  if (bad) atomicOr(&sc->status, 1);
+  if (bad) atomicOr(&sc->status, status_bits);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) my_rate = fmax(my_rate, __shfl_xor_sync(0xffffffffu, my_rate, o));
   if ((threadIdx.x & 31) == 0 && my_rate > 0.0)
@@ -388,12 +391,7 @@ void launch_step_xt(const StepParams& p, const T* in, T* out, const uint8_t* sol
                     const int32_t* Kref, const int32_t* Kcur, unsigned long long* colsum,
                     DevScalars* sc, const double* rhoE_d, const T* rt, cudaStream_t st) {
   const size_t smem = sizeof(Smem<T>);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(step_kernel<T, DEV, XOR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    attr_set = true;
-  }
+  kernel_setup((const void*)step_kernel<T, DEV, XOR>, NT, smem);
   dim3 block(TX, TY);
   dim3 grid((p.nx + TX - 1) / TX, (p.ny + TY - 1) / TY);
   step_kernel<T, DEV, XOR><<<grid, block, smem, st>>>(p, make_consts<T>(p), in, out, solid, Kref,
@@ -412,6 +410,27 @@ void launch_step_t(const StepParams& p, const T* in, T* out, const uint8_t* soli
 }
 
 }  // namespace
+
+int kernel_setup(const void* kernel, int threads, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> resident;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  const auto key = std::make_pair(kernel, dev);
+  auto it = resident.find(key);
+  if (it != resident.end()) return it->second;
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0, sms = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int n = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+  resident.emplace(key, n);
+  return n;
+}
 
 // ---------------------------------------------------------------- batch helpers
 size_t batch_table_bytes(int ndom, bool f64) {
@@ -498,8 +517,10 @@ void launch_prepare(double cfl, DevScalars* sc, cudaStream_t st) {
 }
 
 void launch_prologue_f64(const StepParams& p, const double* q, const uint8_t* solid,
-                         unsigned long long* colsum, DevScalars* sc, cudaStream_t st) {
-  prologue_kernel<<<grid_1d((size_t)p.nx * p.ny), 256, 0, st>>>(p, q, solid, colsum, sc);
+                         unsigned long long* colsum, DevScalars* sc, cudaStream_t st,
+                         int status_bits) {
+  prologue_kernel<<<grid_1d((size_t)p.nx * p.ny), 256, 0, st>>>(p, q, solid, colsum, sc,
+                                                                 status_bits);
 }
 
 void launch_to_dev(const StepParams& p, const double* q, const uint8_t* solid, const int32_t* K,

@@ -26,7 +26,8 @@ struct DevScalars {
   long long steps;
   double dt_cur;          // dt of the next step (cfl / rate_cur)
   float dt_cur_f;         // same, rounded to float
-  int status;             // bit 0: non-admissible state produced
+  int status;             // bit 0: non-admissible state produced; bit 1 (fv_step_static
+                          // only): non-admissible input state
 };
 
 // Equilibrium density table: rhoE[h + 2 ny] = rho0 exp(-kappa (h dy / 2)) for
@@ -95,8 +96,11 @@ void launch_finalize(const StepParams& p, int32_t* Kref, int32_t* Kcur,
                      unsigned long long* colsum, DevScalars* sc, int count_step,
                      cudaStream_t st);
 void launch_prepare(double cfl, DevScalars* sc, cudaStream_t st);
+// Levels' column sums and the signal rate of a state q (before its first
+// step); a non-admissible fluid cell sets status_bits in sc->status.
 void launch_prologue_f64(const StepParams& p, const double* q, const uint8_t* solid,
-                         unsigned long long* colsum, DevScalars* sc, cudaStream_t st);
+                         unsigned long long* colsum, DevScalars* sc, cudaStream_t st,
+                         int status_bits = 1);
 void launch_to_dev(const StepParams& p, const double* q, const uint8_t* solid,
                    const int32_t* K, const Tables& tb, float* out, cudaStream_t st);
 void launch_from_dev(const StepParams& p, const float* in, const uint8_t* solid,
@@ -134,6 +138,14 @@ void launch_batch_step(bool f64, const void* table, const int4* work, int nwork,
 void launch_batch_finalize(bool f64, const void* table, int ndom, double cfl, int count_step,
                            cudaStream_t st);
 void launch_batch_prepare(bool f64, const void* table, int ndom, double cfl, cudaStream_t st);
+
+// One-time set-up of a kernel on the current device, cached per kernel and
+// device ordinal (thread-safe): opts the kernel into `smem` bytes of dynamic
+// shared memory and returns the number of CTAs of `threads` threads that are
+// resident at once on that device (CTAs per SM x SMs, at least 1).  Every
+// launch with more than 48 KB of dynamic shared memory goes through it, so a
+// handle created on a second GPU gets the opt-in on that GPU too.
+int kernel_setup(const void* kernel, int threads, size_t smem);
 
 // Message returned by fv_last_error() on this thread.
 void set_last_error(const char* msg);

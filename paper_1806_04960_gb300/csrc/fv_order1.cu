@@ -238,12 +238,7 @@ void launch_o1_xt(const StepParams& p, const T* in, T* out, const uint8_t* solid
                   const int32_t* Kref, const int32_t* Kcur, unsigned long long* colsum,
                   DevScalars* sc, const T* rt, const T* rq, const T* pq, cudaStream_t st) {
   const size_t smem = sizeof(SmemO1<T>);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(step_o1_kernel<T, DEV, XOR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    attr_set = true;
-  }
+  kernel_setup((const void*)step_o1_kernel<T, DEV, XOR>, TX * TY, smem);
   dim3 block(TX, TY);
   dim3 grid((p.nx + TX - 1) / TX, (p.ny + TY - 1) / TY);
   step_o1_kernel<T, DEV, XOR><<<grid, block, smem, st>>>(p, make_consts<T>(p), in, out, solid,

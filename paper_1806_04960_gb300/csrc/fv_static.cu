@@ -44,9 +44,18 @@ std::mutex g_scratch_mutex;
 // Host copy of the equilibrium density table rho^E(h dy / 2) = rho0 exp(-kappa
 // h dy / 2), h in [-2 ny, 2 ny], filled with the same host arithmetic as
 // fv_create's table; a fixed static buffer, guarded by g_table_mutex while it is
-// filled and copied.
+// filled and copied.  The table is copied to a device's array only when its
+// parameters (ny, dy, rho0, kappa) differ from the ones last copied there.
 double g_host_table[4 * (size_t)kMaxNy + 1];
 std::mutex g_table_mutex;
+struct TableKey {
+  int ny = -1;
+  double dy = 0.0, rho0 = 0.0, kappa = 0.0;
+  bool operator==(const TableKey& o) const {
+    return ny == o.ny && dy == o.dy && rho0 == o.rho0 && kappa == o.kappa;
+  }
+};
+TableKey g_table_key[kMaxDevices];
 
 fv_status static_fail(fv_status s, const std::string& m) {
   fv::set_last_error(m.c_str());
@@ -55,7 +64,7 @@ fv_status static_fail(fv_status s, const std::string& m) {
 
 // Device address of this device's scratch array, looked up once per device
 // with that device current.
-fv_status scratch_for_current_device(unsigned char** out) {
+fv_status scratch_for_current_device(unsigned char** out, int* dev_out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return static_fail(FV_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
@@ -69,6 +78,7 @@ fv_status scratch_for_current_device(unsigned char** out) {
     g_scratch_ptr[dev] = (unsigned char*)p;
   }
   *out = g_scratch_ptr[dev];
+  *dev_out = dev;
   return FV_OK;
 }
 
@@ -93,8 +103,9 @@ extern "C" fv_status fv_step_static(const fv_grid* grid, const fv_eos* eos, cons
   if (!(cfl > 0.0) || !(cfl <= 1.0)) return static_fail(FV_EINVAL, "fv_step_static: cfl must be in (0, 1]");
   if (q_in == q_out) return static_fail(FV_EINVAL, "fv_step_static: q_in and q_out must not alias");
 
+  int dev = 0;
   unsigned char* base = nullptr;
-  fv_status st = scratch_for_current_device(&base);
+  fv_status st = scratch_for_current_device(&base, &dev);
   if (st != FV_OK) return st;
   DevScalars* sc = (DevScalars*)(base + kOffScalars);
   unsigned long long* colsum = (unsigned long long*)(base + kOffColsum);
@@ -124,15 +135,23 @@ extern "C" fv_status fv_step_static(const fv_grid* grid, const fv_eos* eos, cons
   if (e != cudaSuccess) return static_fail(FV_ECUDA, std::string("fv_step_static: ") + cudaGetErrorString(e));
   {
     std::lock_guard<std::mutex> lock(g_table_mutex);
-    for (long h2 = -2L * p.ny; h2 <= 2L * p.ny; ++h2)
-      g_host_table[h2 + 2L * p.ny] = p.rho0 * std::exp(-p.kappa * (0.5 * (double)h2) * p.dy);
-    // pageable source: the copy has consumed the buffer when the call returns
-    e = cudaMemcpyAsync(rhoE, g_host_table, sizeof(double) * (4 * (size_t)p.ny + 1),
-                        cudaMemcpyHostToDevice, stream);
+    TableKey key;
+    key.ny = p.ny;
+    key.dy = p.dy;
+    key.rho0 = p.rho0;
+    key.kappa = p.kappa;
+    if (!(key == g_table_key[dev])) {
+      for (long h2 = -2L * p.ny; h2 <= 2L * p.ny; ++h2)
+        g_host_table[h2 + 2L * p.ny] = p.rho0 * std::exp(-p.kappa * (0.5 * (double)h2) * p.dy);
+      // pageable source: the copy has consumed the buffer when the call returns
+      e = cudaMemcpyAsync(rhoE, g_host_table, sizeof(double) * (4 * (size_t)p.ny + 1),
+                          cudaMemcpyHostToDevice, stream);
+      g_table_key[dev] = e == cudaSuccess ? key : TableKey{};
+    }
   }
   if (e != cudaSuccess) return static_fail(FV_ECUDA, std::string("fv_step_static: ") + cudaGetErrorString(e));
   // Levels and signal rate of q_in (Eq. (Free_surf_detector), CFL), then the step.
-  launch_prologue_f64(p, q_in, solid, colsum, sc, stream);
+  launch_prologue_f64(p, q_in, solid, colsum, sc, stream, 2);
   launch_finalize(p, Kref, Kcur, colsum, sc, 0, stream);
   launch_prepare(cfl, sc, stream);
   Tables tb{rhoE, nullptr};
@@ -146,7 +165,11 @@ extern "C" fv_status fv_step_static(const fv_grid* grid, const fv_eos* eos, cons
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return static_fail(FV_ECUDA, std::string("fv_step_static: ") + cudaGetErrorString(e));
     *dt_out = h.dt_cur;
-    if (h.status) return static_fail(FV_ENONFINITE, "fv_step_static: non-admissible state");
+    if (h.status & 2)
+      return static_fail(FV_EINVAL, "fv_step_static: q_in has a fluid cell with alpha <= 0, "
+                                    "alpha*rho <= 0 or a non-finite value");
+    if (h.status & 1)
+      return static_fail(FV_ENONFINITE, "fv_step_static: the step produced a non-admissible state");
   }
   return FV_OK;
 }

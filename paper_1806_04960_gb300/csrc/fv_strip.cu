@@ -303,16 +303,7 @@ void launch_strip_xt(const StepParams& p, const T* in, T* out, const uint8_t* so
                      DevScalars* sc, const T* rt, int strip_h, cudaStream_t st) {
   constexpr int NTS = strip_threads<T>();
   const size_t smem = sizeof(StripSmem<T>);
-  static int resident = 0;
-  if (!resident) {
-    cudaFuncSetAttribute(strip_kernel<T, DEV, XOR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    int per_sm = 0, dev = 0, sms = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, strip_kernel<T, DEV, XOR>, NTS, smem);
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    resident = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
-  }
+  const int resident = kernel_setup((const void*)strip_kernel<T, DEV, XOR>, NTS, smem);
   const int H = strip_h > 0 ? strip_h : strip_height(p.nx, p.ny, resident);
   const dim3 grid((p.nx + SX - 1) / SX, (p.ny + H - 1) / H);
   strip_kernel<T, DEV, XOR><<<grid, NTS, smem, st>>>(p, make_consts<T>(p), in, out, solid, Kref,
@@ -321,19 +312,8 @@ void launch_strip_xt(const StepParams& p, const T* in, T* out, const uint8_t* so
 
 template <typename T, bool DEV>
 int batch_grid_t() {
-  static int grid = 0;
-  if (!grid) {
-    const size_t smem = sizeof(StripSmem<T>);
-    cudaFuncSetAttribute(batch_strip_kernel<T, DEV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    int per_sm = 0, dev = 0, sms = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_strip_kernel<T, DEV>,
-                                                  strip_threads<T>(), smem);
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    grid = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
-  }
-  return grid;
+  return kernel_setup((const void*)batch_strip_kernel<T, DEV>, strip_threads<T>(),
+                      sizeof(StripSmem<T>));
 }
 
 }  // namespace
