@@ -340,6 +340,18 @@ fv_status fv_step_static(const fv_grid* grid, const fv_eos* eos, const int32_t s
                          const uint8_t* solid, const double* q_in, double* q_out, double cfl,
                          void* cuda_stream, double* dt_out);
 
+/* Measured fused multiply-add peak of the current device (roofline
+ * denominator of the step kernels, which run on the plain FP32/FP64 pipes; the
+ * paper has no counterpart).  kind 0: FP32 scalar FFMA; 1: FP32 paired FFMA2
+ * (two lanes per instruction); 2: FP64 DFMA.  Runs `reps` >= 1 timed launches
+ * of 8 CTAs x 256 threads per SM, each thread advancing 8 independent
+ * recurrences a <- a b + c (about 30 ms per launch), after one warm-up, on a
+ * stream of its own; *tflops receives 2 x FMAs / the fastest launch's CUDA-
+ * event time in TFLOP/s, *best_ms (nullable) that time.  Allocates and frees
+ * a small output buffer; synchronises.  FV_EINVAL for a bad argument,
+ * FV_ECUDA on a CUDA error. */
+fv_status fv_measure_fma_peak(int32_t kind, int32_t reps, double* tflops, double* best_ms);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* fv_last_error(void);
 

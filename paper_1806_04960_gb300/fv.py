@@ -116,6 +116,8 @@ _lib.fv_host_yface.restype = C.c_int
 _lib.fv_adjoint.argtypes = [_H, C.POINTER(fv_adjoint_spec), C.c_void_p, C.c_int,
                             C.POINTER(fv_adjoint_info)]
 _lib.fv_adjoint.restype = C.c_int
+_lib.fv_measure_fma_peak.argtypes = [C.c_int32, C.c_int32, _D, _D]
+_lib.fv_measure_fma_peak.restype = C.c_int
 _lib.fv_set_order.argtypes = [_H, C.c_int32]
 _lib.fv_set_order.restype = C.c_int
 _lib.fv_set_xface.argtypes = [_H, C.c_int32]
@@ -151,7 +153,7 @@ ABI_SYMBOLS = ("fv_create", "fv_set_state", "fv_step", "fv_step_timed", "fv_get_
                "fv_host_adjoint_step", "fv_set_order", "fv_host_yface_o1",
                "fv_host_xface_or", "fv_set_xface", "fv_set_tiling", "fv_host_face_f32",
                "fv_set_strip_height", "fv_tune", "fv_host_height_step", "fv_batch_tune",
-               "fv_batch_set_launch")
+               "fv_batch_set_launch", "fv_measure_fma_peak")
 
 
 def _check(st):
@@ -287,6 +289,14 @@ def fv_host_cell_ops() -> dict:
     d = {k: int(v) for k, v in zip(names, out)}
     d["flops"] = d["add"] + d["mul"] + d["div"] + d["sqrt"]
     return d
+
+
+def fv_measure_fma_peak(kind: int, reps: int = 3):
+    """Measured FMA peak of the current device: kind 0 FP32 FFMA, 1 FP32
+    FFMA2, 2 FP64 DFMA.  Returns (TFLOP/s, fastest launch in ms)."""
+    tf, ms = C.c_double(0.0), C.c_double(0.0)
+    _check(_lib.fv_measure_fma_peak(int(kind), int(reps), C.byref(tf), C.byref(ms)))
+    return tf.value, ms.value
 
 
 def fv_create(grid: fv_grid, eos: fv_eos, bc: fv_bc, prec: int, stream: int = 0):
