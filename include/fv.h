@@ -304,6 +304,59 @@ int32_t fv_batch_size(const fv_batch* b);
 /* Release the ensemble (synchronises; NULL is a no-op). */
 void fv_batch_destroy(fv_batch* b);
 
+/* ---------------------------------------------------------------------------
+ * Partitioned domains, for one grid over several GPUs (x strips: the scheme's
+ * stencil, Eq. (Scheme), reaches two columns to each side of a cell, and the
+ * levels of Eq. (Free_surf_detector) are sums over whole columns; the paper
+ * runs on one GPU and has no partition of its own).  One grid of NX
+ * columns is split into strips owning columns [a_k, b_k); strip k is a handle
+ * created (fv_create) on columns [a_k - 2, b_k + 2) of the grid, clipped at the
+ * grid's sides (its x0, solid mask and the grid's W/E boundary kinds on the
+ * clipped sides accordingly; an inner side's kind is irrelevant).  Its state
+ * (fv_set_state) is the grid's state on those columns.  Per step, for every
+ * strip: fv_step(h, 1, cfl, NULL); then fv_part_rate into one device double
+ * per strip and fv_part_set_rate with all of them (strips on one GPU) or with
+ * their all-reduce(max) (strips on several GPUs); then fv_part_pack of both
+ * inner sides, the transfer of each buffer to the neighbouring strip (the same
+ * device buffer on one GPU, a send/receive between GPUs), and fv_part_unpack
+ * there.  After
+ * fv_set_state the rate exchange is done once before the first step.  The
+ * owned cells then hold bit for bit what one handle on the whole grid
+ * computes, in both precisions.  All calls are asynchronous on the handle's
+ * stream; the caller orders the transfers between streams. */
+
+/* Owned columns [own_lo, own_hi) of this handle's grid: own_lo is 0 (the grid's
+ * W side) or 2 (a strip to the W), nx - own_hi is 0 or 2, own_hi - own_lo >= 2;
+ * (0, 0) = not partitioned (the default).  Only owned cells count in the signal
+ * rate and the status; fv_step and fv_step_timed then take n <= 1 and
+ * fv_adjoint is refused.  FV_EINVAL otherwise. */
+fv_status fv_set_partition(fv_handle* h, int32_t own_lo, int32_t own_hi);
+
+/* Bytes of one side's halo buffer: 4 planes x ny rows x 2 columns of the
+ * handle's element type (double in FV_FP64, float in FV_FP32_DEV, as stored:
+ * alpha rho as its deviation from equilibrium in FP32), plane-major then row
+ * then column, followed by 4 int32 (the 2 columns' levels of the stored state
+ * and of the next step). */
+fv_status fv_part_halo_bytes(const fv_handle* h, int64_t* bytes);
+
+/* Copy the signal rate of the handle's current state (the largest over its
+ * owned fluid cells; over all its cells right after fv_set_state, whose halo
+ * columns then hold the grid's true values) to rate_dev (one device double). */
+fv_status fv_part_rate(fv_handle* h, double* rate_dev);
+
+/* Adopt the largest of the n >= 1 device doubles rates_dev[0..n) (the strips'
+ * rates, or one already reduced across GPUs) as the current state's signal
+ * rate; the next fv_step takes dt = cfl / rate from it and adds that dt to the
+ * simulated time. */
+fv_status fv_part_set_rate(fv_handle* h, const double* rates_dev, int32_t n);
+
+/* side 0 (W) / 1 (E): pack the 2 owned columns next to that side into buf_dev
+ * (device, fv_part_halo_bytes bytes; the receiving strip's halo on its other
+ * side) / unpack buf_dev into the 2 halo columns of that side.  FV_EINVAL if
+ * the side has no neighbouring strip or the handle has no state. */
+fv_status fv_part_pack(fv_handle* h, int32_t side, void* buf_dev);
+fv_status fv_part_unpack(fv_handle* h, int32_t side, const void* buf_dev);
+
 /* Largest grid fv_step_static accepts (size of its static scratch array). */
 #define FV_STATIC_MAX_NX 8192
 #define FV_STATIC_MAX_NY 8192

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(PKG, "libfv.so")
 BUILD = os.path.join(PKG, "_build")
 SOURCES = ["fv_kernels.cu", "fv_strip.cu", "fv_api.cu", "fv_host_model.cu", "fv_static.cu",
-           "fv_batch.cu", "fv_adjoint.cu", "fv_order1.cu", "fv_peak.cu"]
+           "fv_batch.cu", "fv_adjoint.cu", "fv_order1.cu", "fv_peak.cu", "fv_part.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

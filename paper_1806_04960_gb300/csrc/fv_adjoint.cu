@@ -1276,6 +1276,10 @@ extern "C" fv_status fv_adjoint(fv_handle* h, const fv_adjoint_spec* spec, doubl
     set_last_error("fv_adjoint: null argument");
     return FV_EINVAL;
   }
+  if (h->own_hi > 0) {
+    set_last_error("fv_adjoint: the handle is one strip of a partitioned domain");
+    return FV_EINVAL;
+  }
   if (!h->has_state) {
     set_last_error("fv_adjoint: no state (call fv_set_state first)");
     return FV_EINVAL;

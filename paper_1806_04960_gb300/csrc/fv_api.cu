@@ -232,6 +232,8 @@ fv_status fv_step(fv_handle* h, int32_t n, double cfl, double* t_out) {
   if (n < 0) return fail(FV_EINVAL, "fv_step: n must be >= 0");
   if (!(cfl > 0.0) || !(cfl <= 1.0)) return fail(FV_EINVAL, "fv_step: cfl must be in (0, 1]");
   if (!h->has_state) return fail(FV_EINVAL, "fv_step: no state (call fv_set_state first)");
+  if (h->own_hi > 0 && n > 1)
+    return fail(FV_EINVAL, "fv_step: a strip of a partitioned domain advances one step per call");
   h->cfl = cfl;
   const StepParams p = params_of(h, cfl);
   if (n > 0) launch_prepare(cfl, h->d_sc, h->stream);
@@ -258,6 +260,8 @@ fv_status fv_step_timed(fv_handle* h, int32_t n, double cfl, double* kernel_ms,
   if (n < 0) return fail(FV_EINVAL, "fv_step_timed: n must be >= 0");
   if (!(cfl > 0.0) || !(cfl <= 1.0)) return fail(FV_EINVAL, "fv_step_timed: cfl must be in (0, 1]");
   if (!h->has_state) return fail(FV_EINVAL, "fv_step_timed: no state (call fv_set_state first)");
+  if (h->own_hi > 0 && n > 1)
+    return fail(FV_EINVAL, "fv_step_timed: a strip of a partitioned domain advances one step per call");
   h->cfl = cfl;
   const StepParams p = params_of(h, cfl);
   std::vector<cudaEvent_t> ev(2 * (size_t)n + 2);

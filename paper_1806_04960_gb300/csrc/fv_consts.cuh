@@ -81,19 +81,23 @@ __device__ __forceinline__ int32_t level_of(unsigned long long colsum, int ny) {
 // Per-cell epilogue of a step on the new state qn (stored form) with full
 // alpha rho m_full: admissibility, the signal rate of the next dt (reading
 // R-cfl) and the detector weight of Eq. (Free_surf_detector) on the common
-// 2^-32 fixed-point scale.
+// 2^-32 fixed-point scale.  own = false (a halo column of a partitioned
+// domain, whose new values are replaced by its owner's): the cell adds no rate
+// and no status.
 template <typename T, bool DEV>
 __device__ __forceinline__ void cell_epilogue(const StepParams& p, const KConsts<T>& kc,
                                               const T qn[4], T m_full, T& my_rate,
-                                              unsigned long long& my_w, bool& bad) {
+                                              unsigned long long& my_w, bool& bad,
+                                              bool own = true) {
   if (DEV) {
     // float path: in float; the max is taken in double by the reduction
     const T r = rcp(m_full);
     const T u = qn[1] * r, v = qn[2] * r;
-    if (!(m_full > T(0)) || !(qn[3] > T(0)) || !isfinite(u) || !isfinite(v) || !isfinite(qn[3]))
+    if (own && (!(m_full > T(0)) || !(qn[3] > T(0)) || !isfinite(u) || !isfinite(v) ||
+                !isfinite(qn[3])))
       bad = true;
     const T rt_ = (tabs(u) + kc.P.c) * kc.inv_dx + (tabs(v) + kc.P.c) * kc.inv_dy;
-    my_rate = rt_ >= T(0) ? rt_ : T(0);
+    my_rate = own && rt_ >= T(0) ? rt_ : T(0);
     T w = (qn[3] - kc.eps) * kc.inv_1meps;
     w = w >= T(0) ? (w > T(1) ? T(1) : w) : T(0);  // NaN -> 0 (the status flag reports it)
     // 2^-24 resolution in float, placed on the common 2^-32 fixed-point scale
@@ -103,9 +107,10 @@ __device__ __forceinline__ void cell_epilogue(const StepParams& p, const KConsts
     // and the detected levels are reproducible
     const double md = (double)m_full, ad = (double)qn[3];
     const double ud = (double)qn[1] / md, vd = (double)qn[2] / md;
-    if (!(md > 0.0) || !(ad > 0.0) || !isfinite(ud) || !isfinite(vd) || !isfinite(ad)) bad = true;
+    if (own && (!(md > 0.0) || !(ad > 0.0) || !isfinite(ud) || !isfinite(vd) || !isfinite(ad)))
+      bad = true;
     const double rd = (fabs(ud) + p.c) / p.dx + (fabs(vd) + p.c) / p.dy;
-    my_rate = rd >= 0.0 ? (T)rd : T(0);
+    my_rate = own && rd >= 0.0 ? (T)rd : T(0);
     double w = (ad - p.eps) / (1.0 - p.eps);
     w = w >= 0.0 ? (w > 1.0 ? 1.0 : w) : 0.0;  // NaN -> 0 (the status flag reports it)
     my_w = (unsigned long long)__double2ll_rn(w * 4294967296.0);

@@ -39,6 +39,8 @@ struct fv_handle {
   int mass_blocks = 0;
   bool has_state = false;
   double cfl = 0.9;
+  int own_lo = 0;               // owned columns of a partitioned domain (fv_set_partition)
+  int own_hi = 0;               // 0 = the whole grid
 };
 
 inline fv::StepParams params_of(const fv_handle* h, double cfl) {
@@ -56,6 +58,10 @@ inline fv::StepParams params_of(const fv_handle* h, double cfl) {
   p.kappa = h->eos.g * h->eos.rho0 / h->eos.k0;
   for (int s = 0; s < 4; ++s) p.side[s] = h->side[s];
   p.cfl = cfl;
+  if (h->own_hi > 0) {
+    p.own_lo = h->own_lo;
+    p.own_hi = h->own_hi;
+  }
   return p;
 }
 

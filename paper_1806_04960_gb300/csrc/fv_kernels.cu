@@ -182,7 +182,8 @@ __device__ __forceinline__ void step_tile(const StepParams& p, const KConsts<T>&
 #pragma unroll
     for (int v = 0; v < 4; ++v) qout[v * N + c] = qn[v];
     // epilogue: admissibility, signal rate, detector weight
-    cell_epilogue<T, DEV>(p, kc, qn, m_full, my_rate, my_w, bad);
+    cell_epilogue<T, DEV>(p, kc, qn, m_full, my_rate, my_w, bad,
+                          gi_me >= p.own_lo && gi_me < p.own_hi);
   } else if (inside) {
     const size_t c = (size_t)gj_me * nx + gi_me;
 #pragma unroll

@@ -15,6 +15,10 @@ struct StepParams {
   double rho0, k0, g, eps, c, c2, kappa;
   int side[4];            // W, E, S, N: 0 wall, 1 transmissive
   double cfl;
+  // Columns whose cells count in the signal rate and the status (a partitioned
+  // domain's own columns; its halo columns are replaced by their owner's
+  // values after each step); the whole grid unless set.
+  int own_lo = 0, own_hi = 1 << 30;
 };
 
 // Device-resident step bookkeeping (one per domain).

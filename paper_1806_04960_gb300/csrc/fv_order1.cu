@@ -223,7 +223,8 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? 2 : 4))
     const size_t c = (size_t)gj_me * nx + gi_me;
 #pragma unroll
     for (int v = 0; v < 4; ++v) qout[v * N + c] = qn[v];
-    cell_epilogue<T, DEV>(p, kc, qn, m_full, my_rate, my_w, bad);
+    cell_epilogue<T, DEV>(p, kc, qn, m_full, my_rate, my_w, bad,
+                          gi_me >= p.own_lo && gi_me < p.own_hi);
   } else if (inside) {
     const size_t c = (size_t)gj_me * nx + gi_me;
 #pragma unroll

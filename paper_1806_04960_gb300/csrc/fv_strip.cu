@@ -161,6 +161,7 @@ __device__ __forceinline__ void strip_body(const StepParams& p, const KConsts<T>
   bool bad = false;
   const int ux = t % SX, uy = t / SX;  // update: column and row in the block (t < 256)
   const int gi_me = i0 + ux;
+  const bool own_me = gi_me >= p.own_lo && gi_me < p.own_hi;
 
   // the next block's window cell of this thread (t < 288), loaded one block
   // ahead: cell (pwi, pk) of its 8 new rows
@@ -228,7 +229,7 @@ __device__ __forceinline__ void strip_body(const StepParams& p, const KConsts<T>
         for (int v = 0; v < 4; ++v) qout[v * N + c] = qn[v];
         T rate = T(0);
         unsigned long long w = 0;
-        cell_epilogue<T, DEV>(p, kc, qn, m_full, rate, w, bad);
+        cell_epilogue<T, DEV>(p, kc, qn, m_full, rate, w, bad, own_me);
         my_rate = fmax(my_rate, rate);
         my_w += w;
       } else if (inside) {

@@ -116,6 +116,15 @@ _lib.fv_host_yface.restype = C.c_int
 _lib.fv_adjoint.argtypes = [_H, C.POINTER(fv_adjoint_spec), C.c_void_p, C.c_int,
                             C.POINTER(fv_adjoint_info)]
 _lib.fv_adjoint.restype = C.c_int
+_lib.fv_set_partition.argtypes = [_H, C.c_int32, C.c_int32]
+_lib.fv_part_halo_bytes.argtypes = [_H, C.POINTER(C.c_int64)]
+_lib.fv_part_rate.argtypes = [_H, C.c_void_p]
+_lib.fv_part_set_rate.argtypes = [_H, C.c_void_p, C.c_int32]
+_lib.fv_part_pack.argtypes = [_H, C.c_int32, C.c_void_p]
+_lib.fv_part_unpack.argtypes = [_H, C.c_int32, C.c_void_p]
+for _f in ("fv_set_partition", "fv_part_halo_bytes", "fv_part_rate", "fv_part_set_rate",
+           "fv_part_pack", "fv_part_unpack"):
+    getattr(_lib, _f).restype = C.c_int
 _lib.fv_measure_fma_peak.argtypes = [C.c_int32, C.c_int32, _D, _D]
 _lib.fv_measure_fma_peak.restype = C.c_int
 _lib.fv_set_order.argtypes = [_H, C.c_int32]
@@ -153,7 +162,9 @@ ABI_SYMBOLS = ("fv_create", "fv_set_state", "fv_step", "fv_step_timed", "fv_get_
                "fv_host_adjoint_step", "fv_set_order", "fv_host_yface_o1",
                "fv_host_xface_or", "fv_set_xface", "fv_set_tiling", "fv_host_face_f32",
                "fv_set_strip_height", "fv_tune", "fv_host_height_step", "fv_batch_tune",
-               "fv_batch_set_launch", "fv_measure_fma_peak")
+               "fv_batch_set_launch", "fv_measure_fma_peak", "fv_set_partition",
+               "fv_part_halo_bytes", "fv_part_rate", "fv_part_set_rate", "fv_part_pack",
+               "fv_part_unpack")
 
 
 def _check(st):
@@ -289,6 +300,40 @@ def fv_host_cell_ops() -> dict:
     d = {k: int(v) for k, v in zip(names, out)}
     d["flops"] = d["add"] + d["mul"] + d["div"] + d["sqrt"]
     return d
+
+
+def _dev_addr(x) -> int:
+    """Device address of a contiguous CUDA tensor (any dtype)."""
+    if not (getattr(x, "is_cuda", False) and x.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
+    return x.data_ptr()
+
+
+def fv_set_partition(h, own_lo: int, own_hi: int) -> None:
+    _check(_lib.fv_set_partition(h, int(own_lo), int(own_hi)))
+
+
+def fv_part_halo_bytes(h) -> int:
+    n = C.c_int64(0)
+    _check(_lib.fv_part_halo_bytes(h, C.byref(n)))
+    return n.value
+
+
+def fv_part_rate(h, rate_dev) -> None:
+    _check(_lib.fv_part_rate(h, C.c_void_p(_dev_addr(rate_dev))))
+
+
+def fv_part_set_rate(h, rates_dev) -> None:
+    """Adopt the largest of the device doubles in ``rates_dev``."""
+    _check(_lib.fv_part_set_rate(h, C.c_void_p(_dev_addr(rates_dev)), int(rates_dev.numel())))
+
+
+def fv_part_pack(h, side: int, buf_dev) -> None:
+    _check(_lib.fv_part_pack(h, int(side), C.c_void_p(_dev_addr(buf_dev))))
+
+
+def fv_part_unpack(h, side: int, buf_dev) -> None:
+    _check(_lib.fv_part_unpack(h, int(side), C.c_void_p(_dev_addr(buf_dev))))
 
 
 def fv_measure_fma_peak(kind: int, reps: int = 3):

@@ -82,6 +82,24 @@ def test_fp64_dambreak_cfl09_matches_oracle(fv):
     assert abs(tg - to) <= 1e-12 * to
 
 
+def test_fp64_dambreak_cfl09_200_steps_agreement(fv):
+    """The configured run: 200 steps at CFL 0.9.  From about step 140 the
+    wall-row instability of the unsplit step at this CFL (finding F1) grows
+    rounding differences ~4x per step, so no two orderings of the arithmetic
+    agree to 1e-10 at step 200 (measured FP64 GPU vs oracle relative L1: 1.7e-5
+    alpha rho, 9.5e-4 / 7.5e-4 momenta, 9.7e-7 alpha; at step 100: <= 5.2e-14).
+    The largest agreement that holds, with a margin for a different rounding
+    history, is asserted."""
+    c = cases.c1()
+    qo, to, _, _ = O.run(c, 200)
+    qg, tg, _, d = gpu_run(fv, c, 200)
+    e1 = rel_l1(qg, qo)
+    assert d.status == 0 and d.steps == 200
+    assert e1[0] <= 2e-4 and e1[3] <= 1e-5, e1
+    assert e1[1] <= 1e-2 and e1[2] <= 1e-2, e1
+    assert abs(tg - to) <= 1e-6 * to
+
+
 def test_fp64_dt_and_levels_identical_each_step(fv):
     c = cases.c1()
     s = fv.Solver(c, fv.FV_FP64)
@@ -320,14 +338,19 @@ def test_full_size_lake_at_rest(fv, prec):
     assert np.abs(q[0] - c.q[0])[fl].max() <= tol
 
 
-def test_fp32_dambreak_error_vs_oracle(fv):
+@pytest.mark.parametrize("cfl,steps", [(0.45, 200), (0.9, 100)])
+def test_fp32_dambreak_error_vs_oracle(fv, cfl, steps):
+    """FP32 deviation form against the FP64 oracle, relative L1 <= 1e-4 in all
+    four components (measured at CFL 0.45 / 200 steps: 7.2e-7, 3.3e-5, 3.0e-5,
+    4.0e-7; at CFL 0.9 / 100 steps: 4.8e-7, 1.9e-5, 1.9e-5, 3.4e-7).  At CFL 0.9
+    beyond step ~140 finding F1 applies to both precisions (see the FP64 test
+    of the configured run)."""
     c = cases.c1()
-    qo, to, _, _ = O.run(c, 200, cfl=0.45)
-    qg, tg, _, d = gpu_run(fv, c, 200, prec=fv.FV_FP32_DEV, cfl=0.45)
+    qo, to, _, _ = O.run(c, steps, cfl=cfl)
+    qg, tg, _, d = gpu_run(fv, c, steps, prec=fv.FV_FP32_DEV, cfl=cfl)
     e1 = rel_l1(qg, qo)
     assert d.status == 0
-    assert e1[0] <= 1e-4 and e1[3] <= 1e-4, e1
-    assert e1[1] <= 1e-3 and e1[2] <= 1e-3, e1
+    assert np.all(e1 <= 1e-4), e1
     assert abs(tg - to) <= 1e-5 * to
 
 
@@ -342,27 +365,34 @@ def test_fp32_mass_conservation(fv):
     assert abs(m1 - m0) <= 1e-5 * m0
 
 
-def test_drop_fp32_follows_fp64_and_exact_solution(fv):
-    """Config 3 at 1024^2 (2000 steps, t = 2.2e-3): the FP32 and FP64 semi-axes
-    agree to 5e-3 (measured 2.8e-3; 1.1e-4 at 2048^2 in the benchmark) and
-    follow the exact elliptical-drop solution within 2 %.
-    (The eps-gas next to the receding liquid comes close to cavitation; at
-    512^2 and 768^2 a run survives or not depending on the rounding of its
-    arithmetic, while 1024^2 keeps alpha rho >= 0.7 in both precisions.)"""
-    from oracle_refs import drop_semi_axes
+def test_drop_history_matches_the_oracle(fv):
+    """Config 3's semi-axis history against the FP64 oracle's (Section 5.2; the
+    oracle's 1024^2 run stored by tests/golden/make_drop_history.py, pinned
+    to the paper's b(0.0008) and the exact solution): both GPU precisions at
+    1024^2, every 100 of 2000 steps (t = 2.2e-3), same t and semi-axes from
+    the alpha = 0.5 crossings.  The gas next to the receding liquid amplifies
+    rounding differences (finding F2), so the agreement loosens with time;
+    the bounds hold the measured maxima with a margin."""
+    from oracle_refs import read_golden
     from test_oracle_pins import drop_axes
+    ref = np.array([[float(x) for x in r] for r in read_golden("drop_history_oracle_1024.txt")])
     c = cases.drop(1024)
-    res = {}
-    for prec in (fv.FV_FP64, fv.FV_FP32_DEV):
+    worst = {}
+    for name, prec in (("f64", fv.FV_FP64), ("f32", fv.FV_FP32_DEV)):
         s = fv.Solver(c, prec)
         s.set_state(c.q)
-        t = s.step(2000, c.cfl, want_time=True)
-        res[prec] = (t, drop_axes(c, s.get_state()))
+        ea = eb = et = 0.0
+        for step, t_o, a_o, b_o in ref:
+            t = s.step(100, c.cfl, want_time=True)
+            a, b = drop_axes(c, s.get_state())
+            et = max(et, abs(t - t_o) / t_o)
+            ea = max(ea, abs(a - a_o) / a_o)
+            eb = max(eb, abs(b - b_o) / b_o)
         s.close()
-    (t64, (a64, b64)), (t32, (a32, b32)) = res[fv.FV_FP64], res[fv.FV_FP32_DEV]
-    assert abs(b32 - b64) <= 5e-3 * b64 and abs(a32 - a64) <= 5e-3 * a64
-    a_ex, b_ex = drop_semi_axes(t64, nsub=4000)
-    assert abs(b64 - b_ex) <= 0.02 * b_ex and abs(a64 - a_ex) <= 0.02 * a_ex
+        worst[name] = (et, ea, eb)
+    print("drop history vs oracle (t, a, b):", worst)
+    assert worst["f64"][0] <= 1e-9 and max(worst["f64"][1:]) <= 1e-3, worst
+    assert worst["f32"][0] <= 1e-4 and max(worst["f32"][1:]) <= 5e-3, worst
 
 
 @pytest.mark.parametrize("prec", [0, 1])
