@@ -244,6 +244,21 @@ typedef struct {
 fv_status fv_adjoint(fv_handle* h, const fv_adjoint_spec* spec, double* dL_dq0, int on_device,
                      fv_adjoint_info* info);
 
+/* The map whose derivative fv_adjoint returns (reading R-adj; the paper
+ * computes no gradient): n >= 0 steps of Eq. (Scheme) from the handle's state,
+ * step k (0-based) taking dt[k] (host, finite, >= 0) and the levels
+ * K[k*nx .. k*nx + nx) (host, each in [0, ny]) instead of its own, as
+ * fv_adjoint holds them (record them from a free run with fv_get_diag's
+ * dt_next and fv_get_levels before each step).  If ngauges > 0, m_series
+ * (host, n*ngauges) receives alpha rho at gauges[g] (host, cell indices j*nx
+ * + i) after each step, at [k*ngauges + g].  The state advances; the simulated
+ * time and step count do not.  Second order with Gauss-Legendre x faces on an
+ * undivided grid only.  Allocates device memory for its records; synchronises.
+ * FV_EINVAL for bad arguments, FV_ENONFINITE if a step produced a
+ * non-admissible state. */
+fv_status fv_step_frozen(fv_handle* h, int32_t n, const double* dt, const int32_t* K,
+                         int32_t ngauges, const int64_t* gauges, double* m_series);
+
 /* ---- Batched ensemble of independent domains (configs of uneven sizes,
  * parameter sweeps).  Each domain has its own grid, equation of state,
  * boundaries, free-surface levels, dt (its own CFL condition) and time; one

@@ -118,6 +118,13 @@ struct Model {
   // Roe averages of the two states (Eqs. (b_4^x), (b_4^y)) instead of reading
   // R-vel; off by default, kept so that the tests can show why R-vel is taken
   int roe = 0;
+  // Alternatives to three more readings, off by default, for the experiments
+  // on the weir of Section 5.5: bj_printed = 1: the Barth-Jespersen factor as
+  // printed (no ramp at small face increments, reading R-bj); no_pos = 1: no
+  // first-order fallback for non-admissible reconstructed states (reading
+  // R-pos); aE_mode = 1: alpha^E = 1 in every cell, 2: alpha^E = 1 below the
+  // detected level and eps above it (instead of the cell's own alpha, R-eq).
+  int bj_printed = 0, no_pos = 0, aE_mode = 0;
 };
 
 // Tait equation of state, Eq. (TaitLaw), with gamma = 1.
@@ -555,7 +562,9 @@ Rec reconstruct(const Ctx& C, int i, int j) {
   const Model& M = C.M;
   const size_t n = (size_t)G.nx * G.ny;
   const int K = C.K[i];
-  const double aE = C.Q[3 * n + at(G, i, j)];
+  const double aE = M.aE_mode == 1 ? 1.0
+                    : M.aE_mode == 2 ? (j < K ? 1.0 : M.eps)
+                                     : C.Q[3 * n + at(G, i, j)];
   Rec r;
   double QEc[4];
   QE_centre(C, j, K, aE, QEc);
@@ -614,6 +623,7 @@ Rec reconstruct(const Ctx& C, int i, int j) {
       else if (d < 0.0) phi_bj = std::fmin(1.0, (mn - Qf[v]) / d);
       double ramp = (std::fabs(d) - eta) / eta;
       ramp = ramp < 0.0 ? 0.0 : (ramp > 1.0 ? 1.0 : ramp);
+      if (M.bj_printed) ramp = 1.0;
       const double phi = 1.0 - ramp * (1.0 - phi_bj);
       if (phi < p) p = phi;
     }
@@ -671,7 +681,7 @@ Rec reconstruct(const Ctx& C, int i, int j) {
   bool ok = true;
   for (int k = 0; k < 5; ++k)
     if (!(states[k][0] > 0.0 && states[k][3] > 0.0)) ok = false;
-  if (!ok) {
+  if (!ok && !M.no_pos) {
     for (int v = 0; v < 4; ++v) {
       psi[v] = 0.0;
       r.qW[v] = r.qE[v] = r.qc[v] = QEc[v] + Qf[v];
@@ -1153,7 +1163,10 @@ int orc_run(const int32_t* gi, const double* gd, const double* eos, const int32_
 // 3.2-3.3, reading R-o1; bit 4: x faces by the conservative Osher-Romberg
 // viscosity of Eq. (OR_cons) instead of Gauss-Legendre; bit 5, second order
 // with Gauss-Legendre x faces only: the printed Roe averages in b4x and b4y
-// instead of reading R-vel) recording, for each step, its levels (K_hist, nsteps*nx,
+// instead of reading R-vel; bit 6: the printed Barth-Jespersen factor instead
+// of reading R-bj; bit 7: no first-order fallback of reading R-pos; bits 8-9:
+// alpha^E = 1 (1) or two-layer (2) instead of reading R-eq; bits 5-9 are
+// experiment switches, second order only) recording, for each step, its levels (K_hist, nsteps*nx,
 // nullable), its dt (dt_hist, nullable) and alpha rho at the gauge cells after
 // it (m_hist, nsteps*ngauges, nullable).  With dt_fix and K_fix (both given),
 // step s uses dt_fix[s] and the levels K_fix[s*nx ..] instead of those of its
@@ -1170,8 +1183,11 @@ int orc_run_record(const int32_t* gi, const double* gd, const double* eos, const
   const int order = scheme & 15;
   C.xsolver = (scheme >> 4) & 1;
   C.M.roe = (scheme >> 5) & 1;
-  if ((order != 1 && order != 2) || (scheme >> 6) != 0) return 1;
-  if (C.M.roe && (order != 2 || C.xsolver != 0)) return 1;
+  C.M.bj_printed = (scheme >> 6) & 1;
+  C.M.no_pos = (scheme >> 7) & 1;
+  C.M.aE_mode = (scheme >> 8) & 3;
+  if ((order != 1 && order != 2) || (scheme >> 10) != 0 || C.M.aE_mode == 3) return 1;
+  if ((scheme >> 5) && (order != 2 || C.xsolver != 0 || cap)) return 1;
   const size_t n1 = (size_t)C.G.nx * C.G.ny, n4 = 4 * n1;
   if (cap) {
     if (order != 2) return 1;

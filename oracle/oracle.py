@@ -118,7 +118,8 @@ def run(case, nsteps: int, q=None, cfl: float | None = None):
 
 
 def run_record(case, nsteps: int, gauges, q=None, cfl: float | None = None, dt_fix=None,
-               K_fix=None, order: int = 2, xsolver: int = 0, cap=None, roe: bool = False):
+               K_fix=None, order: int = 2, xsolver: int = 0, cap=None, roe: bool = False,
+               bj_printed: bool = False, no_pos: bool = False, aE_mode: int = 0):
     """Advance ``nsteps`` steps of the scheme of ``order`` (2: Eq. (Scheme);
     1: the first-order scheme of Sections 3.2-3.3) with x faces by
     ``xsolver`` (0: Gauss-Legendre Osher; 1: conservative Osher-Romberg,
@@ -128,7 +129,11 @@ def run_record(case, nsteps: int, gauges, q=None, cfl: float | None = None, dt_f
     of their own.  ``cap`` (ny, nx), second order only: the fluid capacities
     of reading R-h (a partial cell on top of an obstacle; 1 = a whole cell).
     ``roe`` (second order, Gauss-Legendre x faces): the printed sqrt(rho)-
-    weighted Roe averages of Eqs. (b_4^x), (b_4^y) in place of reading R-vel.
+    weighted Roe averages of Eqs. (b_4^x), (b_4^y) in place of reading R-vel;
+    ``bj_printed``: the printed Barth-Jespersen factor (no ramp, reading R-bj);
+    ``no_pos``: no first-order fallback of reading R-pos; ``aE_mode`` 1 / 2:
+    alpha^E = 1 / two-layer (1 below the level, eps above) instead of reading
+    R-eq.  These switches exist for experiments and tests of the readings.
     Returns (q_out, dt (nsteps), K (nsteps, nx), m (nsteps, ngauges))."""
     L = lib()
     gi, gd, eos, sides, solid = _case_args(case)
@@ -150,7 +155,9 @@ def run_record(case, nsteps: int, gauges, q=None, cfl: float | None = None, dt_f
                           _p(qin), _p(qout), int(nsteps), float(case.cfl if cfl is None else cfl),
                           None if dfix is None else _p(dfix),
                           None if kfix is None else _p(kfix, _I32), _p(dts), _p(Ks, _I32),
-                          _p(g, _I64), int(g.size), _p(ms), int(order) | (int(xsolver) << 4) | (int(bool(roe)) << 5),
+                          _p(g, _I64), int(g.size), _p(ms), (int(order) | (int(xsolver) << 4) | (int(bool(roe)) << 5)
+                           | (int(bool(bj_printed)) << 6) | (int(bool(no_pos)) << 7)
+                           | (int(aE_mode) << 8)),
                           None if cp is None else _p(cp))
     if rc == 1:
         raise OracleError("invalid input")

@@ -1325,3 +1325,100 @@ extern "C" fv_status fv_adjoint(fv_handle* h, const fv_adjoint_spec* spec, doubl
   if (h->prec == FV_FP64) return run_adjoint<double, false>(h, spec, dL_dq0, on_device, info, hcell);
   return run_adjoint<float, true>(h, spec, dL_dq0, on_device, info, hcell);
 }
+
+// ------------------------------------------------------------------ frozen map
+// The map whose derivative fv_adjoint returns (reading R-adj): steps of Eq.
+// (Scheme) with each step's dt and levels given instead of its own.
+namespace {
+
+template <typename T, bool DEV>
+fv_status run_frozen(fv_handle* h, int32_t n, const double* dt, const int32_t* K, int32_t ng,
+                     const int64_t* gauges, double* m_series) {
+  using namespace fv;
+  const int nx = h->grid.nx, ny = h->grid.ny;
+  cudaStream_t st = h->stream;
+  DevBuf dK, dg, dm;
+  if (!dK.alloc(sizeof(int32_t) * (size_t)n * nx) ||
+      (ng > 0 && (!dg.alloc(sizeof(int64_t) * ng) || !dm.alloc(sizeof(double) * (size_t)n * ng)))) {
+    set_last_error("fv_step_frozen: device allocation failed");
+    return FV_ENOMEM;
+  }
+  auto fail = [](cudaError_t e) {
+    set_last_error((std::string("fv_step_frozen: ") + cudaGetErrorString(e)).c_str());
+    return FV_ECUDA;
+  };
+  cudaError_t e = cudaMemcpyAsync(dK.p, K, sizeof(int32_t) * (size_t)n * nx,
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && ng > 0)
+    e = cudaMemcpyAsync(dg.p, gauges, sizeof(int64_t) * ng, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return fail(e);
+  const StepParams p = params_of(h, h->cfl);
+  const Tables tb{h->d_rhoE, h->d_rhoE_f};
+  for (int32_t k = 0; k < n && e == cudaSuccess; ++k) {
+    // this step's levels and dt; the state stays stored relative to Kref
+    e = cudaMemcpyAsync(h->d_Kcur, dK.as<int32_t>() + (size_t)k * nx, sizeof(int32_t) * nx,
+                        cudaMemcpyDeviceToDevice, st);
+    adj_set_dt_kernel<<<1, 1, 0, st>>>(h->d_sc, dt[k]);
+    const int a = h->cur, b = 1 - h->cur;
+    launch_replay_step<T, DEV>(p, (const T*)h->d_q[a], (T*)h->d_q[b], h->d_solid, h->d_Kref,
+                               h->d_Kcur, h->d_colsum, h->d_sc, tb, h->tiling, h->strip_h, st);
+    // Kref <- the levels just used (the new state's reference), Kcur, rate and
+    // status from the step's epilogue; time and step count are not advanced
+    launch_finalize(p, h->d_Kref, h->d_Kcur, h->d_colsum, h->d_sc, 0, st);
+    h->cur = b;
+    if (ng > 0)
+      adj_after_step_kernel<T, DEV><<<1, 256, 0, st>>>(
+          nx, ny, (const T*)h->d_q[b], h->d_Kref, h->d_rhoE, dg.as<int64_t>(), ng,
+          dm.as<double>() + (size_t)k * ng, h->d_Kcur, nullptr, h->d_sc, nullptr);
+    if (e == cudaSuccess) e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && ng > 0)
+    e = cudaMemcpyAsync(m_series, dm.p, sizeof(double) * (size_t)n * ng, cudaMemcpyDeviceToHost, st);
+  DevScalars sc;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&sc, h->d_sc, sizeof(sc), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(e);
+  if (sc.status) {
+    set_last_error("fv_step_frozen: a step produced a non-admissible state");
+    return FV_ENONFINITE;
+  }
+  return FV_OK;
+}
+
+}  // namespace
+
+extern "C" fv_status fv_step_frozen(fv_handle* h, int32_t n, const double* dt, const int32_t* K,
+                                    int32_t ngauges, const int64_t* gauges, double* m_series) {
+  using namespace fv;
+  if (!h || n < 0 || (n > 0 && (!dt || !K)) || ngauges < 0 ||
+      (ngauges > 0 && (!gauges || !m_series))) {
+    set_last_error("fv_step_frozen: null argument or negative count");
+    return FV_EINVAL;
+  }
+  if (!h->has_state) {
+    set_last_error("fv_step_frozen: no state (call fv_set_state first)");
+    return FV_EINVAL;
+  }
+  if (h->own_hi > 0 || h->order != 2 || h->xface != FV_XFACE_GL) {
+    set_last_error("fv_step_frozen: second order with Gauss-Legendre x faces, undivided grids only");
+    return FV_EINVAL;
+  }
+  for (size_t k = 0; k < (size_t)n * h->grid.nx; ++k)
+    if (K[k] < 0 || K[k] > h->grid.ny) {
+      set_last_error("fv_step_frozen: levels must lie in [0, ny]");
+      return FV_EINVAL;
+    }
+  for (int32_t k = 0; k < n; ++k)
+    if (!(dt[k] >= 0.0) || !std::isfinite(dt[k])) {
+      set_last_error("fv_step_frozen: dt values must be finite and >= 0");
+      return FV_EINVAL;
+    }
+  for (int g = 0; g < ngauges; ++g)
+    if (gauges[g] < 0 || gauges[g] >= (int64_t)h->ncell) {
+      set_last_error("fv_step_frozen: gauges must be cell indices j*nx + i");
+      return FV_EINVAL;
+    }
+  if (n == 0) return FV_OK;
+  if (h->prec == FV_FP64) return run_frozen<double, false>(h, n, dt, K, ngauges, gauges, m_series);
+  return run_frozen<float, true>(h, n, dt, K, ngauges, gauges, m_series);
+}

@@ -123,8 +123,11 @@ _lib.fv_part_set_rate.argtypes = [_H, C.c_void_p, C.c_int32]
 _lib.fv_part_pack.argtypes = [_H, C.c_int32, C.c_void_p]
 _lib.fv_part_unpack.argtypes = [_H, C.c_int32, C.c_void_p]
 for _f in ("fv_set_partition", "fv_part_halo_bytes", "fv_part_rate", "fv_part_set_rate",
-           "fv_part_pack", "fv_part_unpack"):
+           "fv_part_pack", "fv_part_unpack", "fv_step_frozen"):
     getattr(_lib, _f).restype = C.c_int
+_lib.fv_step_frozen.argtypes = [_H, C.c_int32, _D, C.POINTER(C.c_int32), C.c_int32,
+                                C.POINTER(C.c_int64), _D]
+_lib.fv_step_frozen.restype = C.c_int
 _lib.fv_measure_fma_peak.argtypes = [C.c_int32, C.c_int32, _D, _D]
 _lib.fv_measure_fma_peak.restype = C.c_int
 _lib.fv_set_order.argtypes = [_H, C.c_int32]
@@ -164,7 +167,7 @@ ABI_SYMBOLS = ("fv_create", "fv_set_state", "fv_step", "fv_step_timed", "fv_get_
                "fv_set_strip_height", "fv_tune", "fv_host_height_step", "fv_batch_tune",
                "fv_batch_set_launch", "fv_measure_fma_peak", "fv_set_partition",
                "fv_part_halo_bytes", "fv_part_rate", "fv_part_set_rate", "fv_part_pack",
-               "fv_part_unpack")
+               "fv_part_unpack", "fv_step_frozen")
 
 
 def _check(st):
@@ -334,6 +337,20 @@ def fv_part_pack(h, side: int, buf_dev) -> None:
 
 def fv_part_unpack(h, side: int, buf_dev) -> None:
     _check(_lib.fv_part_unpack(h, int(side), C.c_void_p(_dev_addr(buf_dev))))
+
+
+def fv_step_frozen(h, dt, K, gauges=None):
+    """len(dt) steps with the given dt (n,) and levels K (n, nx) (fv_step_frozen);
+    returns alpha rho at the gauges after each step, (n, ngauges)."""
+    dt = np.ascontiguousarray(dt, dtype=np.float64)
+    K = np.ascontiguousarray(K, dtype=np.int32)
+    n = dt.size
+    g = np.ascontiguousarray([] if gauges is None else gauges, dtype=np.int64)
+    m = np.zeros((max(n, 1), max(g.size, 1)))
+    _check(_lib.fv_step_frozen(h, n, dt.ctypes.data_as(_D), K.ctypes.data_as(C.POINTER(C.c_int32)),
+                               g.size, g.ctypes.data_as(C.POINTER(C.c_int64)) if g.size else None,
+                               m.ctypes.data_as(_D) if g.size else None))
+    return m[:n, :g.size]
 
 
 def fv_measure_fma_peak(kind: int, reps: int = 3):
@@ -506,6 +523,24 @@ class Solver:
                                       gauges, target, grad, checkpoint_every, want_series,
                                       height_id=height_id)
         return grad, dh, info, series
+
+    def record_free_run(self, nsteps: int, cfl: float | None = None):
+        """Advance nsteps one at a time, recording the dt and levels each step
+        used (the values fv_adjoint holds; input of step_frozen)."""
+        cfl = self.case.cfl if cfl is None else cfl
+        dts = np.zeros(nsteps)
+        Ks = np.zeros((nsteps, self.case.nx), dtype=np.int32)
+        fv_step(self.h, 0, cfl)
+        for k in range(nsteps):
+            Ks[k] = self.levels()
+            dts[k] = self.diag().dt_next
+            fv_step(self.h, 1, cfl)
+        return dts, Ks
+
+    def step_frozen(self, dt, K, gauges=None):
+        """Steps with the given dt and levels (fv_step_frozen); returns the
+        gauges' alpha rho after each step."""
+        return fv_step_frozen(self.h, dt, K, gauges)
 
     def diag(self) -> fv_diag:
         return fv_get_diag(self.h)

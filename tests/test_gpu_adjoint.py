@@ -225,3 +225,45 @@ def test_full_grid_gradient_on_conditioned_horizon(fv):
         assert np.all(np.isfinite(g))
         fd = (loss(c.q + h * d, t) - loss(c.q - h * d, t)) / (2 * h)
         assert abs(np.sum(g * d) - fd) <= tol * abs(fd), (prec, np.sum(g * d), fd)
+
+
+def test_frozen_map_matches_oracle_and_its_differences_match_the_adjoint(fv, problem):
+    """fv_step_frozen, the map fv_adjoint differentiates: with the free run's
+    dt and levels (recorded through the C ABI) its gauge record equals the
+    oracle's (<= 1e-10) in FP64, and central differences of its loss along
+    seeded directions equal the adjoint's directional derivatives (the same
+    bound as against the oracle's differences)."""
+    c, gauges, target = problem["case"], problem["gauges"], problem["target"]
+    s = fv.Solver(c, fv.FV_FP64)
+    s.set_state(c.q)
+    dts, Ks = s.record_free_run(NSTEPS, CFL)
+    s.close()
+    assert np.array_equal(Ks, problem["K"])
+    assert np.all(np.abs(dts - problem["dt"]) <= 1e-14 * problem["dt"])
+
+    def loss(q):
+        s = fv.Solver(c, fv.FV_FP64)
+        s.set_state(q)
+        m = s.step_frozen(dts, Ks, gauges)
+        s.close()
+        return float(np.sum(dts * np.sum((m - target) ** 2, axis=1))), m
+
+    l0, m0 = loss(c.q)
+    assert np.max(np.abs(m0 - problem["m"]) / np.abs(problem["m"])) < 1e-10
+    assert abs(l0 - problem["loss"]) <= 1e-9 * problem["loss"]
+    g, _, _ = gpu_grad(fv, problem, fv.FV_FP64)
+    d = cases.c5_directions(c, count=32)[:8]
+    dd = np.array([np.sum(g * dk) for dk in d])
+    fd = np.array([(loss(c.q + H * dk)[0] - loss(c.q - H * dk)[0]) / (2 * H) for dk in d])
+    assert np.all(np.abs(dd - fd) < 1e-5 * np.max(np.abs(fd))), (dd, fd)
+
+
+def test_frozen_map_arguments(fv, problem):
+    c = problem["case"]
+    s = fv.Solver(c, fv.FV_FP64)
+    s.set_state(c.q)
+    with pytest.raises(fv.FvError):
+        s.step_frozen(np.array([1e-4]), np.full((1, c.nx), c.ny + 1))    # level above the grid
+    with pytest.raises(fv.FvError):
+        s.step_frozen(np.array([np.nan]), np.zeros((1, c.nx)))             # dt not finite
+    s.close()
