@@ -420,31 +420,37 @@ def measure_path(fv, case, prec, steps, warmup, stream_sync, barrier, device_ind
             "clocks": clk.summary(), "strip_rows": rows}
 
 
-def measure_batch(fv, cases_mod, steps, warmup, stream_sync, barrier):
+def measure_batch(fv, cases_mod, steps, warmup, stream_sync, barrier, cfl=0.45):
     """Config 4: 256 dam breaks over a one-cell weir, sizes 64..1024 per side
-    (seed 4960), FP32 deviation form, every domain with its own dt; n ensemble
-    steps replayed from one CUDA graph."""
+    (seed 4960), FP32 deviation form, every domain with its own dt; the
+    configured 500 ensemble steps from the initial states replayed from one
+    CUDA graph (captured, with the launch form fv_batch_tune picks, on a first
+    run of the same steps, then the states reset).  CFL 0.45: at 0.9 the
+    wall-row instability of the unsplit step (finding F1) turns some domains
+    non-admissible within 400-1000 steps (domain 44 by step 400)."""
     doms = cases_mod.weir_domains()
     b = fv.Batch(doms, fv.FV_FP32_DEV)
     for k, c in enumerate(doms):
         b.set_state(k, c.q)
-    b.step(warmup, 0.9)
-    rows, order, pers = b.tune(0.9)
-    b.step_timed(steps, 0.9)   # capture the graph for this step count once
+    b.step(warmup, cfl)
+    rows, order, pers = b.tune(cfl)
+    b.step_timed(steps, cfl)   # capture the graph for this step count once
+    for k, c in enumerate(doms):
+        b.set_state(k, c.q)
     stream_sync()
     barrier()
-    total_ms = b.step_timed(steps, 0.9)
+    total_ms = b.step_timed(steps, cfl)
     barrier()
     cells = sum(c.nx * c.ny for c in doms)
     bad = sum(b.diag(k).status != 0 for k in range(len(doms)))
     t = [b.diag(k).t for k in range(len(doms))]
     b.close()
     return {"value": cells * steps / (total_ms * 1e-3) / 1e6, "unit": UNIT,
-            "ms_per_step": total_ms / steps, "steps": steps, "domains": len(doms), "cells": cells,
-            "dtype": "f32", "launch": ("persistent grid" if pers else "one CTA per strip") +
-                                      " of the strip kernel + per-domain finalize per step, "
-                                      "CUDA graph of all steps (form, strip height and order "
-                                      "from fv_batch_tune)",
+            "ms_per_step": total_ms / steps, "steps": steps, "cfl": cfl, "domains": len(doms),
+            "cells": cells, "dtype": "f32",
+            "launch": ("persistent grid" if pers else "one CTA per strip") +
+                      " of the strip kernel + per-domain finalize per step, CUDA graph of all "
+                      "steps (form, strip height and order from fv_batch_tune)",
             "strip_rows": rows, "work_order": "longest strips first" if order else "by domain",
             "bad_domains": int(bad), "t_min": min(t), "t_max": max(t)}
 

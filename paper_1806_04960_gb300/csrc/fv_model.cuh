@@ -32,6 +32,41 @@ __host__ __device__ __forceinline__ T tabs(T x) {
   return x < T(0) ? -x : x;
 }
 
+// FP64 device code: sign, magnitude and comparisons with zero on the integer
+// pipe (the FP64 pipe runs at 1/64 of the FP32 rate on this part).  A double's
+// bits, read as a signed 64-bit integer, are > 0 exactly for the values > 0,
+// and < 0 for the values < 0 and -0 (NaN aside: non-admissible anyway).
+#ifdef __CUDA_ARCH__
+template <>
+__device__ __forceinline__ double sgn<double>(double x) {
+  const long long b = __double_as_longlong(x);
+  return b > 0 ? 1.0 : (b < 0 && (b << 1) != 0 ? -1.0 : 0.0);
+}
+template <>
+__device__ __forceinline__ double tabs<double>(double x) {
+  return __longlong_as_double(__double_as_longlong(x) & 0x7fffffffffffffffLL);
+}
+#endif
+// x > 0, and |x| > y for y >= 0 (the same integer reading in FP64 device code).
+template <typename T>
+__host__ __device__ __forceinline__ bool gtz(T x) {
+  return x > T(0);
+}
+template <typename T>
+__host__ __device__ __forceinline__ bool abs_gt(T x, T y) {
+  return tabs(x) > y;
+}
+#ifdef __CUDA_ARCH__
+template <>
+__device__ __forceinline__ bool gtz<double>(double x) {
+  return __double_as_longlong(x) > 0;
+}
+template <>
+__device__ __forceinline__ bool abs_gt<double>(double x, double y) {
+  return (__double_as_longlong(x) & 0x7fffffffffffffffLL) > __double_as_longlong(y);
+}
+#endif
+
 // A face state: full conserved state q plus the exact jump to the other side
 // is formed by the caller.  Velocities from 1/m.
 template <typename T>
@@ -39,11 +74,31 @@ struct Vel {
   T u, v;
 };
 
-// Reciprocal: IEEE in double; the fast hardware reciprocal in float on the
-// device (relative error ~1e-7, inside the float path's stated tolerance).
+// Reciprocal: IEEE division on the host; on the device the refined hardware
+// approximation below in double and the fast hardware reciprocal in float
+// (relative error ~1e-7, inside the float path's stated tolerance).
 template <typename T>
 __host__ __device__ __forceinline__ T rcp(T x) {
   return T(1) / x;
+}
+// Double on the device: the hardware's approximate reciprocal (rcp.approx.f64)
+// refined by two steps of Newton's iteration for 1/x, r <- r + r (1 - x r)
+// (each squares the relative error; the last one rounds once through the
+// fused multiply-add), within one ulp of 1/x (tests/test_gpu_parity.py checks
+// it against CUDA's division); fewer FP64-pipe instructions than IEEE
+// division, whose pipe bounds the FP64 step.
+template <>
+__host__ __device__ __forceinline__ double rcp<double>(double x) {
+#ifdef __CUDA_ARCH__
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+#else
+  return 1.0 / x;
+#endif
 }
 template <>
 __host__ __device__ __forceinline__ float rcp<float>(float x) {
@@ -354,12 +409,13 @@ __host__ __device__ __forceinline__ T recon_core(const T Qf[4], T fW[4], T fE[4]
       // faces at -h/2 and +h/2 see increments -d and +d
       const T d = dir == 0 ? R.half_dx * gx[v] : R.half_dy * gy[v];
       const T ad = tabs(d);
-      if (ad > R.eta[v]) {
+      if (abs_gt(d, R.eta[v])) {
         const T inv = rcp(d);
         const T ramp = fmin(T(1), (ad - R.eta[v]) * R.inv_eta[v]);
         // face with increment +d: bound up if d > 0, dn if d < 0; face with -d: the other
-        const T phi_p = fmin(T(1), (d > T(0) ? up : dn) * inv);
-        const T phi_m = fmin(T(1), -(d > T(0) ? dn : up) * inv);
+        const bool dpos = gtz(d);
+        const T phi_p = fmin(T(1), (dpos ? up : dn) * inv);
+        const T phi_m = fmin(T(1), -(dpos ? dn : up) * inv);
         psi = fmin(psi, T(1) - ramp * (T(1) - phi_p));
         psi = fmin(psi, T(1) - ramp * (T(1) - phi_m));
       }
@@ -401,10 +457,9 @@ __host__ __device__ __forceinline__ T recon_core(const T Qf[4], T fW[4], T fE[4]
     fS[c] = base[c] - syh;
     fN[c] = base[c] + syh;
   }
-  const bool ok = (mEc + fW[0] > T(0)) && (aE + fW[3] > T(0)) && (mEc + fE[0] > T(0)) &&
-                  (aE + fE[3] > T(0)) && (mES + fS[0] > T(0)) && (aE + fS[3] > T(0)) &&
-                  (mEN + fN[0] > T(0)) && (aE + fN[3] > T(0)) && (mEc + base[0] > T(0)) &&
-                  (aE + base[3] > T(0));
+  const bool ok = gtz(mEc + fW[0]) && gtz(aE + fW[3]) && gtz(mEc + fE[0]) && gtz(aE + fE[3]) &&
+                  gtz(mES + fS[0]) && gtz(aE + fS[3]) && gtz(mEN + fN[0]) && gtz(aE + fN[3]) &&
+                  gtz(mEc + base[0]) && gtz(aE + base[3]);
   if (!ok) {
     psi = T(0);
 #pragma unroll

@@ -14,6 +14,7 @@
 
 #include "fv.h"
 #include "fv_kernels.cuh"
+#include "fv_model.cuh"
 
 namespace {
 
@@ -123,5 +124,32 @@ extern "C" fv_status fv_measure_fma_peak(int32_t kind, int32_t reps, double* tfl
   const double fmas = (double)blocks * kThreads * iters * kUnroll * kChains * lanes;
   *tflops = 2.0 * fmas / (best * 1e-3) / 1e12;
   if (best_ms) *best_ms = best;
+  return FV_OK;
+}
+
+namespace {
+__global__ void rcp_probe_kernel(const double* __restrict__ x, double* __restrict__ out,
+                                 long long n) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x)
+    out[k] = fv::rcp(x[k]);
+}
+}  // namespace
+
+extern "C" fv_status fv_device_rcp(const double* x_dev, double* out_dev, int64_t n,
+                                   void* cuda_stream) {
+  if (!x_dev || !out_dev || n < 0) {
+    fv::set_last_error("fv_device_rcp: null argument or n < 0");
+    return FV_EINVAL;
+  }
+  if (n == 0) return FV_OK;
+  const long long blocks = (n + 255) / 256;
+  rcp_probe_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0,
+                     (cudaStream_t)cuda_stream>>>(x_dev, out_dev, n);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    fv::set_last_error(cuda_msg("fv_device_rcp", e).c_str());
+    return FV_ECUDA;
+  }
   return FV_OK;
 }

@@ -51,6 +51,26 @@ template <typename T>
 __device__ __forceinline__ T min3(T a, T b, T c) {
   return fmin(fmin(a, b), c);
 }
+// In FP64 the bounds are formed on the integer pipe: a double's bits, with
+// the magnitude bits of a negative value inverted, order as a signed 64-bit
+// integer exactly as the values do (-0 before +0); the largest / smallest of
+// three is then selected by two integer comparisons.
+__device__ __forceinline__ long long ord64(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+template <>
+__device__ __forceinline__ double max3<double>(double a, double b, double c) {
+  const long long ia = ord64(a), ib = ord64(b), ic = ord64(c);
+  const double ab = ia >= ib ? a : b;
+  return max(ia, ib) >= ic ? ab : c;
+}
+template <>
+__device__ __forceinline__ double min3<double>(double a, double b, double c) {
+  const long long ia = ord64(a), ib = ord64(b), ic = ord64(c);
+  const double ab = ia <= ib ? a : b;
+  return min(ia, ib) <= ic ? ab : c;
+}
 template <>
 __device__ __forceinline__ float max3<float>(float a, float b, float c) {
   float d;

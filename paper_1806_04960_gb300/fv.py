@@ -123,11 +123,13 @@ _lib.fv_part_set_rate.argtypes = [_H, C.c_void_p, C.c_int32]
 _lib.fv_part_pack.argtypes = [_H, C.c_int32, C.c_void_p]
 _lib.fv_part_unpack.argtypes = [_H, C.c_int32, C.c_void_p]
 for _f in ("fv_set_partition", "fv_part_halo_bytes", "fv_part_rate", "fv_part_set_rate",
-           "fv_part_pack", "fv_part_unpack", "fv_step_frozen"):
+           "fv_part_pack", "fv_part_unpack", "fv_step_frozen", "fv_device_rcp"):
     getattr(_lib, _f).restype = C.c_int
 _lib.fv_step_frozen.argtypes = [_H, C.c_int32, _D, C.POINTER(C.c_int32), C.c_int32,
                                 C.POINTER(C.c_int64), _D]
 _lib.fv_step_frozen.restype = C.c_int
+_lib.fv_device_rcp.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]
+_lib.fv_device_rcp.restype = C.c_int
 _lib.fv_measure_fma_peak.argtypes = [C.c_int32, C.c_int32, _D, _D]
 _lib.fv_measure_fma_peak.restype = C.c_int
 _lib.fv_set_order.argtypes = [_H, C.c_int32]
@@ -167,7 +169,7 @@ ABI_SYMBOLS = ("fv_create", "fv_set_state", "fv_step", "fv_step_timed", "fv_get_
                "fv_set_strip_height", "fv_tune", "fv_host_height_step", "fv_batch_tune",
                "fv_batch_set_launch", "fv_measure_fma_peak", "fv_set_partition",
                "fv_part_halo_bytes", "fv_part_rate", "fv_part_set_rate", "fv_part_pack",
-               "fv_part_unpack", "fv_step_frozen")
+               "fv_part_unpack", "fv_step_frozen", "fv_device_rcp")
 
 
 def _check(st):
@@ -351,6 +353,12 @@ def fv_step_frozen(h, dt, K, gauges=None):
                                g.size, g.ctypes.data_as(C.POINTER(C.c_int64)) if g.size else None,
                                m.ctypes.data_as(_D) if g.size else None))
     return m[:n, :g.size]
+
+
+def fv_device_rcp(x_dev, out_dev, stream: int = 0) -> None:
+    """The FP64 device reciprocal at the doubles of x_dev (fv_device_rcp)."""
+    _check(_lib.fv_device_rcp(C.c_void_p(_dev_addr(x_dev)), C.c_void_p(_dev_addr(out_dev)),
+                              int(x_dev.numel()), C.c_void_p(stream)))
 
 
 def fv_measure_fma_peak(kind: int, reps: int = 3):
