@@ -58,6 +58,9 @@ def parse():
                          "paper's dam break against a wall (1000x500, to t = 1) and its "
                          "sharp-crested weir (800x250, to t = 0.18)")
     ap.add_argument("--adjoint-steps", type=int, default=2000)
+    ap.add_argument("--grid", type=str, default="4096x2048",
+                    help="NXxNY of the dam-break workload for --only runs (profiling a smaller "
+                         "case of the same kernel); the benchmark line itself is 4096x2048")
     ap.add_argument("--strip-rows", type=int, default=0,
                     help="strip height of the step kernel; 0 (default): chosen by fv_tune before "
                          "the timed region (profiling runs fix it so that the captured launch is "
@@ -520,6 +523,49 @@ def measure_adjoint(fv, cases_mod, prec, nsteps, stream_sync):
             "height_cells": int((hid >= 0).sum())}
 
 
+def conditioned_gradient(fv, cases_mod, nsteps=400, ndirs=32, h=1e-11):
+    """The gradient on a horizon where the map is well conditioned: 400 steps of
+    the 512 x 256 dam break (CFL 0.45) from a generic state (cases.generic: all
+    four fields perturbed by 1e-3, so that no stencil extrema tie exactly), 16
+    gauges, target = the gauges' initial alpha rho + 500 held constant.  The
+    FP64 and FP32 adjoints' directional derivatives along the 32 seeded
+    directions (cases.c5_directions) against central differences (relative
+    step 1e-11) of the FP64 frozen-branch map the adjoint differentiates
+    (fv_step_frozen with the free run's dt and levels), relative to the
+    largest difference."""
+    import numpy as np
+    c = cases_mod.generic(cases_mod.c5(512, 256), 7)
+    g = cases_mod.c5_gauges(c)
+    target = np.repeat(c.q[0].ravel()[g][None, :] + 500.0, nsteps, axis=0)
+    s = fv.Solver(c, fv.FV_FP64)
+    s.set_state(c.q)
+    dts, Ks = s.record_free_run(nsteps, c.cfl)
+
+    def loss(q):
+        s.set_state(q)
+        m = s.step_frozen(dts, Ks, g)
+        return float(np.sum(dts * np.sum((m - target) ** 2, axis=1)))
+
+    t0 = time.perf_counter()
+    dirs = cases_mod.c5_directions(c, count=ndirs)
+    fd = np.array([(loss(c.q + h * d) - loss(c.q - h * d)) / (2 * h) for d in dirs])
+    fd_s = time.perf_counter() - t0
+    s.close()
+    out = {"workload": "adjoint_dambreak_512x256_generic", "steps": nsteps, "cfl": c.cfl,
+           "directions": ndirs, "fd_step_rel": h, "fd_seconds": fd_s,
+           "reference": "central differences of the FP64 frozen-branch map (fv_step_frozen)"}
+    for name, prec in (("f64", fv.FV_FP64), ("f32", fv.FV_FP32_DEV)):
+        s = fv.Solver(c, prec)
+        s.set_state(c.q)
+        grad, info, _ = s.adjoint(nsteps, g, target, cfl=c.cfl)
+        s.close()
+        dd = np.array([float(np.sum(grad * d)) for d in dirs])
+        err = np.abs(dd - fd) / np.max(np.abs(fd))
+        out[name] = {"max_rel_err": float(err.max()), "median_rel_err": float(np.median(err)),
+                     "loss": info.loss, "finite": bool(np.isfinite(grad).all())}
+    return out
+
+
 def adjoint_block(fv, cases_mod, na, stream_sync):
     return {"workload": "adjoint_dambreak_512x256", "steps": na, "cfl": 0.45, "gauges": 16,
             "checkpoint_every": int(math.ceil(math.sqrt(na))),
@@ -527,7 +573,8 @@ def adjoint_block(fv, cases_mod, na, stream_sync):
             "f64": measure_adjoint(fv, cases_mod, fv.FV_FP64, na, stream_sync),
             "note": "timing of the configured horizon; beyond about step 600 the bed toe of the "
                     "wave amplifies perturbations, so gradient values there exceed 1e25 (float: "
-                    "overflow); parity is tested on 80-400 steps"}
+                    "overflow); the checked gradient is under conditioned",
+            "conditioned": conditioned_gradient(fv, cases_mod)}
 
 
 def run_adjoint(args):
@@ -718,7 +765,10 @@ def run_ours(args):
     build.build()
     from paper_1806_04960_gb300 import cases, fv
 
-    case = cases.c2()
+    nx, ny = (int(x) for x in args.grid.lower().split("x"))
+    if (nx, ny) != (4096, 2048) and not args.only:
+        raise SystemExit("--grid applies to --only runs (profiling); the benchmark is 4096x2048")
+    case = cases.c2(nx, ny)
     steps, warmup = max(1, args.steps), max(3, args.warmup)
     ops = fv.fv_host_cell_ops()
     pk = measure_peaks(fv, local)
@@ -739,7 +789,7 @@ def run_ours(args):
                             "steps": r["steps"], "warmup": warmup, "ms_per_step": r["ms_per_step"],
                             "kernel_ms_per_step": r["kernel_ms_per_step"], "dtype": args.only,
                             "roofline": r["roofline"], "clocks": r["clocks"], "status": r["status"],
-                            "peaks": pk, "config": {"workload": WORKLOAD}}), flush=True)
+                            "peaks": pk, "config": {"workload": case.name}}), flush=True)
         return
 
     e2e = e2e_step = None

@@ -374,7 +374,9 @@ def test_drop_history_matches_the_oracle(fv):
     (linear interpolation of its history).  The gas next to the receding
     liquid amplifies rounding differences (finding F2), and the fastest gas
     cells set dt, so the runs reach a given step at times up to ~10 % apart;
-    the interface itself, and so a(t) and b(t), agree far closer."""
+    the interface itself, and so a(t) and b(t), agree far closer (measured at
+    equal t: FP64 a 1.8e-4, b 9.4e-5; FP32 a 2.8e-4, b 4.0e-5; equal steps
+    fall 10.6 % (FP64) and 1.0 % (FP32) apart in time)."""
     from oracle_refs import read_golden
     from test_oracle_pins import drop_axes
     ref = np.array([[float(x) for x in r] for r in read_golden("drop_history_oracle_1024.txt")])
@@ -399,7 +401,7 @@ def test_drop_history_matches_the_oracle(fv):
         worst[name] = (et, ea, eb)
     print("drop history vs oracle (t at equal steps; a, b at equal t):", worst)
     for name in worst:
-        assert worst[name][0] <= 0.2 and max(worst[name][1:]) <= 2e-3, worst
+        assert worst[name][0] <= 0.2 and max(worst[name][1:]) <= 1e-3, worst
 
 
 @pytest.mark.parametrize("prec", [0, 1])
