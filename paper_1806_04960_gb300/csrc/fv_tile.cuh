@@ -247,18 +247,49 @@ __device__ __forceinline__ void recon_cell(const V4<T>* wS, const V4<T>* wC, con
     }
   };
   T fW[4], fE[4], fSo[4], fNo[4];
-  if (!nbf(-1, 0, fW)) ghost(-1, 0, 1, sd.W, fW);
-  if (!nbf(1, 0, fE)) ghost(1, 0, 1, sd.E, fE);
-  if (!nbf(0, -1, fSo)) ghost(0, -1, 2, sd.S, fSo);
-  if (!nbf(0, 1, fNo)) ghost(0, 1, 2, sd.N, fNo);
-  // limiter bounds over the 3 x 3 stencil; a diagonal neighbour that is not
-  // fluid contributes the cell's own fluctuation, already among the bounds
-  T fd[4][4];
+  T fd[4][4];  // diagonal neighbours SW, SE, NW, NE
+  // In deviation form most cells have a fluid 3 x 3 stencil whose three
+  // columns share one level: every neighbour then takes the one formula of nbf
+  // below, evaluated without the per-neighbour tests (an issue-bound FP32
+  // kernel gains; the FP64 kernel is bound by its FP64 pipe and does not).
+  const bool all_fluid = (fS[wi - 1] | fS[wi] | fS[wi + 1] | fC[wi - 1] | fC[wi + 1] |
+                          fN[wi - 1] | fN[wi] | fN[wi + 1]) == F_FLUID;
+  const bool one_level = Kw[wi - 1] == K && Kw[wi + 1] == K;
+  if (DEV && all_fluid && one_level) {
+    const T rnS = rE(2 * (gj - 1 - K) + 1), rnN = rE(2 * (gj + 1 - K) + 1);
+    auto fl = [&](const V4<T>& wn, T rn, T out[4]) {
+      const T an = wn.w;
+      if (DEV) {
+        const T mshift = (an - aE) * rn;
+        out[0] = wn.x + mshift;
+      } else {
+        out[0] = wn.x - aE * rn;
+      }
+      out[1] = wn.y;
+      out[2] = wn.z;
+      out[3] = an - aE;
+    };
+    fl(wC[wi - 1], rEc, fW);
+    fl(wC[wi + 1], rEc, fE);
+    fl(wS[wi], rnS, fSo);
+    fl(wN[wi], rnN, fNo);
+    fl(wS[wi - 1], rnS, fd[0]);
+    fl(wS[wi + 1], rnS, fd[1]);
+    fl(wN[wi - 1], rnN, fd[2]);
+    fl(wN[wi + 1], rnN, fd[3]);
+  } else {
+    if (!nbf(-1, 0, fW)) ghost(-1, 0, 1, sd.W, fW);
+    if (!nbf(1, 0, fE)) ghost(1, 0, 1, sd.E, fE);
+    if (!nbf(0, -1, fSo)) ghost(0, -1, 2, sd.S, fSo);
+    if (!nbf(0, 1, fNo)) ghost(0, 1, 2, sd.N, fNo);
+    // limiter bounds over the 3 x 3 stencil; a diagonal neighbour that is not
+    // fluid contributes the cell's own fluctuation, already among the bounds
 #pragma unroll
-  for (int d = 0; d < 4; ++d) {
-    if (!nbf((d & 1) ? 1 : -1, (d & 2) ? 1 : -1, fd[d])) {
+    for (int d = 0; d < 4; ++d) {
+      if (!nbf((d & 1) ? 1 : -1, (d & 2) ? 1 : -1, fd[d])) {
 #pragma unroll
-      for (int v = 0; v < 4; ++v) fd[d][v] = Qf[v];
+        for (int v = 0; v < 4; ++v) fd[d][v] = Qf[v];
+      }
     }
   }
   T mx[4], mn[4];
