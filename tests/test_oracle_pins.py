@@ -455,17 +455,19 @@ def test_drop_semi_axis_follows_exact_solution():
     assert abs(a - a_ode) <= 0.01 * a_ode, (a, a_ode)
 
 
-def test_stored_oracle_drop_history_reaches_the_paper_point():
-    """Section 5.2: the FP64 oracle's drop at 1024^2 on [-2,2]^2 over 2000 steps
-    (t = 2.2e-3; written by tests/golden/make_drop_history.py, which calls only
-    the oracle) passes the paper's printed b(0.0008) = 1.083 within 0.2 % and
-    follows the exact solution within 0.3 % in both semi-axes at every sample
+@pytest.mark.parametrize("n,t_end", [(1024, 2.2e-3), (2048, 1.1e-3)])
+def test_stored_oracle_drop_history_reaches_the_paper_point(n, t_end):
+    """Section 5.2: the FP64 oracle's drop on [-2,2]^2 over 2000 steps (at
+    1024^2 to t = 2.2e-3, at the benchmark's 2048^2 to t = 1.1e-3; written by
+    tests/golden/make_drop_history.py, which calls only the oracle) passes the
+    paper's printed b(0.0008) = 1.083 within 0.2 % (1.0823 in both) and follows
+    the exact solution within 0.3 % in both semi-axes at every sample
     (measured at most 0.14 %)."""
-    rows = [r for r in read_golden("drop_history_oracle_1024.txt")]
+    rows = [r for r in read_golden(f"drop_history_oracle_{n}.txt")]
     t = np.array([float(r[1]) for r in rows])
     a = np.array([float(r[2]) for r in rows])
     b = np.array([float(r[3]) for r in rows])
-    assert len(rows) == 20 and int(rows[-1][0]) == 2000 and t[-1] > 2e-3
+    assert len(rows) == 20 and int(rows[-1][0]) == 2000 and t[-1] > t_end
     paper = {float(r[0]): float(r[1]) for r in read_golden("drop_semi_axis.txt")}
     assert abs(np.interp(0.0008, t, b) - paper[0.0008]) <= 0.002 * paper[0.0008]
     for tt, aa, bb in zip(t, a, b):
