@@ -697,3 +697,23 @@ def test_printed_roe_average_breaks_the_dam_break():
         assert q2[3][fl].max() > 1.01
         with pytest.raises(O.OracleError):
             O.run_record(c, 6, [0], cfl=cfl, roe=True)
+
+
+def test_weir_readings_record():
+    """Section 5.5, finding F5: the oracle's record of the sharp-crested weir
+    with each alternative reading (tests/golden/weir_readings.py).  At the
+    paper's 800 x 250 every variant turns non-admissible before t = 0.25 (the
+    paper reaches t = 1); only the printed Barth-Jespersen factor (no ramp,
+    reading R-bj's alternative) moves the failure by more than 1 %."""
+    rows = read_golden("weir_readings.txt")
+    rec = {(int(r[0]), r[2]): (float(r[3]), int(r[5])) for r in rows}
+    variants = ("default", "bj_printed", "no_pos", "bj_printed+no_pos")
+    for v in variants:
+        t, failed = rec[(800, v)]
+        assert failed == 1 and t < 0.25, (v, t)
+    t0 = rec[(800, "default")][0]
+    assert 0.2 < t0 < 0.22
+    assert abs(rec[(800, "no_pos")][0] - t0) < 0.01 * t0
+    assert rec[(800, "bj_printed")][0] > 1.05 * t0
+    # at 400 x 125 the default fails at t = 0.375, alpha^E = 1 already at t = 0.085
+    assert rec[(400, "default")][1] == 1 and rec[(400, "aE_one")][0] < 0.1
