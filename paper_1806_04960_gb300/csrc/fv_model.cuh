@@ -56,6 +56,10 @@ template <typename T>
 __host__ __device__ __forceinline__ bool abs_gt(T x, T y) {
   return tabs(x) > y;
 }
+template <typename T>
+__host__ __device__ __forceinline__ bool abs_lt(T x, T y) {
+  return tabs(x) < y;
+}
 #ifdef __CUDA_ARCH__
 template <>
 __device__ __forceinline__ bool gtz<double>(double x) {
@@ -64,6 +68,10 @@ __device__ __forceinline__ bool gtz<double>(double x) {
 template <>
 __device__ __forceinline__ bool abs_gt<double>(double x, double y) {
   return (__double_as_longlong(x) & 0x7fffffffffffffffLL) > __double_as_longlong(y);
+}
+template <>
+__device__ __forceinline__ bool abs_lt<double>(double x, double y) {
+  return (__double_as_longlong(x) & 0x7fffffffffffffffLL) < __double_as_longlong(y);
 }
 #endif
 
@@ -270,11 +278,24 @@ __host__ __device__ __forceinline__ void xface_or(const T qm[4], const T qp[4], 
 template <typename T>
 __host__ __device__ __forceinline__ void sign_A2(T u, T v, const T r[4], const Phys<T>& P,
                                                  T out[4]) {
+  const T s3 = sgn(v);
+  if (abs_lt(v, P.c)) {
+    // |v| < c: the acoustic eigenvalues v - c < 0 < v + c, so the two acoustic
+    // terms combine to (w5 - w1) = (r2 - v r0) / c and (w5 + w1) = r0 - rho0 r3
+    const T D = r[0] - P.rho0 * r[3];
+    const T Pk = (r[2] - v * r[0]) * P.inv_c;
+    const T o0 = Pk + s3 * P.rho0 * r[3];
+    out[0] = o0;
+    out[1] = u * Pk + s3 * (r[1] - u * D);
+    out[2] = v * o0 + P.c * D;
+    out[3] = s3 * r[3];
+    return;
+  }
   const T vc = v * P.inv_c;
   const T w1 = T(0.5) * ((T(1) + vc) * r[0] - r[2] * P.inv_c - P.rho0 * r[3]);
   const T w5 = T(0.5) * ((T(1) - vc) * r[0] + r[2] * P.inv_c - P.rho0 * r[3]);
   const T w2 = r[1] - u * (r[0] - P.rho0 * r[3]);
-  const T s1 = sgn(v - P.c), s5 = sgn(v + P.c), s3 = sgn(v);
+  const T s1 = sgn(v - P.c), s5 = sgn(v + P.c);
   const T a1 = s1 * w1, a5 = s5 * w5;
   const T Pk = a1 + a5;
   const T srho = s3 * P.rho0 * r[3];
@@ -605,27 +626,29 @@ __host__ __device__ __forceinline__ void xface_f2(const float qm[4], const float
   }
 }
 
-// sign_A2 on float2 lanes (closed form of sign_A2).
+// sign_A2 on float2 lanes (closed form of sign_A2): the subsonic form for
+// both lanes, and the general one, selected lane by lane, when a lane is not
+// subsonic (rare; the per-lane formulas are those of sign_A2).
 __host__ __device__ __forceinline__ void sign_A2_f2(float2 u, float2 v, const float2 r[4],
                                                     const Phys<float>& P, float2 out[4]) {
-  const float2 vc = mul2(v, bc2(P.inv_c));
   const float2 rr = mul2(bc2(P.rho0), r[3]);
-  const float2 half = bc2(0.5f);
-  // w1 = ((1 + vc) r0 - r2 / c - rho0 r3) / 2, w5 = ((1 - vc) r0 + r2 / c - rho0 r3) / 2
-  const float2 r2c = mul2(r[2], bc2(P.inv_c));
-  const float2 vr0 = mul2(vc, r[0]);
-  const float2 base = sub2(r[0], rr);
-  const float2 w1 = mul2(half, add2(sub2(base, r2c), vr0));
-  const float2 w5 = mul2(half, sub2(add2(base, r2c), vr0));
-  const float2 w2 = fma2(make_float2(-u.x, -u.y), base, r[1]);
-  const float2 s1 = sgn2(add2(v, bc2(-P.c))), s5 = sgn2(add2(v, bc2(P.c))), s3 = sgn2(v);
-  const float2 a1 = mul2(s1, w1), a5 = mul2(s5, w5);
-  const float2 Pk = add2(a1, a5);
-  const float2 srho = mul2(s3, rr);
-  out[0] = add2(Pk, srho);
-  out[1] = fma2(u, Pk, mul2(s3, w2));
-  out[2] = fma2(v, add2(Pk, srho), mul2(bc2(P.c), sub2(a5, a1)));
+  const float2 s3 = sgn2(v);
+  const float2 D = sub2(r[0], rr);
+  const float2 Pk = mul2(fma2(make_float2(-v.x, -v.y), r[0], r[2]), bc2(P.inv_c));
+  const float2 o0 = fma2(s3, rr, Pk);
+  out[0] = o0;
+  out[1] = fma2(u, Pk, mul2(s3, fma2(make_float2(-u.x, -u.y), D, r[1])));
+  out[2] = fma2(v, o0, mul2(bc2(P.c), D));
   out[3] = mul2(s3, r[3]);
+  const bool sx = tabs(v.x) < P.c, sy = tabs(v.y) < P.c;
+  if (!(sx && sy)) {
+    const float rx[4] = {r[0].x, r[1].x, r[2].x, r[3].x}, ry[4] = {r[0].y, r[1].y, r[2].y, r[3].y};
+    float ox[4], oy[4];
+    sign_A2(u.x, v.x, rx, P, ox);
+    sign_A2(u.y, v.y, ry, P, oy);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) out[c] = make_float2(ox[c], oy[c]);
+  }
 }
 
 // yface in FP32: the two half-segment terms of the Osher-Romberg sum (nodes
