@@ -149,23 +149,34 @@ __host__ __device__ __forceinline__ void xface_scalar(const T qm[4], const T qp[
   const T w_gl[3] = {T(5.0 / 18.0), T(8.0 / 18.0), T(5.0 / 18.0)};
   T V0 = 0, V1 = 0, V2 = 0, V3 = 0, ubar = 0;
   const T dr = dq[0] - P.rho0 * dq[3];  // d1 - rho0 d4
+  const T cdr = P.c * dr, B = P.rho0 * dq[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const T m = qm[0] + s_gl[k] * dq[0];
     const T mu = qm[1] + s_gl[k] * dq[1];
     const T mv = qm[2] + s_gl[k] * dq[2];
     const Vel<T> w = velocity(m, mu, mv);
-    const T uc = w.u * P.inv_c;
-    // R1^-1 dq (rows 1, 2, 5; row 3 is d4 / c2)
-    const T w1 = T(0.5) * ((T(1) + uc) * dq[0] - dq[1] * P.inv_c - P.rho0 * dq[3]);
-    const T w5 = T(0.5) * ((T(1) - uc) * dq[0] + dq[1] * P.inv_c - P.rho0 * dq[3]);
+    const T la = tabs(w.u);
     const T w2 = dq[2] - w.v * dr;
-    const T l1 = tabs(w.u - P.c), l5 = tabs(w.u + P.c), la = tabs(w.u);
-    const T a1 = l1 * w1, a5 = l5 * w5;
-    const T Pk = a1 + a5;
-    const T r0 = Pk + la * P.rho0 * dq[3];
+    T Pk, amd;  // a1 + a5 and a5 - a1
+    if (abs_lt(w.u, P.c)) {
+      // |u| < c: |u - c| = c - u, |u + c| = c + u, so the two acoustic terms
+      // combine to c dr + u e / c and e + u dr, e = d2 - u d1
+      const T e = dq[1] - w.u * dq[0];
+      Pk = cdr + (w.u * P.inv_c) * e;
+      amd = e + w.u * dr;
+    } else {
+      const T uc = w.u * P.inv_c;
+      // R1^-1 dq (rows 1, 2, 5; row 3 is d4 / c2)
+      const T w1 = T(0.5) * ((T(1) + uc) * dq[0] - dq[1] * P.inv_c - B);
+      const T w5 = T(0.5) * ((T(1) - uc) * dq[0] + dq[1] * P.inv_c - B);
+      const T a1 = tabs(w.u - P.c) * w1, a5 = tabs(w.u + P.c) * w5;
+      Pk = a1 + a5;
+      amd = a5 - a1;
+    }
+    const T r0 = Pk + la * B;
     V0 += w_gl[k] * r0;
-    V1 += w_gl[k] * (w.u * r0 + P.c * (a5 - a1));
+    V1 += w_gl[k] * (w.u * r0 + P.c * amd);
     V2 += w_gl[k] * (w.v * Pk + la * w2);
     V3 += w_gl[k] * (la * dq[3]);
     ubar += w_gl[k] * w.u;
