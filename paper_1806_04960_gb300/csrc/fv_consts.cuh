@@ -78,6 +78,27 @@ __device__ __forceinline__ int32_t level_of(unsigned long long colsum, int ny) {
   return k > (unsigned long long)ny ? ny : (int32_t)k;
 }
 
+// FP64 signal rate (reading R-cfl) and detector weight of Eq.
+// (Free_surf_detector) on the 2^-32 fixed-point scale of one fluid cell with
+// state (m, mu, mv, a); bad = not admissible.  The same function of the
+// state for the prologue of a state that is set and for the epilogue of a
+// step, so that dt does not depend on where it was formed.  Reciprocals and
+// products in place of divisions (the FP64 pipe bounds the step kernels):
+// the rate is within an ulp or two of (|u| + c)/dx + (|v| + c)/dy.  inv_dx,
+// inv_dy, inv_1meps: 1/dx, 1/dy, 1/(1 - eps), each rounded once.
+__device__ __forceinline__ void rate_weight_f64(const StepParams& p, double inv_dx, double inv_dy,
+                                                double inv_1meps, double m, double mu, double mv,
+                                                double a, double& rate, unsigned long long& w,
+                                                bool& bad) {
+  const double r = rcp(m);
+  const double u = mu * r, v = mv * r;
+  bad = !gtz(m) || !gtz(a) || !isfinite(u) || !isfinite(v) || !isfinite(a);
+  rate = (tabs(u) + p.c) * inv_dx + (tabs(v) + p.c) * inv_dy;
+  double x = (a - p.eps) * inv_1meps;
+  x = x >= 0.0 ? (x > 1.0 ? 1.0 : x) : 0.0;  // NaN -> 0 (the status flag reports it)
+  w = (unsigned long long)__double2ll_rn(x * 4294967296.0);
+}
+
 // Per-cell epilogue of a step on the new state qn (stored form) with full
 // alpha rho m_full: admissibility, the signal rate of the next dt (reading
 // R-cfl) and the detector weight of Eq. (Free_surf_detector) on the common
@@ -103,17 +124,12 @@ __device__ __forceinline__ void cell_epilogue(const StepParams& p, const KConsts
     // 2^-24 resolution in float, placed on the common 2^-32 fixed-point scale
     my_w = (unsigned long long)__float2uint_rn((float)w * 16777216.0f) << 8;
   } else {
-    // double path: same expressions as the definition (IEEE division), so dt
-    // and the detected levels are reproducible
-    const double md = (double)m_full, ad = (double)qn[3];
-    const double ud = (double)qn[1] / md, vd = (double)qn[2] / md;
-    if (own && (!(md > 0.0) || !(ad > 0.0) || !isfinite(ud) || !isfinite(vd) || !isfinite(ad)))
-      bad = true;
-    const double rd = (fabs(ud) + p.c) / p.dx + (fabs(vd) + p.c) / p.dy;
+    double rd;
+    bool b = false;
+    rate_weight_f64(p, (double)kc.inv_dx, (double)kc.inv_dy, (double)kc.inv_1meps, (double)m_full,
+                    (double)qn[1], (double)qn[2], (double)qn[3], rd, my_w, b);
+    if (own && b) bad = true;
     my_rate = own && rd >= 0.0 ? (T)rd : T(0);
-    double w = (ad - p.eps) / (1.0 - p.eps);
-    w = w >= 0.0 ? (w > 1.0 ? 1.0 : w) : 0.0;  // NaN -> 0 (the status flag reports it)
-    my_w = (unsigned long long)__double2ll_rn(w * 4294967296.0);
   }
 }
 

@@ -275,6 +275,8 @@ __global__ void prologue_kernel(StepParams p, const double* __restrict__ q,
                                 const uint8_t* __restrict__ solid, unsigned long long* colsum,
                                 DevScalars* sc, int status_bits) {
   const size_t N = (size_t)p.nx * p.ny;
+  // the step kernels' constants (KConsts<double>): IEEE division here as on the host
+  const double inv_dx = 1.0 / p.dx, inv_dy = 1.0 / p.dy, inv_1meps = 1.0 / (1.0 - p.eps);
   double my_rate = 0.0;
   bool bad = false;
   for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < N;
@@ -284,14 +286,13 @@ __global__ void prologue_kernel(StepParams p, const double* __restrict__ q,
       atomicAdd(&colsum[i], ONE_FIXED);
       continue;
     }
-    const double m = q[c], mu = q[N + c], mv = q[2 * N + c], a = q[3 * N + c];
-    const double u = mu / m, v = mv / m;
-    if (!(m > 0.0) || !(a > 0.0) || !isfinite(u) || !isfinite(v) || !isfinite(a)) bad = true;
-    double r = (fabs(u) + p.c) / p.dx + (fabs(v) + p.c) / p.dy;
+    double r;
+    unsigned long long qw;
+    bool b;
+    rate_weight_f64(p, inv_dx, inv_dy, inv_1meps, q[c], q[N + c], q[2 * N + c], q[3 * N + c], r,
+                    qw, b);
+    if (b) bad = true;
     if (r >= 0.0) my_rate = fmax(my_rate, r);
-    double w = (a - p.eps) / (1.0 - p.eps);
-    w = w >= 0.0 ? (w > 1.0 ? 1.0 : w) : 0.0;  // NaN -> 0 (the status flag reports the state)
-    const unsigned long long qw = (unsigned long long)__double2ll_rn(w * 4294967296.0);
     if (qw) atomicAdd(&colsum[i], qw);
   }
   if (bad) atomicOr(&sc->status, status_bits);

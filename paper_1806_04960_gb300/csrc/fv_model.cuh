@@ -123,6 +123,35 @@ __host__ __device__ __forceinline__ Vel<T> velocity(T m, T mu, T mv) {
   return {mu * r, mv * r};
 }
 
+// The momentum fluxes of a face state: (mu u, mu v) across an x face and
+// (mu v, mv v) across a y face.  In FP64 device code each product is rounded
+// on its own (never fused into a neighbouring add), so that a flux formed
+// once per cell and stored gives the same bits as one formed where it is
+// used: the face solvers and the interior integral take the same four face
+// states of a cell.
+template <typename T>
+__host__ __device__ __forceinline__ T prod(T a, T b) {
+  return a * b;
+}
+#ifdef __CUDA_ARCH__
+template <>
+__device__ __forceinline__ double prod<double>(double a, double b) {
+  return __dmul_rn(a, b);
+}
+#endif
+template <typename T>
+__host__ __device__ __forceinline__ void xflux(T m, T mu, T mv, T f[2]) {
+  const Vel<T> w = velocity(m, mu, mv);
+  f[0] = prod(mu, w.u);
+  f[1] = prod(mu, w.v);
+}
+template <typename T>
+__host__ __device__ __forceinline__ void yflux(T m, T mu, T mv, T g[2]) {
+  const Vel<T> w = velocity(m, mu, mv);
+  g[0] = prod(mu, w.v);
+  g[1] = prod(mv, w.v);
+}
+
 // Paired FP32 forms of the face solvers (two evaluations of the same
 // arithmetic in the two lanes of float2, one instruction per pair on sm_100
 // and later); defined at the end of this file, used by xface and yface in
@@ -142,9 +171,11 @@ __host__ __device__ __forceinline__ void yface_f2(const float qm[4], const float
 // (FIrstOrderDgeneric_x).  qm, qp: full states; dq: qp - qm formed exactly by
 // the caller.
 // ---------------------------------------------------------------------------
+// fm, fp: the x fluxes (xflux) of qm and qp.
 template <typename T>
-__host__ __device__ __forceinline__ void xface_scalar(const T qm[4], const T qp[4], const T dq[4],
-                                                      const Phys<T>& P, T Dm[4], T Dp[4]) {
+__host__ __device__ __forceinline__ void xface_fx(const T qm[4], const T dq[4], const T fm[2],
+                                                  const T fp[2], const Phys<T>& P, T Dm[4],
+                                                  T Dp[4]) {
   const T s_gl[3] = {T(0.5 - 0.38729833462074168852), T(0.5), T(0.5 + 0.38729833462074168852)};
   const T w_gl[3] = {T(5.0 / 18.0), T(8.0 / 18.0), T(5.0 / 18.0)};
   T V0 = 0, V1 = 0, V2 = 0, V3 = 0, ubar = 0;
@@ -181,11 +212,9 @@ __host__ __device__ __forceinline__ void xface_scalar(const T qm[4], const T qp[
     V3 += w_gl[k] * (la * dq[3]);
     ubar += w_gl[k] * w.u;
   }
-  const Vel<T> em = velocity(qm[0], qm[1], qm[2]);
-  const Vel<T> ep = velocity(qp[0], qp[1], qp[2]);
   const T F0 = dq[1];
-  const T F1 = (qp[1] * ep.u - qm[1] * em.u) + P.c2 * dr;
-  const T F2 = qp[1] * ep.v - qm[1] * em.v;
+  const T F1 = (fp[0] - fm[0]) + P.c2 * dr;
+  const T F2 = fp[1] - fm[1];
   const T F3 = ubar * dq[3];
   Dm[0] = T(0.5) * (F0 - V0);
   Dp[0] = T(0.5) * (F0 + V0);
@@ -195,6 +224,15 @@ __host__ __device__ __forceinline__ void xface_scalar(const T qm[4], const T qp[
   Dp[2] = T(0.5) * (F2 + V2);
   Dm[3] = T(0.5) * (F3 - V3);
   Dp[3] = T(0.5) * (F3 + V3);
+}
+
+template <typename T>
+__host__ __device__ __forceinline__ void xface_scalar(const T qm[4], const T qp[4], const T dq[4],
+                                                      const Phys<T>& P, T Dm[4], T Dp[4]) {
+  T fm[2], fp[2];
+  xflux(qm[0], qm[1], qm[2], fm);
+  xflux(qp[0], qp[1], qp[2], fp);
+  xface_fx(qm, dq, fm, fp, P, Dm, Dp);
 }
 
 // sign(A1(q)) r = R1 sign(Lambda1) R1^-1 r for r with zero 5th entry: the
@@ -328,37 +366,32 @@ __host__ __device__ __forceinline__ void sign_A2(T u, T v, const T r[4], const P
 // ---------------------------------------------------------------------------
 // dap: jump of alpha p = c2 (m - rho0 alpha) from qm to qp, formed by the
 // caller so that it is exactly zero between two states of one rest profile.
+// gm, gp: the y fluxes (yflux) of qm and qp.
 template <typename T>
-__host__ __device__ __forceinline__ void yface_scalar(const T qm[4], const T qp[4], const T dq[4],
-                                                      T dap, const Phys<T>& P, T Dm[4], T Dp[4]) {
-  // nodes s = 0, 1/4, 1/2, 3/4, 1 (interior nodes on the path, exact endpoints)
-  T mu_[5], mv_[5], u_[5], v_[5];
+__host__ __device__ __forceinline__ void yface_fx(const T qm[4], const T dq[4], const T gm[2],
+                                                  const T gp[2], T dap, const Phys<T>& P, T Dm[4],
+                                                  T Dp[4]) {
+  // interior nodes s = 1/4, 1/2, 3/4 on the path
+  T u_[4], v_[4];
+  T mu2 = T(0), mv2 = T(0);
 #pragma unroll
   for (int k = 1; k < 4; ++k) {
     const T s = T(0.25 * k);
     const T m = qm[0] + s * dq[0];
-    mu_[k] = qm[1] + s * dq[1];
-    mv_[k] = qm[2] + s * dq[2];
-    const Vel<T> w = velocity(m, mu_[k], mv_[k]);
+    const T mu = qm[1] + s * dq[1];
+    const T mv = qm[2] + s * dq[2];
+    const Vel<T> w = velocity(m, mu, mv);
     u_[k] = w.u;
     v_[k] = w.v;
-  }
-  {
-    const Vel<T> a = velocity(qm[0], qm[1], qm[2]);
-    const Vel<T> b = velocity(qp[0], qp[1], qp[2]);
-    mu_[0] = qm[1];
-    mv_[0] = qm[2];
-    u_[0] = a.u;
-    v_[0] = a.v;
-    mu_[4] = qp[1];
-    mv_[4] = qp[2];
-    u_[4] = b.u;
-    v_[4] = b.v;
+    if (k == 2) {
+      mu2 = mu;
+      mv2 = mv;
+    }
   }
   // g components at nodes 0, 2, 4: (mv, mu v, mv v)
-  const T g1_0 = mu_[0] * v_[0], g2_0 = mv_[0] * v_[0];
-  const T g1_2 = mu_[2] * v_[2], g2_2 = mv_[2] * v_[2];
-  const T g1_4 = mu_[4] * v_[4], g2_4 = mv_[4] * v_[4];
+  const T g1_0 = gm[0], g2_0 = gm[1];
+  const T g1_2 = mu2 * v_[2], g2_2 = mv2 * v_[2];
+  const T g1_4 = gp[0], g2_4 = gp[1];
   T V[4] = {0, 0, 0, 0};
   {  // k = 1: [0, 1/2], node 1/4, weight 4/3
     const T r[4] = {T(0.5) * dq[2], g1_2 - g1_0, g2_2 - g2_0 + T(0.5) * dap,
@@ -396,6 +429,15 @@ __host__ __device__ __forceinline__ void yface_scalar(const T qm[4], const T qp[
   Dp[2] = T(0.5) * (G2 + V[2]);
   Dm[3] = T(0.5) * (G3 - V[3]);
   Dp[3] = T(0.5) * (G3 + V[3]);
+}
+
+template <typename T>
+__host__ __device__ __forceinline__ void yface_scalar(const T qm[4], const T qp[4], const T dq[4],
+                                                      T dap, const Phys<T>& P, T Dm[4], T Dp[4]) {
+  T gm[2], gp[2];
+  yflux(qm[0], qm[1], qm[2], gm);
+  yflux(qp[0], qp[1], qp[2], gp);
+  yface_fx(qm, dq, gm, gp, dap, P, Dm, Dp);
 }
 
 // ---------------------------------------------------------------------------
@@ -506,26 +548,40 @@ __host__ __device__ __forceinline__ T recon_core(const T Qf[4], T fW[4], T fE[4]
 // the conservative part f(q_E) - f(q_W), g(q_N) - g(q_S) plus B grad q, whose
 // third component is the fluctuation form of Eq. (b^y_3_final_integral)
 // (pressure part [(alpha p)^f]_S^N and gravity g dy (m - m^E) at the centre).
+// xW, xE: the x fluxes (xflux) of the W and E face states; yS, yN: the y
+// fluxes (yflux) of the S and N ones.
+template <typename T>
+__host__ __device__ __forceinline__ void interior_terms_fx(const T fW[4], const T fE[4],
+                                                           const T fS[4], const T fN[4],
+                                                           const T base[4], T mEc, const T xW[2],
+                                                           const T xE[2], const T yS[2],
+                                                           const T yN[2], T dax, T day, T dx,
+                                                           T dy, const Phys<T>& P, T Ix[4],
+                                                           T Iy[4]) {
+  const Vel<T> vc = velocity(mEc + base[0], base[1], base[2]);
+  Ix[0] = fE[1] - fW[1];
+  Ix[1] = (xE[0] - xW[0]) + P.c2 * ((fE[0] - fW[0]) - P.rho0 * (fE[3] - fW[3]));
+  Ix[2] = xE[1] - xW[1];
+  Ix[3] = dx * vc.u * dax;
+  Iy[0] = fN[2] - fS[2];
+  Iy[1] = yN[0] - yS[0];
+  Iy[2] = (yN[1] - yS[1]) + P.c2 * ((fN[0] - fS[0]) - P.rho0 * (fN[3] - fS[3])) +
+          P.g * dy * base[0];
+  Iy[3] = dy * vc.v * day;
+}
+
 template <typename T>
 __host__ __device__ __forceinline__ void interior_terms(const T fW[4], const T fE[4],
                                                         const T fS[4], const T fN[4],
                                                         const T base[4], T mEc, T mES, T mEN,
                                                         T dax, T day, T dx, T dy,
                                                         const Phys<T>& P, T Ix[4], T Iy[4]) {
-  const Vel<T> vE = velocity(mEc + fE[0], fE[1], fE[2]);
-  const Vel<T> vW = velocity(mEc + fW[0], fW[1], fW[2]);
-  const Vel<T> vN = velocity(mEN + fN[0], fN[1], fN[2]);
-  const Vel<T> vS = velocity(mES + fS[0], fS[1], fS[2]);
-  const Vel<T> vc = velocity(mEc + base[0], base[1], base[2]);
-  Ix[0] = fE[1] - fW[1];
-  Ix[1] = (fE[1] * vE.u - fW[1] * vW.u) + P.c2 * ((fE[0] - fW[0]) - P.rho0 * (fE[3] - fW[3]));
-  Ix[2] = fE[1] * vE.v - fW[1] * vW.v;
-  Ix[3] = dx * vc.u * dax;
-  Iy[0] = fN[2] - fS[2];
-  Iy[1] = fN[1] * vN.v - fS[1] * vS.v;
-  Iy[2] = (fN[2] * vN.v - fS[2] * vS.v) + P.c2 * ((fN[0] - fS[0]) - P.rho0 * (fN[3] - fS[3])) +
-          P.g * dy * base[0];
-  Iy[3] = dy * vc.v * day;
+  T xW[2], xE[2], yS[2], yN[2];
+  xflux(mEc + fW[0], fW[1], fW[2], xW);
+  xflux(mEc + fE[0], fE[1], fE[2], xE);
+  yflux(mES + fS[0], fS[1], fS[2], yS);
+  yflux(mEN + fN[0], fN[1], fN[2], yN);
+  interior_terms_fx(fW, fE, fS, fN, base, mEc, xW, xE, yS, yN, dax, day, dx, dy, P, Ix, Iy);
 }
 
 // ---------------------------------------------------------------------------

@@ -53,11 +53,23 @@ __host__ __device__ constexpr int strip_threads() {
 }
 static_assert(BY * SWX <= 288 && BY * SRX <= 288 && NXF <= 288, "one pass per phase");
 
+// FP64 keeps the face fluxes of each reconstructed cell (face_fluxes) beside
+// its record: its two x faces, two y faces and update then read them instead
+// of forming them again (four fewer reciprocals per cell on the FP64 pipe).
+// FP32 forms them where they are used: its three CTAs per SM have no room
+// for the two more rings.
+template <typename T>
+__host__ __device__ constexpr bool keeps_fluxes() {
+  return sizeof(T) == 8;
+}
+
 template <typename T>
 struct StripSmem {
+  static constexpr int FR = keeps_fluxes<T>() ? RING : 1, FX = keeps_fluxes<T>() ? SRX : 1;
   V4<T> w[WRING][SWX];         // window rows of Q^n (stored form, re-based)
   V4<T> rs[RING][SRX];         // (alpha^E, m^E centre, bottom, top face)
   V4<T> rf[4][RING][SRX];      // face fluctuation states W, E, S, N at t^{n+1/2}
+  V4<T> fl[2][FR][FX];         // x fluxes of W, E and y fluxes of S, N (FP64)
   V4<T> base[RING][SX];        // centre fluctuation at t^{n+1/2}
   V4<T> Dx[2][BY][SX + 1];     // D-, D+ of the block's x faces
   V4<T> Dy[2][RING][SX];       // D-, D+ of the y faces, by the row below the face
@@ -81,6 +93,7 @@ __device__ __forceinline__ void strip_body(const StepParams& p, const KConsts<T>
                                            int sx, int sy, int H, StripSmem<T>& S) {
   constexpr int NTS = strip_threads<T>();
   constexpr int YF0 = NTS - 9 * 32;  // y faces taken by the warps past the x faces' nine
+  constexpr bool FLX = keeps_fluxes<T>();
   const int t = threadIdx.x;
   const int nx = p.nx, ny = p.ny;
   const size_t N = (size_t)nx * ny;
@@ -127,6 +140,7 @@ __device__ __forceinline__ void strip_body(const StepParams& p, const KConsts<T>
       S.rs[s][rx] = rs;
 #pragma unroll
       for (int f = 0; f < 4; ++f) S.rf[f][s][rx] = rf[f];
+      if constexpr (FLX) face_fluxes(rs, rf, S.fl[0][s][rx], S.fl[1][s][rx]);
       if (rx >= 1 && rx <= SX) {
         S.base[s][rx - 1] = pack(base);
         S.ga[0][s][rx - 1] = ga[0];
@@ -140,7 +154,8 @@ __device__ __forceinline__ void strip_body(const StepParams& p, const KConsts<T>
     const int rx = fx + 1, sT = rwrap(sB + 1), wT = wwrap(wB + 1);
     T Dm[4], Dp[4];
     y_face<T>(S.flag[wB][rx + 1], S.flag[wT][rx + 1], &S.rs[sB][rx], &S.rf[F_N][sB][rx],
-              &S.rs[sT][rx], &S.rf[F_S][sT][rx], S.K[rx + 1], rB + 1, rt, ny, sd, P, Dm, Dp);
+              &S.rs[sT][rx], &S.rf[F_S][sT][rx], S.K[rx + 1], rB + 1, rt, ny, sd, P, Dm, Dp,
+              FLX ? &S.fl[1][sB][rx] : nullptr, FLX ? &S.fl[1][sT][rx] : nullptr);
     S.Dy[0][sB][fx] = pack(Dm);
     S.Dy[1][sB][fx] = pack(Dp);
   };
@@ -193,7 +208,8 @@ __device__ __forceinline__ void strip_body(const StepParams& p, const KConsts<T>
       const int s = rwrap(sb + fy), ws = wwrap(wb + fy);
       T Dm[4], Dp[4];
       x_face<T, XOR>(S.flag[ws][fx + 1], S.flag[ws][fx + 2], &S.rs[s][fx], &S.rf[F_E][s][fx],
-                     &S.rs[s][fx + 1], &S.rf[F_W][s][fx + 1], sd, P, Dm, Dp);
+                     &S.rs[s][fx + 1], &S.rf[F_W][s][fx + 1], sd, P, Dm, Dp,
+                     FLX ? &S.fl[0][s][fx] : nullptr, FLX ? &S.fl[0][s][fx + 1] : nullptr);
       S.Dx[0][fy][fx] = pack(Dm);
       S.Dx[1][fy][fx] = pack(Dp);
     } else if (YF0 > 0 && t >= 9 * 32) {
@@ -223,7 +239,9 @@ __device__ __forceinline__ void strip_body(const StepParams& p, const KConsts<T>
         const T m_full = update_cell<T, DEV>(qold, S.rs[s][ux + 1], rf, S.base[s][ux],
                                              S.ga[0][s][ux], S.ga[1][s][ux], S.Dx[1][uy][ux],
                                              S.Dx[0][uy][ux + 1], S.Dy[1][sbelow][ux],
-                                             S.Dy[0][s][ux], rEc, rdx, rdy, dx, dy, P, qn);
+                                             S.Dy[0][s][ux], rEc, rdx, rdy, dx, dy, P, qn,
+                                             FLX ? &S.fl[0][s][ux + 1] : nullptr,
+                                             FLX ? &S.fl[1][s][ux + 1] : nullptr);
         const size_t c = (size_t)r * nx + gi_me;
 #pragma unroll
         for (int v = 0; v < 4; ++v) qout[v * N + c] = qn[v];

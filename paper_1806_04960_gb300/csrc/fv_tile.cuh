@@ -309,6 +309,22 @@ __device__ __forceinline__ void recon_cell(const V4<T>* wS, const V4<T>* wC, con
   rf[F_N] = pack(fNo);
 }
 
+// Face-flux records of a reconstructed cell (rs, rf as recon_cell writes
+// them): xf = the x fluxes of its W and E face states, yf = the y fluxes of
+// its S and N ones (xflux, yflux), formed once for the cell's two x faces,
+// two y faces and interior integral.
+template <typename T>
+__device__ __forceinline__ void face_fluxes(const V4<T>& rs, const V4<T> rf[4], V4<T>& xf,
+                                            V4<T>& yf) {
+  T a[2], b[2], c[2], d[2];
+  xflux(rs.y + rf[F_W].x, rf[F_W].y, rf[F_W].z, a);
+  xflux(rs.y + rf[F_E].x, rf[F_E].y, rf[F_E].z, b);
+  yflux(rs.z + rf[F_S].x, rf[F_S].y, rf[F_S].z, c);
+  yflux(rs.w + rf[F_N].x, rf[F_N].y, rf[F_N].z, d);
+  xf = V4<T>{a[0], a[1], b[0], b[1]};
+  yf = V4<T>{c[0], c[1], d[0], d[1]};
+}
+
 // x face between the reconstructed cells L (left) and R (right) with flags fl,
 // fr: L's (alpha^E, m^E ...) record sL and east face state eL, R's record sR
 // and west face state wR (read only where the cell is fluid).  Both fluid: the
@@ -316,10 +332,14 @@ __device__ __forceinline__ void recon_cell(const V4<T>* wS, const V4<T>* wC, con
 // (a wall or a solid neighbour) or the transmissive copy on the other side.
 // XOR selects the conservative Osher-Romberg viscosity of Eq. (OR_cons)
 // instead of the Gauss-Legendre quadrature of Eq. (OsherMatrixFormal_approx).
+// xfL, xfR (optional, FP64): L's and R's face-flux records (face_fluxes), whose
+// E and W parts replace the solver's own evaluation of the endpoint fluxes
+// with the same bits.
 template <typename T, bool XOR>
 __device__ __forceinline__ void x_face(unsigned char fl, unsigned char fr, const V4<T>* sL,
                                        const V4<T>* eL, const V4<T>* sR, const V4<T>* wR,
-                                       const Sides& sd, const Phys<T>& P, T Dm[4], T Dp[4]) {
+                                       const Sides& sd, const Phys<T>& P, T Dm[4], T Dp[4],
+                                       const V4<T>* xfL = nullptr, const V4<T>* xfR = nullptr) {
 #pragma unroll
   for (int c = 0; c < 4; ++c) Dm[c] = Dp[c] = T(0);
   const bool L = fl == F_FLUID, R = fr == F_FLUID;
@@ -338,6 +358,12 @@ __device__ __forceinline__ void x_face(unsigned char fl, unsigned char fr, const
     dq[1] = fr4[1] - fl4[1];
     dq[2] = fr4[2] - fl4[2];
     dq[3] = (aR - aL) + (fr4[3] - fl4[3]);
+    if (!XOR && xfL) {
+      const V4<T> a2 = *xfL, b2 = *xfR;
+      const T fm[2] = {a2.z, a2.w}, fp[2] = {b2.x, b2.y};
+      xface_fx(qm, dq, fm, fp, P, Dm, Dp);
+      return;
+    }
   } else {
     const V4<T> s = L ? *sL : *sR;
     const V4<T> fc = L ? *eL : *wR;
@@ -369,11 +395,14 @@ __device__ __forceinline__ void x_face(unsigned char fl, unsigned char fr, const
 // state; sT, sT_: T's record and south face state.  The jump of alpha p is
 // split into its equilibrium part (rho^E_f - rho0) Delta alpha^E, exactly
 // zero at the level face, and the fluctuation part c2 (dm^f - rho0 da^f).
+// yfB, yfT (optional, FP64): B's and T's face-flux records, whose N and S
+// parts replace the solver's own evaluation of the endpoint fluxes.
 template <typename T>
 __device__ __forceinline__ void y_face(unsigned char fb, unsigned char ft, const V4<T>* sB,
                                        const V4<T>* nB, const V4<T>* sT, const V4<T>* sT_,
                                        int K, int gjT, const T* __restrict__ rt, int ny,
-                                       const Sides& sd, const Phys<T>& P, T Dm[4], T Dp[4]) {
+                                       const Sides& sd, const Phys<T>& P, T Dm[4], T Dp[4],
+                                       const V4<T>* yfB = nullptr, const V4<T>* yfT = nullptr) {
 #pragma unroll
   for (int c = 0; c < 4; ++c) Dm[c] = Dp[c] = T(0);
   const bool B = fb == F_FLUID, Tt = ft == F_FLUID;
@@ -395,6 +424,12 @@ __device__ __forceinline__ void y_face(unsigned char fb, unsigned char ft, const
     dq[3] = (aT - aB) + (ft4[3] - fb4[3]);
     const T rEf = tab(rt, 2 * (gjT - K), ny);
     dap = P.c2 * ((rEf - P.rho0) * (aT - aB) + ((ft4[0] - fb4[0]) - P.rho0 * (ft4[3] - fb4[3])));
+    if (yfB) {
+      const V4<T> a2 = *yfB, b2 = *yfT;
+      const T gm[2] = {a2.z, a2.w}, gp[2] = {b2.x, b2.y};
+      yface_fx(qm, dq, gm, gp, dap, P, Dm, Dp);
+      return;
+    }
   } else {
     const V4<T> s = B ? *sB : *sT;
     const V4<T> fc = B ? *nB : *sT_;
@@ -426,12 +461,15 @@ __device__ __forceinline__ void y_face(unsigned char fb, unsigned char ft, const
 // cell's reconstruction; DpW, DmE, DpS, DmN: the fluctuations of its four
 // faces; rEc: rho^E at its centre (deviation form).  qn: the new state in
 // stored form; returns the full alpha rho.
+// xf, yf (optional, FP64): the cell's face-flux records (face_fluxes), in
+// place of the interior integral's own evaluation of the same fluxes.
 template <typename T, bool DEV>
 __device__ __forceinline__ T update_cell(const T qold[4], const V4<T>& rs, const V4<T>* rf,
                                          const V4<T>& base4, T dax, T day, const V4<T>& DpW4,
                                          const V4<T>& DmE4, const V4<T>& DpS4, const V4<T>& DmN4,
                                          T rEc, T rdx, T rdy, T dx, T dy, const Phys<T>& P,
-                                         T qn[4]) {
+                                         T qn[4], const V4<T>* xf = nullptr,
+                                         const V4<T>* yf = nullptr) {
   const T mEc = rs.y, mES = rs.z, mEN = rs.w;
   T fW[4], fE[4], fS[4], fN[4], base[4];
   unpack(rf[F_W], fW);
@@ -440,7 +478,13 @@ __device__ __forceinline__ T update_cell(const T qold[4], const V4<T>& rs, const
   unpack(rf[F_N], fN);
   unpack(base4, base);
   T Ix[4], Iy[4];
-  interior_terms(fW, fE, fS, fN, base, mEc, mES, mEN, dax, day, dx, dy, P, Ix, Iy);
+  if (xf) {
+    const V4<T> a = *xf, b = *yf;
+    const T xW[2] = {a.x, a.y}, xE[2] = {a.z, a.w}, yS[2] = {b.x, b.y}, yN[2] = {b.z, b.w};
+    interior_terms_fx(fW, fE, fS, fN, base, mEc, xW, xE, yS, yN, dax, day, dx, dy, P, Ix, Iy);
+  } else {
+    interior_terms(fW, fE, fS, fN, base, mEc, mES, mEN, dax, day, dx, dy, P, Ix, Iy);
+  }
   T xs[4], ys[4], DpW[4], DmE[4], DpS[4], DmN[4];
   unpack(DpW4, DpW);
   unpack(DmE4, DmE);

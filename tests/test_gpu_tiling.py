@@ -77,7 +77,10 @@ CASES = {
 def test_strip_equals_tile(fv, name, prec):
     c = CASES[name]()
     p = getattr(fv, prec)
-    n = 30 if c.nx * c.ny > 100000 else 60
+    # the 96^2 drop turns non-admissible near step 50, where its gas cavitates
+    # at the receding interface (roundoff decides the step: the oracle's own
+    # run fails at 60 steps with CFL 0.9 and passes with 0.9 (1 + 1e-12))
+    n = 30 if c.nx * c.ny > 100000 or name == "drop_96" else 60
     a = run(fv, c, p, fv.FV_TILING_TILE, n)
     b = run(fv, c, p, fv.FV_TILING_STRIP, n)
     same(a, b)
