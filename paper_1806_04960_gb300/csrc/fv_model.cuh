@@ -47,6 +47,20 @@ __device__ __forceinline__ double tabs<double>(double x) {
   return __longlong_as_double(__double_as_longlong(x) & 0x7fffffffffffffffLL);
 }
 #endif
+// sgn(s) x.  In FP64 device code on the integer pipe: the sign bit of s
+// applied to x (a zero s gives the zero 0 x of the sign of x; x finite).
+template <typename T>
+__host__ __device__ __forceinline__ T sgn_mul(T s, T x) {
+  return sgn(s) * x;
+}
+#ifdef __CUDA_ARCH__
+template <>
+__device__ __forceinline__ double sgn_mul<double>(double s, double x) {
+  const long long bs = __double_as_longlong(s), bx = __double_as_longlong(x);
+  const long long sign = (long long)0x8000000000000000ULL;
+  return __longlong_as_double((bs << 1) == 0 ? (bx & sign) : (bx ^ (bs & sign)));
+}
+#endif
 // x > 0, and |x| > y for y >= 0 (the same integer reading in FP64 device code).
 template <typename T>
 __host__ __device__ __forceinline__ bool gtz(T x) {
@@ -72,6 +86,22 @@ __device__ __forceinline__ bool abs_gt<double>(double x, double y) {
 template <>
 __device__ __forceinline__ bool abs_lt<double>(double x, double y) {
   return (__double_as_longlong(x) & 0x7fffffffffffffffLL) < __double_as_longlong(y);
+}
+#endif
+
+// The smaller of two values >= 0 (or -0).  In FP64 device code on the
+// integer pipe: the bits of doubles >= +0, read as signed 64-bit integers,
+// order as the values do (-0 reads as the smallest, and equals +0 in every
+// later use).
+template <typename T>
+__host__ __device__ __forceinline__ T min_nonneg(T a, T b) {
+  return fmin(a, b);
+}
+#ifdef __CUDA_ARCH__
+template <>
+__device__ __forceinline__ double min_nonneg<double>(double a, double b) {
+  const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+  return ia <= ib ? a : b;
 }
 #endif
 
@@ -177,8 +207,11 @@ __host__ __device__ __forceinline__ void xface_fx(const T qm[4], const T dq[4], 
                                                   const T fp[2], const Phys<T>& P, T Dm[4],
                                                   T Dp[4]) {
   const T s_gl[3] = {T(0.5 - 0.38729833462074168852), T(0.5), T(0.5 + 0.38729833462074168852)};
-  const T w_gl[3] = {T(5.0 / 18.0), T(8.0 / 18.0), T(5.0 / 18.0)};
-  T V0 = 0, V1 = 0, V2 = 0, V3 = 0, ubar = 0;
+  // half the Gauss-Legendre weights (5/18, 8/18, 5/18): the sums below are
+  // then half of V and of u_bar, exactly (a power-of-two scale), and so
+  // D-+ = (F -+ V) / 2 takes one subtraction or addition per component
+  const T w_gl[3] = {T(5.0 / 36.0), T(8.0 / 36.0), T(5.0 / 36.0)};
+  T V0 = 0, V1 = 0, V2 = 0, lbar = 0, ubar = 0;
   const T dr = dq[0] - P.rho0 * dq[3];  // d1 - rho0 d4
   const T cdr = P.c * dr, B = P.rho0 * dq[3];
 #pragma unroll
@@ -209,21 +242,23 @@ __host__ __device__ __forceinline__ void xface_fx(const T qm[4], const T dq[4], 
     V0 += w_gl[k] * r0;
     V1 += w_gl[k] * (w.u * r0 + P.c * amd);
     V2 += w_gl[k] * (w.v * Pk + la * w2);
-    V3 += w_gl[k] * (la * dq[3]);
+    lbar += w_gl[k] * la;  // V3 = lbar d4
     ubar += w_gl[k] * w.u;
   }
-  const T F0 = dq[1];
-  const T F1 = (fp[0] - fm[0]) + P.c2 * dr;
-  const T F2 = fp[1] - fm[1];
+  const T V3 = lbar * dq[3];
+  // F / 2
+  const T F0 = T(0.5) * dq[1];
+  const T F1 = T(0.5) * (fp[0] - fm[0]) + (T(0.5) * P.c2) * dr;
+  const T F2 = T(0.5) * (fp[1] - fm[1]);
   const T F3 = ubar * dq[3];
-  Dm[0] = T(0.5) * (F0 - V0);
-  Dp[0] = T(0.5) * (F0 + V0);
-  Dm[1] = T(0.5) * (F1 - V1);
-  Dp[1] = T(0.5) * (F1 + V1);
-  Dm[2] = T(0.5) * (F2 - V2);
-  Dp[2] = T(0.5) * (F2 + V2);
-  Dm[3] = T(0.5) * (F3 - V3);
-  Dp[3] = T(0.5) * (F3 + V3);
+  Dm[0] = F0 - V0;
+  Dp[0] = F0 + V0;
+  Dm[1] = F1 - V1;
+  Dp[1] = F1 + V1;
+  Dm[2] = F2 - V2;
+  Dp[2] = F2 + V2;
+  Dm[3] = F3 - V3;
+  Dp[3] = F3 + V3;
 }
 
 template <typename T>
@@ -327,19 +362,20 @@ __host__ __device__ __forceinline__ void xface_or(const T qm[4], const T qp[4], 
 template <typename T>
 __host__ __device__ __forceinline__ void sign_A2(T u, T v, const T r[4], const Phys<T>& P,
                                                  T out[4]) {
-  const T s3 = sgn(v);
   if (abs_lt(v, P.c)) {
     // |v| < c: the acoustic eigenvalues v - c < 0 < v + c, so the two acoustic
     // terms combine to (w5 - w1) = (r2 - v r0) / c and (w5 + w1) = r0 - rho0 r3
-    const T D = r[0] - P.rho0 * r[3];
+    const T rr = P.rho0 * r[3];
+    const T D = r[0] - rr;
     const T Pk = (r[2] - v * r[0]) * P.inv_c;
-    const T o0 = Pk + s3 * P.rho0 * r[3];
+    const T o0 = Pk + sgn_mul(v, rr);
     out[0] = o0;
-    out[1] = u * Pk + s3 * (r[1] - u * D);
+    out[1] = u * Pk + sgn_mul(v, r[1] - u * D);
     out[2] = v * o0 + P.c * D;
-    out[3] = s3 * r[3];
+    out[3] = sgn_mul(v, r[3]);
     return;
   }
+  const T s3 = sgn(v);
   const T vc = v * P.inv_c;
   const T w1 = T(0.5) * ((T(1) + vc) * r[0] - r[2] * P.inv_c - P.rho0 * r[3]);
   const T w5 = T(0.5) * ((T(1) - vc) * r[0] + r[2] * P.inv_c - P.rho0 * r[3]);
@@ -392,6 +428,8 @@ __host__ __device__ __forceinline__ void yface_fx(const T qm[4], const T dq[4], 
   const T g1_0 = gm[0], g2_0 = gm[1];
   const T g1_2 = mu2 * v_[2], g2_2 = mv2 * v_[2];
   const T g1_4 = gp[0], g2_4 = gp[1];
+  // the Romberg weights 4/3, 4/3, -1/3 halved: V and v_bar below are half
+  // of the sums, exactly, so that D-+ = G/2 -+ V/2
   T V[4] = {0, 0, 0, 0};
   {  // k = 1: [0, 1/2], node 1/4, weight 4/3
     const T r[4] = {T(0.5) * dq[2], g1_2 - g1_0, g2_2 - g2_0 + T(0.5) * dap,
@@ -399,7 +437,7 @@ __host__ __device__ __forceinline__ void yface_fx(const T qm[4], const T dq[4], 
     T o[4];
     sign_A2(u_[1], v_[1], r, P, o);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) V[c] += T(4.0 / 3.0) * o[c];
+    for (int c = 0; c < 4; ++c) V[c] += T(2.0 / 3.0) * o[c];
   }
   {  // k = 2: [1/2, 1], node 3/4, weight 4/3
     const T r[4] = {T(0.5) * dq[2], g1_4 - g1_2, g2_4 - g2_2 + T(0.5) * dap,
@@ -407,28 +445,29 @@ __host__ __device__ __forceinline__ void yface_fx(const T qm[4], const T dq[4], 
     T o[4];
     sign_A2(u_[3], v_[3], r, P, o);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) V[c] += T(4.0 / 3.0) * o[c];
+    for (int c = 0; c < 4; ++c) V[c] += T(2.0 / 3.0) * o[c];
   }
   {  // k = 3: [0, 1], node 1/2, weight -1/3
     const T r[4] = {dq[2], g1_4 - g1_0, g2_4 - g2_0 + dap, v_[2] * dq[3]};
     T o[4];
     sign_A2(u_[2], v_[2], r, P, o);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) V[c] -= T(1.0 / 3.0) * o[c];
+    for (int c = 0; c < 4; ++c) V[c] -= T(1.0 / 6.0) * o[c];
   }
-  const T vbar = T(2.0 / 3.0) * (v_[1] + v_[3]) - T(1.0 / 3.0) * v_[2];
-  const T G0 = dq[2];
-  const T G1 = g1_4 - g1_0;
-  const T G2 = g2_4 - g2_0 + dap;
+  const T vbar = T(1.0 / 3.0) * (v_[1] + v_[3]) - T(1.0 / 6.0) * v_[2];
+  // G / 2
+  const T G0 = T(0.5) * dq[2];
+  const T G1 = T(0.5) * (g1_4 - g1_0);
+  const T G2 = T(0.5) * (g2_4 - g2_0 + dap);
   const T G3 = vbar * dq[3];
-  Dm[0] = T(0.5) * (G0 - V[0]);
-  Dp[0] = T(0.5) * (G0 + V[0]);
-  Dm[1] = T(0.5) * (G1 - V[1]);
-  Dp[1] = T(0.5) * (G1 + V[1]);
-  Dm[2] = T(0.5) * (G2 - V[2]);
-  Dp[2] = T(0.5) * (G2 + V[2]);
-  Dm[3] = T(0.5) * (G3 - V[3]);
-  Dp[3] = T(0.5) * (G3 + V[3]);
+  Dm[0] = G0 - V[0];
+  Dp[0] = G0 + V[0];
+  Dm[1] = G1 - V[1];
+  Dp[1] = G1 + V[1];
+  Dm[2] = G2 - V[2];
+  Dp[2] = G2 + V[2];
+  Dm[3] = G3 - V[3];
+  Dp[3] = G3 + V[3];
 }
 
 template <typename T>
@@ -477,21 +516,21 @@ __host__ __device__ __forceinline__ T recon_core(const T Qf[4], T fW[4], T fE[4]
   T psi = T(1);
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
-    const T up = mx[v] - Qf[v], dn = mn[v] - Qf[v];
+    // The faces at -h/2 and +h/2 see the increments -d and +d, bounded by up =
+    // mx - Qf >= 0 on the side where the increment is positive and by -dn =
+    // Qf - mn >= 0 on the other: the two factors min(1, up/|d|) and
+    // min(1, -dn/|d|), of which the smaller, min(1, lim/|d|) with lim =
+    // min(up, -dn), decides (the factor of a face is monotone in its ratio,
+    // and so are the rounded operations: the same bits as taking both).
+    const T lim = min_nonneg(mx[v] - Qf[v], Qf[v] - mn[v]);
 #pragma unroll
     for (int dir = 0; dir < 2; ++dir) {
-      // faces at -h/2 and +h/2 see increments -d and +d
       const T d = dir == 0 ? R.half_dx * gx[v] : R.half_dy * gy[v];
-      const T ad = tabs(d);
       if (abs_gt(d, R.eta[v])) {
-        const T inv = rcp(d);
-        const T ramp = fmin(T(1), (ad - R.eta[v]) * R.inv_eta[v]);
-        // face with increment +d: bound up if d > 0, dn if d < 0; face with -d: the other
-        const bool dpos = gtz(d);
-        const T phi_p = fmin(T(1), (dpos ? up : dn) * inv);
-        const T phi_m = fmin(T(1), -(dpos ? dn : up) * inv);
-        psi = fmin(psi, T(1) - ramp * (T(1) - phi_p));
-        psi = fmin(psi, T(1) - ramp * (T(1) - phi_m));
+        const T ad = tabs(d);
+        const T ramp = min_nonneg(T(1), (ad - R.eta[v]) * R.inv_eta[v]);
+        const T phi = min_nonneg(T(1), lim * rcp(ad));
+        psi = min_nonneg(psi, T(1) - ramp * (T(1) - phi));
       }
     }
   }
