@@ -402,6 +402,14 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------- our arm
+def order_mix(case, q):
+    """Fluid cells of a state and those of them that the order switch of
+    Section 3.4 (alpha <= 10 eps) advances at first order."""
+    import numpy as np
+    fluid = case.solid == 0
+    return int(fluid.sum()), int((fluid & (q[3] <= 10.0 * case.eps)).sum())
+
+
 def measure_path(fv, case, prec, steps, warmup, stream_sync, barrier, device_index, strip_rows=0):
     s = fv.Solver(case, prec)
     s.set_state(case.q)
@@ -412,15 +420,25 @@ def measure_path(fv, case, prec, steps, warmup, stream_sync, barrier, device_ind
         s.step(warmup, case.cfl)
     if not strip_rows:
         rows = s.tune()      # strip height by measurement (fv_tune), outside the timed region
+    mix0 = order_mix(case, s.get_state())
     stream_sync()
     barrier()
     with ClockSampler(device_index) as clk:
         kernel_ms, total_ms = s.step_timed(steps, case.cfl)
     barrier()
     d = s.diag()
+    mix1 = order_mix(case, s.get_state())
     s.close()
     return {"kernel_ms": kernel_ms, "total_ms": total_ms, "status": d.status, "t": d.t,
-            "clocks": clk.summary(), "strip_rows": rows}
+            "clocks": clk.summary(), "strip_rows": rows,
+            "fluid_cells": mix0[0], "first_order_cells": 0.5 * (mix0[1] + mix1[1])}
+
+
+def cell_flops(ops, ops1, fluid, first_order):
+    """Algorithmic flops of one step: second-order cells at ops, the cells the
+    order switch advances at first order at ops1 (the mean of their counts at
+    the start and the end of the timed steps), solid cells none."""
+    return (fluid - first_order) * ops["flops"] + first_order * ops1["flops"]
 
 
 def measure_batch(fv, cases_mod, steps, warmup, stream_sync, barrier, cfl=0.45):
@@ -445,6 +463,10 @@ def measure_batch(fv, cases_mod, steps, warmup, stream_sync, barrier, cfl=0.45):
     total_ms = b.step_timed(steps, cfl)
     barrier()
     cells = sum(c.nx * c.ny for c in doms)
+    mix = [order_mix(c, c.q) for c in doms] + [order_mix(c, b.get_state(k))
+                                               for k, c in enumerate(doms)]
+    fluid = sum(m[0] for m in mix) // 2
+    first = 0.5 * sum(m[1] for m in mix)
     bad = sum(b.diag(k).status != 0 for k in range(len(doms)))
     t = [b.diag(k).t for k in range(len(doms))]
     b.close()
@@ -455,7 +477,8 @@ def measure_batch(fv, cases_mod, steps, warmup, stream_sync, barrier, cfl=0.45):
                       " of the strip kernel + per-domain finalize per step, CUDA graph of all "
                       "steps (form, strip height and order from fv_batch_tune)",
             "strip_rows": rows, "work_order": "longest strips first" if order else "by domain",
-            "bad_domains": int(bad), "t_min": min(t), "t_max": max(t)}
+            "bad_domains": int(bad), "t_min": min(t), "t_max": max(t),
+            "fluid_cells": fluid, "first_order_cells": first}
 
 
 def measure_e2e(fv, case, prec, steps):
@@ -618,13 +641,13 @@ def measure_e2e_per_step(fv, case, prec, steps):
             "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
 
 
-def path_summary(name, r, ops, pk, prof, cells, world=1):
+def path_summary(name, r, ops, ops1, pk, prof, cells, world=1):
     """Throughput, roofline (plain-ALU bound against the FMA peak measured in
     this run; DRAM traffic and warp instructions from the committed ncu record)
     and clocks of one precision's timed region."""
     tot, ker, steps = r["total_ms"], r["kernel_ms"], r["steps"]
     ms_step, kms = tot / steps, ker / steps
-    flops = ops["flops"] * cells
+    flops = cell_flops(ops, ops1, r["fluid_cells"], r["first_order_cells"])
     achieved = flops / (kms * 1e-3) / 1e12
     peak = pk["fp32_tflops"] if name == "f32" else pk["fp64_tflops"]
     bytes_alg = (33 if name == "f32" else 65) * cells
@@ -637,8 +660,12 @@ def path_summary(name, r, ops, pk, prof, cells, world=1):
                      "peak_source": ("FP32 FFMA/FFMA2" if name == "f32" else "FP64 DFMA") +
                                     " throughput measured in this run (of measured)",
                      "traffic": prof.get(name),
-                     "flops_per_cell": ops["flops"], "algorithmic_bytes_per_cell":
-                         33 if name == "f32" else 65,
+                     "flops_per_cell": flops / cells,
+                     "flops_per_cell_second_order": ops["flops"],
+                     "flops_per_cell_first_order": ops1["flops"],
+                     "first_order_fraction": r["first_order_cells"] / r["fluid_cells"],
+                     "solid_fraction": 1.0 - r["fluid_cells"] / cells,
+                     "algorithmic_bytes_per_cell": 33 if name == "f32" else 65,
                      "hbm_achieved_gbs": bytes_alg / (kms * 1e-3) / 1e9,
                      "hbm_frac": bytes_alg / (kms * 1e-3) / 1e9 / pk["hbm_gbs"],
                      "issue": issue_ceiling(prof.get(name + "_inst"), kms, sm_mhz)},
@@ -773,7 +800,7 @@ def run_ours(args):
         raise SystemExit("--grid applies to --only runs (profiling); the benchmark is 4096x2048")
     case = cases.c2(nx, ny)
     steps, warmup = max(1, args.steps), max(3, args.warmup)
-    ops = fv.fv_host_cell_ops()
+    ops, ops1 = fv.fv_host_cell_ops(), fv.fv_host_cell_ops(first_order=True)
     pk = measure_peaks(fv, local)
     prof = recorded_profile()
     cells = case.nx * case.ny
@@ -785,7 +812,7 @@ def run_ours(args):
         r = measure_path(fv, case, prec, steps, warmup, torch.cuda.synchronize, barrier, local,
                          args.strip_rows)
         r["steps"] = steps
-        line_paths[name] = path_summary(name, r, ops, pk, prof, cells)
+        line_paths[name] = path_summary(name, r, ops, ops1, pk, prof, cells)
     if args.only:
         r = line_paths[args.only]
         print(dumps_finite({"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1,
@@ -804,10 +831,14 @@ def run_ours(args):
     batch = None
     if not args.no_batch:
         batch = measure_batch(fv, cases, 500, warmup, torch.cuda.synchronize, barrier)
-        b_tf = ops["flops"] * batch["cells"] / (batch["ms_per_step"] * 1e-3) / 1e12
+        b_fl = cell_flops(ops, ops1, batch["fluid_cells"], batch["first_order_cells"])
+        b_tf = b_fl / (batch["ms_per_step"] * 1e-3) / 1e12
         batch["roofline"] = {"bound": "alu", "achieved": b_tf, "peak": pk["fp32_tflops"],
                              "unit": "TFLOP/s", "frac": b_tf / pk["fp32_tflops"],
-                             "flops_per_cell": ops["flops"], "timed": "whole ensemble step"}
+                             "flops_per_cell": b_fl / batch["cells"],
+                             "first_order_fraction": batch["first_order_cells"] /
+                                                     batch["fluid_cells"],
+                             "timed": "whole ensemble step"}
     adjoint = None
     if not args.no_adjoint:
         adjoint = adjoint_block(fv, cases, args.adjoint_steps, torch.cuda.synchronize)

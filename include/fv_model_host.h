@@ -62,6 +62,12 @@ int fv_host_yface_o1(const double* model, const double* fa, double aEa, const do
  * comparisons.  Returns 0, or 1 on a null pointer. */
 int fv_host_cell_ops(double* out);
 
+/* The same count for a cell that the order switch of Section 3.4 (alpha <=
+ * 10 eps) advances at first order: its reconstruction is its own fluctuation
+ * (the equilibrium products only); faces, interior integral, update and
+ * epilogue as above.  Returns 0, or 1 on a null pointer. */
+int fv_host_cell_ops_first_order(double* out);
+
 /* Forward value and reverse-mode derivative of one per-face or per-cell
  * function of the kernels (the building blocks of fv_adjoint), on the host.
  * which = 0: x face, in = qm[4], qp[4], out = D-[4], D+[4];

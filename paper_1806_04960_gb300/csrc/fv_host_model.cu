@@ -224,8 +224,10 @@ inline CD fmax(CD a, CD b) { ++g_ops.cmp; return CD(a.v > b.v ? a.v : b.v); }
 }  // namespace
 
 // out[0..4] = additions/subtractions, multiplications, divisions, square roots,
-// comparisons (min, max, abs, compare) of one cell-update.
-extern "C" int fv_host_cell_ops(double* out) {
+// comparisons (min, max, abs, compare) of one cell-update; first_order: a cell
+// that the order switch (alpha <= 10 eps) advances at first order, whose
+// reconstruction is its own fluctuation (the equilibrium products only).
+static int count_cell(bool first_order, double* out) {
   if (!out) return 1;
   using T = CD;
   fv::Phys<T> P;
@@ -248,9 +250,18 @@ extern "C" int fv_host_cell_ops(double* out) {
   // a generic liquid cell in motion with all four neighbours fluid
   const double q0[4] = {1003.0, 520.0, -130.0, 0.93};
   g_ops = Ops();
+  T fW[4], fE[4], fS[4], fN[4], base[4], ga[2];
+  const T aE = T(0.93), rEc = T(1001.0), rES = T(1001.2), rEN = T(1000.8);
+  const T mEc = aE * rEc, mES = aE * rES, mEN = aE * rEN;
+  if (first_order) {
+    const T Qf[4] = {T(1003.0) - mEc, T(520.0), T(-130.0), T(0.0)};
+    for (int v = 0; v < 4; ++v) fW[v] = fE[v] = fS[v] = fN[v] = base[v] = Qf[v];
+    ga[0] = ga[1] = T(0.0);
+  } else {
   // neighbour fluctuations (8 neighbours: one multiply-subtract each for m, one
   // subtraction for alpha) and the stencil min/max are part of the kernel body
-  T Qf[4] = {T(2.0), T(520.0), T(-130.0), T(0.0)};
+  // the cell's own fluctuation: m - alpha^E rho^E
+  T Qf[4] = {T(1003.0) - mEc, T(520.0), T(-130.0), T(0.0)};
   T nb[8][4];
   const double shift[8] = {-3.1, 4.2, -1.7, 2.5, 0.7, -0.9, 1.3, -2.2};
   for (int k = 0; k < 8; ++k) {
@@ -261,7 +272,7 @@ extern "C" int fv_host_cell_ops(double* out) {
     nb[k][2] = T(-130.0 + 7.0 * shift[k]);
     nb[k][3] = an - T(0.93);
   }
-  T fW[4], fE[4], fS[4], fN[4], mx[4], mn[4];
+  T mx[4], mn[4];
   for (int v = 0; v < 4; ++v) {
     fW[v] = nb[0][v];
     fE[v] = nb[1][v];
@@ -274,10 +285,8 @@ extern "C" int fv_host_cell_ops(double* out) {
       mn[v] = fmin(mn[v], nb[d][v]);
     }
   }
-  const T aE = T(0.93), rEc = T(1001.0), rES = T(1001.2), rEN = T(1000.8);
-  const T mEc = aE * rEc, mES = aE * rES, mEN = aE * rEN;
-  T base[4], ga[2];
   fv::recon_core(Qf, fW, fE, fS, fN, mx, mn, aE, mEc, mES, mEN, rEc, P, R, base, ga);
+  }
   // one x face and one y face per cell
   {
     const T qm[4] = {q0[0], q0[1], q0[2], q0[3]};
@@ -315,3 +324,7 @@ extern "C" int fv_host_cell_ops(double* out) {
   out[4] = (double)g_ops.cmp;
   return 0;
 }
+
+extern "C" int fv_host_cell_ops(double* out) { return count_cell(false, out); }
+
+extern "C" int fv_host_cell_ops_first_order(double* out) { return count_cell(true, out); }

@@ -210,6 +210,23 @@ __device__ __forceinline__ void recon_cell(const V4<T>* wS, const V4<T>* wC, con
   Qf[1] = wc.y;
   Qf[2] = wc.z;
   Qf[3] = T(0);
+  // The order switch of Section 3.4: a cell with alpha <= 10 eps is advanced
+  // at first order (no slopes, no predictor), so its four face states and its
+  // centre state at t^{n+1/2} are its own fluctuation whatever its
+  // neighbours: the stencil is not read (recon_core gives the same states,
+  // up to the sign of zero components, after evaluating it).
+  if (aE <= RC.ten_eps) {
+    rs = V4<T>{aE, mEc, aE * rES, aE * rEN};
+    const V4<T> q = pack(Qf);
+    rf[F_W] = q;
+    rf[F_E] = q;
+    rf[F_S] = q;
+    rf[F_N] = q;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) base[c] = Qf[c];
+    ga[0] = ga[1] = T(0);
+    return;
+  }
 
   auto wrow = [&](int dwj) -> const V4<T>* { return dwj < 0 ? wS : (dwj > 0 ? wN : wC); };
   auto frow = [&](int dwj) -> const unsigned char* { return dwj < 0 ? fS : (dwj > 0 ? fN : fC); };

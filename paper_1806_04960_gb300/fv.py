@@ -90,6 +90,8 @@ _lib.fv_host_xface.restype = C.c_int
 _lib.fv_host_xface_or.argtypes = [_D, _D, _D, _D, _D]
 _lib.fv_host_xface_or.restype = C.c_int
 _lib.fv_host_cell_ops.argtypes = [_D]
+_lib.fv_host_cell_ops_first_order.argtypes = [_D]
+_lib.fv_host_cell_ops_first_order.restype = C.c_int
 _lib.fv_step_static.argtypes = [C.POINTER(fv_grid), C.POINTER(fv_eos), C.POINTER(C.c_int32),
                                 C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, _D]
 _lib.fv_step_static.restype = C.c_int
@@ -161,7 +163,7 @@ _lib.fv_host_adj_check.restype = C.c_int
 ABI_SYMBOLS = ("fv_create", "fv_set_state", "fv_step", "fv_step_timed", "fv_get_state",
                "fv_get_levels",
                "fv_get_diag", "fv_destroy", "fv_last_error", "fv_version", "fv_host_xface",
-               "fv_host_yface", "fv_host_cell_ops", "fv_host_adj_check", "fv_step_static", "fv_batch_create",
+               "fv_host_yface", "fv_host_cell_ops", "fv_host_cell_ops_first_order", "fv_host_adj_check", "fv_step_static", "fv_batch_create",
                "fv_batch_set_state", "fv_batch_step", "fv_batch_step_timed", "fv_batch_get_state",
                "fv_batch_get_diag", "fv_batch_size", "fv_batch_destroy", "fv_adjoint",
                "fv_host_adjoint_step", "fv_set_order", "fv_host_yface_o1",
@@ -297,10 +299,12 @@ def fv_tune(h) -> int:
     return rows.value
 
 
-def fv_host_cell_ops() -> dict:
-    """Operation counts of one cell-update of the kernels (see fv_model_host.h)."""
+def fv_host_cell_ops(first_order: bool = False) -> dict:
+    """Operation counts of one cell-update of the kernels (see fv_model_host.h);
+    first_order: a cell that the order switch advances at first order."""
     out = np.zeros(5)
-    _check(_lib.fv_host_cell_ops(out.ctypes.data_as(_D)) and FV_EINVAL)
+    f = _lib.fv_host_cell_ops_first_order if first_order else _lib.fv_host_cell_ops
+    _check(f(out.ctypes.data_as(_D)) and FV_EINVAL)
     names = ("add", "mul", "div", "sqrt", "cmp")
     d = {k: int(v) for k, v in zip(names, out)}
     d["flops"] = d["add"] + d["mul"] + d["div"] + d["sqrt"]
