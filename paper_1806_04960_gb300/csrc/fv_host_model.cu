@@ -218,6 +218,7 @@ inline CD& operator-=(CD& a, CD b) { a = a - b; return a; }
 inline bool operator<(CD a, CD b) { ++g_ops.cmp; return a.v < b.v; }
 inline bool operator>(CD a, CD b) { ++g_ops.cmp; return a.v > b.v; }
 inline bool operator<=(CD a, CD b) { ++g_ops.cmp; return a.v <= b.v; }
+inline bool operator==(CD a, CD b) { ++g_ops.cmp; return a.v == b.v; }
 inline CD fmin(CD a, CD b) { ++g_ops.cmp; return CD(a.v < b.v ? a.v : b.v); }
 inline CD fmax(CD a, CD b) { ++g_ops.cmp; return CD(a.v > b.v ? a.v : b.v); }
 
@@ -299,9 +300,21 @@ static int count_cell(bool first_order, double* out) {
     const T dap = P.c2 * ((T(1000.1) - P.rho0) * T(0.0) + (dq[0] - P.rho0 * dq[3]));
     fv::yface_fx(qm, dq, fm, fp, dap, P, Dm, Dp);
   }
+  // the momentum fluxes of the four face states, once per cell (a first-order
+  // cell's W and E states are the same), then the interior integral
+  T xW[2], xE[2], yS[2], yN[2];
+  fv::xflux(mEc + fW[0], fW[1], fW[2], xW);
+  if (first_order) {
+    xE[0] = xW[0];
+    xE[1] = xW[1];
+  } else {
+    fv::xflux(mEc + fE[0], fE[1], fE[2], xE);
+  }
+  fv::yflux(mES + fS[0], fS[1], fS[2], yS);
+  fv::yflux(mEN + fN[0], fN[1], fN[2], yN);
   T Ix[4], Iy[4];
-  fv::interior_terms(fW, fE, fS, fN, base, mEc, mES, mEN, ga[0], ga[1], T(1.0 / 32), T(1.0 / 32), P,
-                     Ix, Iy);
+  fv::interior_terms_fx(fW, fE, fS, fN, base, mEc, xW, xE, yS, yN, ga[0], ga[1], T(1.0 / 32),
+                        T(1.0 / 32), P, Ix, Iy);
   // update: Q^{n+1} = Q^n - dt/dx (D+_W + D-_E + I_x) - dt/dy (D+_S + D-_N + I_y)
   const T rdx = T(1e-4) / T(1.0 / 32), rdy = T(1e-4) / T(1.0 / 32);
   T qn[4];

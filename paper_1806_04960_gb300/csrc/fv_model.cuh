@@ -597,16 +597,23 @@ __host__ __device__ __forceinline__ void interior_terms_fx(const T fW[4], const 
                                                            const T yN[2], T dax, T day, T dx,
                                                            T dy, const Phys<T>& P, T Ix[4],
                                                            T Iy[4]) {
-  const Vel<T> vc = velocity(mEc + base[0], base[1], base[2]);
   Ix[0] = fE[1] - fW[1];
   Ix[1] = (xE[0] - xW[0]) + P.c2 * ((fE[0] - fW[0]) - P.rho0 * (fE[3] - fW[3]));
   Ix[2] = xE[1] - xW[1];
-  Ix[3] = dx * vc.u * dax;
   Iy[0] = fN[2] - fS[2];
   Iy[1] = yN[0] - yS[0];
   Iy[2] = (yN[1] - yS[1]) + P.c2 * ((fN[0] - fS[0]) - P.rho0 * (fN[3] - fS[3])) +
           P.g * dy * base[0];
-  Iy[3] = dy * vc.v * day;
+  // the non-conservative alpha transport u d(alpha)/dx, v d(alpha)/dy: zero
+  // where alpha is uniform (both limited slopes zero: every cell away from
+  // the interface), without the centre velocity
+  if (dax == T(0) && day == T(0)) {
+    Ix[3] = Iy[3] = T(0);
+  } else {
+    const Vel<T> vc = velocity(mEc + base[0], base[1], base[2]);
+    Ix[3] = dx * vc.u * dax;
+    Iy[3] = dy * vc.v * day;
+  }
 }
 
 template <typename T>

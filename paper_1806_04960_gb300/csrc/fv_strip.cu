@@ -140,7 +140,8 @@ __device__ __forceinline__ void strip_body(const StepParams& p, const KConsts<T>
       S.rs[s][rx] = rs;
 #pragma unroll
       for (int f = 0; f < 4; ++f) S.rf[f][s][rx] = rf[f];
-      if constexpr (FLX) face_fluxes(rs, rf, S.fl[0][s][rx], S.fl[1][s][rx]);
+      if constexpr (FLX)
+        face_fluxes(rs, rf, rs.x <= RC.ten_eps, S.fl[0][s][rx], S.fl[1][s][rx]);
       if (rx >= 1 && rx <= SX) {
         S.base[s][rx - 1] = pack(base);
         S.ga[0][s][rx - 1] = ga[0];

@@ -329,13 +329,19 @@ __device__ __forceinline__ void recon_cell(const V4<T>* wS, const V4<T>* wC, con
 // Face-flux records of a reconstructed cell (rs, rf as recon_cell writes
 // them): xf = the x fluxes of its W and E face states, yf = the y fluxes of
 // its S and N ones (xflux, yflux), formed once for the cell's two x faces,
-// two y faces and interior integral.
+// two y faces and interior integral.  first: the cell is advanced at first
+// order (recon_cell's order switch), so its W and E states are the same.
 template <typename T>
-__device__ __forceinline__ void face_fluxes(const V4<T>& rs, const V4<T> rf[4], V4<T>& xf,
-                                            V4<T>& yf) {
+__device__ __forceinline__ void face_fluxes(const V4<T>& rs, const V4<T> rf[4], bool first,
+                                            V4<T>& xf, V4<T>& yf) {
   T a[2], b[2], c[2], d[2];
   xflux(rs.y + rf[F_W].x, rf[F_W].y, rf[F_W].z, a);
-  xflux(rs.y + rf[F_E].x, rf[F_E].y, rf[F_E].z, b);
+  if (first) {
+    b[0] = a[0];
+    b[1] = a[1];
+  } else {
+    xflux(rs.y + rf[F_E].x, rf[F_E].y, rf[F_E].z, b);
+  }
   yflux(rs.z + rf[F_S].x, rf[F_S].y, rf[F_S].z, c);
   yflux(rs.w + rf[F_N].x, rf[F_N].y, rf[F_N].z, d);
   xf = V4<T>{a[0], a[1], b[0], b[1]};
