@@ -112,6 +112,7 @@ struct CellRec {
   T aE, rEc, rES, rEN, mEc, mES, mEN;
   T fo[4][4];       // face states W, E, S, N at t^{n+1/2}
   T base[4], ga[2];
+  bool first;       // alpha <= 10 eps: advanced at first order (the stencil is not read)
 };
 
 // Same loads, fluctuations, ghosts, extrema and reconstruction as the step kernel.
@@ -132,6 +133,23 @@ __host__ __device__ __forceinline__ void recon_cell(const AdjArgs<T>& A, int i, 
   C.Qf[1] = A.q[N + c];
   C.Qf[2] = A.q[2 * N + c];
   C.Qf[3] = T(0);
+  // the order switch, as the step kernels take it: face and centre states are
+  // the cell's own fluctuation and depend on no neighbour
+  C.first = aE <= A.kc.R.ten_eps;
+  if (C.first) {
+    C.mES = aE * C.rES;
+    C.mEN = aE * C.rEN;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      C.nfl[k] = C.dfl[k] = C.ncopy[k] = false;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) C.fo[k][v] = C.Qf[v];
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) C.base[v] = C.Qf[v];
+    C.ga[0] = C.ga[1] = T(0);
+    return;
+  }
   auto nbf = [&](int di, int dj, T out[4], T& rn) -> bool {
     const int ni = i + di, nj = j + dj;
     rn = T(0);
@@ -435,39 +453,45 @@ __host__ __device__ void cell_body(const AdjArgs<T>& A, int i, int j) {
   for (int k = 0; k < 4; ++k)
 #pragma unroll
     for (int v = 0; v < 4; ++v) lfi[k][v] = T(0);
-  recon_core_adj(C.Qf, C.fi[0], C.fi[1], C.fi[2], C.fi[3], C.mx, C.mn, C.aE, C.mEc, C.mES, C.mEN,
-                 C.rEc, P, A.kc.R, lfo[0], lfo[1], lfo[2], lfo[3], lbase, lga, lQf, lfi[0], lfi[1],
-                 lfi[2], lfi[3], lmx, lmn, laE, lmEc);
-  // stencil extrema: to the first candidate attaining them, in the forward's order
   T lfd[4][4];
 #pragma unroll
   for (int d = 0; d < 4; ++d)
 #pragma unroll
     for (int v = 0; v < 4; ++v) lfd[d][v] = T(0);
+  if (C.first) {
+    // face and centre states = Qf (Qf[3] = 0 is a constant)
 #pragma unroll
-  for (int v = 0; v < 4; ++v) {
-#pragma unroll
-    for (int pass = 0; pass < 2; ++pass) {
-      const T target = pass == 0 ? C.mx[v] : C.mn[v];
-      const T l = pass == 0 ? lmx[v] : lmn[v];
-      if (C.Qf[v] == target) { lQf[v] += l; continue; }
-      bool done = false;
-#pragma unroll
-      for (int k = 0; k < 4; ++k)
-        if (!done && C.fi[k][v] == target) { lfi[k][v] += l; done = true; }
-#pragma unroll
-      for (int d = 0; d < 4; ++d)
-        if (!done && C.dfl[d] && C.fd[d][v] == target) { lfd[d][v] += l; done = true; }
+    for (int v = 0; v < 3; ++v) lQf[v] = lbase[v] + lfo[0][v] + lfo[1][v] + lfo[2][v] + lfo[3][v];
+  } else {
+    recon_core_adj(C.Qf, C.fi[0], C.fi[1], C.fi[2], C.fi[3], C.mx, C.mn, C.aE, C.mEc, C.mES, C.mEN,
+                   C.rEc, P, A.kc.R, lfo[0], lfo[1], lfo[2], lfo[3], lbase, lga, lQf, lfi[0], lfi[1],
+                   lfi[2], lfi[3], lmx, lmn, laE, lmEc);
+    // stencil extrema: to the first candidate attaining them, in the forward's order
+  #pragma unroll
+    for (int v = 0; v < 4; ++v) {
+  #pragma unroll
+      for (int pass = 0; pass < 2; ++pass) {
+        const T target = pass == 0 ? C.mx[v] : C.mn[v];
+        const T l = pass == 0 ? lmx[v] : lmn[v];
+        if (C.Qf[v] == target) { lQf[v] += l; continue; }
+        bool done = false;
+  #pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (!done && C.fi[k][v] == target) { lfi[k][v] += l; done = true; }
+  #pragma unroll
+        for (int d = 0; d < 4; ++d)
+          if (!done && C.dfl[d] && C.fd[d][v] == target) { lfd[d][v] += l; done = true; }
+      }
     }
+    // ghosts are (mirrored) copies of Qf; Qf[3] = 0 is a constant
+  #pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (!C.nfl[k]) {
+        lQf[0] += lfi[k][0];
+        lQf[1] += (k < 2 && !C.ncopy[k]) ? -lfi[k][1] : lfi[k][1];
+        lQf[2] += (k >= 2 && !C.ncopy[k]) ? -lfi[k][2] : lfi[k][2];
+      }
   }
-  // ghosts are (mirrored) copies of Qf; Qf[3] = 0 is a constant
-#pragma unroll
-  for (int k = 0; k < 4; ++k)
-    if (!C.nfl[k]) {
-      lQf[0] += lfi[k][0];
-      lQf[1] += (k < 2 && !C.ncopy[k]) ? -lfi[k][1] : lfi[k][1];
-      lQf[2] += (k >= 2 && !C.ncopy[k]) ? -lfi[k][2] : lfi[k][2];
-    }
   // to the state: Qf = (m - aE rEc, mu, mv, 0); neighbour fluctuations
   // (m_n - aE rn, mu_n, mv_n, a_n - aE); equilibrium masses aE rE
   laE += C.rEc * lmEc + C.rES * lmES + C.rEN * lmEN - C.rEc * lQf[0];
