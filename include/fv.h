@@ -397,8 +397,7 @@ fv_status fv_part_unpack(fv_handle* h, int32_t side, const void* buf_dev);
  *     value (as fv_set_state), else FV_ENONFINITE if q_out is not admissible.
  *     Without dt_out the call is asynchronous and neither state is checked.
  * Calls no allocating routine.  The first call on a device looks up the
- * array's device address with that device current; make that first call
- * before any stream capture.  The equilibrium table in the array is copied
+ * array's device address with that device current.  The equilibrium table in the array is copied
  * from a host buffer when ny, dy, rho0 or the gravity constant differ from the
  * previous call's on that device.  Every call reuses the same array, which keeps
  * the previous call's contents (the accumulators are cleared at the start of
