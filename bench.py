@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-drop", action="store_true")
+    ap.add_argument("--no-full-run", action="store_true",
+                    help="skip the 1000-step run of the configured throughput workload")
     ap.add_argument("--only", choices=("f32", "f64"), default=None,
                     help="time one path only (profiling runs)")
     ap.add_argument("--workload", choices=("dambreak", "drop", "adjoint", "impact", "weir"),
@@ -230,6 +232,21 @@ def issue_ceiling(warp_inst, kernel_ms, sm_mhz, sms=152):
     min_ms = warp_inst / (sms * 4 * sm_mhz * 1e6) * 1e3
     return {"warp_inst_per_launch": warp_inst, "sm_mhz": sm_mhz, "min_ms": min_ms,
             "frac": min_ms / kernel_ms}
+
+
+def fp64_pipe(fp64_inst, kernel_ms, dfma_tflops):
+    """Occupancy of the FP64 pipe over a launch: the launch's FP64-pipe warp
+    instructions (ncu record) per second against the pipe's measured rate, one
+    warp instruction per 32 lanes x 2 flops of the DFMA peak.  Adds and
+    multiplies take a pipe slot as an FMA does, so this is the fraction that
+    bounds the FP64 kernel; the flop fraction counts them as half a slot."""
+    if not fp64_inst or not dfma_tflops:
+        return None
+    peak = dfma_tflops * 1e12 / 64.0
+    achieved = fp64_inst / (kernel_ms * 1e-3)
+    return {"fp64_warp_inst_per_launch": fp64_inst, "achieved_per_s": achieved,
+            "peak_per_s": peak, "frac": achieved / peak,
+            "peak_source": "the DFMA peak measured in this run"}
 
 
 # --------------------------------------------------------------------------- CPU oracle
@@ -432,6 +449,38 @@ def measure_path(fv, case, prec, steps, warmup, stream_sync, barrier, device_ind
     return {"kernel_ms": kernel_ms, "total_ms": total_ms, "status": d.status, "t": d.t,
             "clocks": clk.summary(), "strip_rows": rows,
             "fluid_cells": mix0[0], "first_order_cells": 0.5 * (mix0[1] + mix1[1])}
+
+
+def config2_full_run(fv, case, ops, ops1, steps=1000, every=100):
+    """The configured throughput workload end to end: 4096 x 2048 from the
+    initial state for 1000 steps in each precision, device time of every
+    100-step chunk (step_timed, CUDA events on the launching stream) and the
+    share of fluid cells at first order (order switch) after each chunk, so
+    that the rate of the short timed window can be set beside the rate of the
+    whole configured run."""
+    out = {"workload": case.name, "steps": steps, "cfl": case.cfl}
+    for name, prec in (("f64", fv.FV_FP64), ("f32", fv.FV_FP32_DEV)):
+        s = fv.Solver(case, prec)
+        s.set_state(case.q)
+        s.tune()
+        s.set_state(case.q)
+        ms, chunks, fo, flops = 0.0, [], [], 0.0
+        mix = order_mix(case, case.q)
+        for _ in range(steps // every):
+            _, tot = s.step_timed(every, case.cfl)
+            ms += tot
+            mix1 = order_mix(case, s.get_state())
+            flops += every * cell_flops(ops, ops1, mix[0], 0.5 * (mix[1] + mix1[1]))
+            mix = mix1
+            chunks.append(round(case.nx * case.ny * every / (tot * 1e-3) / 1e6, 1))
+            fo.append(round(mix1[1] / mix1[0], 4))
+        d = s.diag()
+        s.close()
+        out[name] = {"value": case.nx * case.ny * steps / (ms * 1e-3) / 1e6, "unit": UNIT,
+                     "device_s": ms * 1e-3, "t_end": d.t, "status": d.status,
+                     "mcups_per_100_steps": chunks, "first_order_fraction_per_100_steps": fo,
+                     "achieved_tflops": flops / (ms * 1e-3) / 1e12}
+    return out
 
 
 def cell_flops(ops, ops1, fluid, first_order):
@@ -668,7 +717,9 @@ def path_summary(name, r, ops, ops1, pk, prof, cells, world=1):
                      "algorithmic_bytes_per_cell": 33 if name == "f32" else 65,
                      "hbm_achieved_gbs": bytes_alg / (kms * 1e-3) / 1e9,
                      "hbm_frac": bytes_alg / (kms * 1e-3) / 1e9 / pk["hbm_gbs"],
-                     "issue": issue_ceiling(prof.get(name + "_inst"), kms, sm_mhz)},
+                     "issue": issue_ceiling(prof.get(name + "_inst"), kms, sm_mhz),
+                     "fp64_pipe": fp64_pipe(prof.get(name + "_fp64inst"), kms, pk["fp64_tflops"])
+                     if name == "f64" else None},
         "status": r["status"], "clocks": r["clocks"], "strip_rows": r["strip_rows"]}
 
 
@@ -843,6 +894,7 @@ def run_ours(args):
     if not args.no_adjoint:
         adjoint = adjoint_block(fv, cases, args.adjoint_steps, torch.cuda.synchronize)
     drop = None if args.no_drop else drop_block(fv, cases)
+    full = None if args.no_full_run else config2_full_run(fv, case, ops, ops1)
     cpu = err = c1err = None
     if not args.no_cpu_baseline:
         try:
@@ -880,6 +932,7 @@ def run_ours(args):
         "batch": batch,
         "adjoint": adjoint,
         "drop": drop,
+        "config2_full_run": full,
         "status": {"f64": f64["status"], "f32": f32["status"]},
     }
     print(dumps_finite(line), flush=True)
