@@ -79,3 +79,20 @@ def test_host_face_null_pointer_is_einval(fvmod):
     lib = ctypes.CDLL(fvmod.LIB_PATH)
     lib.fv_host_xface.restype = ctypes.c_int
     assert lib.fv_host_xface(None, None, None, None, None) == 1
+
+
+def test_cell_operation_counts(fvmod):
+    """The algorithmic counts of one cell-update that the benchmark's roofline
+    uses: a first-order cell (the order switch) needs a strict subset of a
+    second-order cell's work (no slopes, limiter or predictor), and with gamma
+    = 1 (c constant) neither takes a square root."""
+    so = fvmod.fv_host_cell_ops()
+    fo = fvmod.fv_host_cell_ops(first_order=True)
+    assert so["sqrt"] == 0 and fo["sqrt"] == 0
+    assert 0 < fo["flops"] < so["flops"]
+    for k in ("add", "mul", "div", "cmp"):
+        assert 0 < fo[k] < so[k], k
+    assert so["flops"] == so["add"] + so["mul"] + so["div"] + so["sqrt"]
+    lib = ctypes.CDLL(fvmod.LIB_PATH)
+    lib.fv_host_cell_ops_first_order.restype = ctypes.c_int
+    assert lib.fv_host_cell_ops_first_order(None) == 1
