@@ -717,3 +717,43 @@ def test_weir_readings_record():
     assert rec[(800, "bj_printed")][0] > 1.05 * t0
     # at 400 x 125 the default fails at t = 0.375, alpha^E = 1 already at t = 0.085
     assert rec[(400, "default")][1] == 1 and rec[(400, "aE_one")][0] < 0.1
+
+
+def test_order_switch_reconstruction_ignores_the_stencil():
+    """Section 3.4's switch to first order for alpha <= 10 eps (reading R-sw):
+    such a cell's face and centre states at t^{n+1/2} are its own fluctuation on
+    the water-at-rest state of each point (no slopes, no predictor), so changing
+    its eight neighbours changes none of them, and its W and E states are its
+    cell average.  A cell just above the threshold does see its neighbours
+    (slopes and predictor), so the check is not vacuous.  The GPU kernels
+    skip the stencil of such cells on this basis."""
+    c = cases.c1()
+    rng = np.random.default_rng(39)
+    i, j = 60, 40            # gas (alpha = eps), fluid neighbours all round
+
+    def perturbed_neighbours(q):
+        q1 = q.copy()
+        for dj in (-1, 0, 1):
+            for di in (-1, 0, 1):
+                if di or dj:
+                    q1[0, j + dj, i + di] *= 1.0 + 0.05 * rng.uniform(-1, 1)
+                    q1[1, j + dj, i + di] += 0.3 * rng.uniform(-1, 1)
+                    q1[2, j + dj, i + di] += 0.3 * rng.uniform(-1, 1)
+                    q1[3, j + dj, i + di] *= 1.0 + 0.5 * rng.uniform(0, 1)
+        return q1
+
+    keys = ("qW", "qE", "fS", "fN", "qc")
+    for alpha, first_order in ((c.eps, True), (10.0 * c.eps, True), (11.0 * c.eps, False)):
+        q = c.q.copy()
+        q[0, j, i] *= alpha / q[3, j, i]
+        q[3, j, i] = alpha
+        q[1, j, i], q[2, j, i] = 0.2, -0.1
+        r0 = O.cell_rec(c, q, i, j)
+        r1 = O.cell_rec(c, perturbed_neighbours(q), i, j)
+        same = all(np.array_equal(r0[k], r1[k]) for k in keys)
+        assert same == first_order, alpha
+        if first_order:
+            assert r0["dax"] == 0.0 and r0["day"] == 0.0
+            assert np.array_equal(r0["qW"], r0["qE"])
+            assert np.allclose(r0["qW"], q[:, j, i], rtol=1e-14, atol=0.0)
+            assert np.allclose(r0["qc"], q[:, j, i], rtol=1e-14, atol=0.0)
