@@ -420,7 +420,8 @@ fv_status fv_step_static(const fv_grid* grid, const fv_eos* eos, const int32_t s
 fv_status fv_measure_fma_peak(int32_t kind, int32_t reps, double* tflops, double* best_ms);
 
 /* The double-precision reciprocal the FP64 device code uses (the hardware
- * approximation refined by two Newton steps), evaluated at n device doubles
+ * approximation r refined by the series r (1 + e + e^2), e = 1 - x r),
+ * evaluated at n device doubles
  * x_dev into out_dev on cuda_stream (asynchronous), so that it can be checked
  * against IEEE division; the paper has no counterpart. */
 fv_status fv_device_rcp(const double* x_dev, double* out_dev, int64_t n, void* cuda_stream);

@@ -119,21 +119,21 @@ template <typename T>
 __host__ __device__ __forceinline__ T rcp(T x) {
   return T(1) / x;
 }
-// Double on the device: the hardware's approximate reciprocal (rcp.approx.f64)
-// refined by two steps of Newton's iteration for 1/x, r <- r + r (1 - x r)
-// (each squares the relative error; the last one rounds once through the
-// fused multiply-add), within one ulp of 1/x (tests/test_gpu_parity.py checks
-// it against CUDA's division); fewer FP64-pipe instructions than IEEE
-// division, whose pipe bounds the FP64 step.
+// Double on the device: the hardware's approximate reciprocal r
+// (rcp.approx.f64) refined by the series 1/x = r / (1 - e) = r (1 + e + e^2 +
+// ...) with e = 1 - x r, truncated after e^2 (relative error e^3, below the
+// last rounding for the approximation's |e|), rounded once by the last fused
+// multiply-add: within one ulp of 1/x (tests/test_gpu_parity.py checks it
+// against CUDA's division) in three FP64-pipe instructions, where two steps
+// of Newton's iteration take four and IEEE division more; that pipe bounds
+// the FP64 step.
 template <>
 __host__ __device__ __forceinline__ double rcp<double>(double x) {
 #ifdef __CUDA_ARCH__
   double r;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-  double e = fma(-x, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-x, r, 1.0);
-  return fma(r, e, r);
+  const double e = fma(-x, r, 1.0);
+  return fma(r, fma(e, e, e), r);
 #else
   return 1.0 / x;
 #endif
