@@ -411,8 +411,11 @@ __host__ __device__ void face_body(const AdjArgs<T>& A, long long idx) {
   }
 }
 
+// Double: at most 128 registers, so that two CTAs fit per SM (its subsonic and
+// general branches of the reverse face solvers together take up to 140 when
+// the compiler is left free).  Float takes 64 unbounded (four CTAs).
 template <typename T>
-__global__ void __launch_bounds__(256) adj_face_kernel(AdjArgs<T> A) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 0 : 2) adj_face_kernel(AdjArgs<T> A) {
   const long long nf = (long long)(A.nx + 1) * A.ny + (long long)A.nx * (A.ny + 1);
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx < nf) face_body<T>(A, idx);

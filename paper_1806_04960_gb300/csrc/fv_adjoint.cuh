@@ -69,6 +69,48 @@ __host__ __device__ __forceinline__ void xface_adj(const T qm[4], const T qp[4],
     const T mu = qm[1] + s_gl[k] * dq[1];
     const T mv = qm[2] + s_gl[k] * dq[2];
     const Vel<T> w = velocity(m, mu, mv);
+    const T g0 = w_gl[k] * lV[0], g1 = w_gl[k] * lV[1], g2 = w_gl[k] * lV[2], g3 = w_gl[k] * lV[3];
+    if (sizeof(T) == 8 && abs_lt(w.u, P.c)) {
+      // FP64 (its pipe bounds the reverse face kernel; the float kernel, bound
+      // by its registers, keeps the general form): the subsonic closed form of
+      // xface_scalar: e = d2 - u d1, Pk = c dr + (u / c) e,
+      // a5 - a1 = e + u dr, r0 = Pk + |u| rho0 d4
+      const T sua = sgn_frozen(w.u), la = sua * w.u;
+      const T e = dq[1] - w.u * dq[0];
+      const T Pk = P.c * dr + (w.u * P.inv_c) * e;
+      const T r0 = Pk + la * P.rho0 * dq[3];
+      const T w2 = dq[2] - w.v * dr;
+      // V0 += w r0; V1 += w (u r0 + c (e + u dr)); V2 += w (v Pk + la w2); V3 += w la dq3
+      const T lr0 = g0 + g1 * w.u;
+      T lu = g1 * r0 + w_gl[k] * lubar;
+      const T lamd = g1 * P.c;
+      T lv = g2 * Pk;
+      const T lPk = lr0 + g2 * w.v;
+      const T lla = lr0 * P.rho0 * dq[3] + g2 * w2 + g3 * dq[3];
+      ldq[3] += lr0 * la * P.rho0 + g3 * la;
+      const T lw2 = g2 * la;
+      // a5 - a1 = e + u dr and Pk = c dr + (u / c) e
+      const T le = lamd + lPk * w.u * P.inv_c;
+      lu += lamd * dr + lPk * P.inv_c * e;
+      ldr += lamd * w.u + lPk * P.c;
+      // e = d2 - u d1; w2 = d3 - v dr; la = |u|
+      ldq[1] += le;
+      lu -= le * dq[0];
+      ldq[0] -= le * w.u;
+      ldq[2] += lw2;
+      lv -= lw2 * dr;
+      ldr -= lw2 * w.v;
+      lu += lla * sua;
+      T lm = 0, lmu = 0, lmv = 0;
+      velocity_adj(m, mu, mv, lu, lv, lm, lmu, lmv);
+      lqm[0] += lm;
+      lqm[1] += lmu;
+      lqm[2] += lmv;
+      ldq[0] += s_gl[k] * lm;
+      ldq[1] += s_gl[k] * lmu;
+      ldq[2] += s_gl[k] * lmv;
+      continue;
+    }
     const T uc = w.u * P.inv_c;
     const T w1 = T(0.5) * ((T(1) + uc) * dq[0] - dq[1] * P.inv_c - P.rho0 * dq[3]);
     const T w5 = T(0.5) * ((T(1) - uc) * dq[0] + dq[1] * P.inv_c - P.rho0 * dq[3]);
@@ -79,7 +121,6 @@ __host__ __device__ __forceinline__ void xface_adj(const T qm[4], const T qp[4],
     const T Pk = a1 + a5;
     const T r0 = Pk + la * P.rho0 * dq[3];
     // V0 += w r0; V1 += w (u r0 + c (a5 - a1)); V2 += w (v Pk + la w2); V3 += w la dq3
-    const T g0 = w_gl[k] * lV[0], g1 = w_gl[k] * lV[1], g2 = w_gl[k] * lV[2], g3 = w_gl[k] * lV[3];
     T lu = g1 * r0 + w_gl[k] * lubar;
     T lv = g2 * Pk;
     const T lr0 = g0 + g1 * w.u;
@@ -121,6 +162,30 @@ __host__ __device__ __forceinline__ void xface_adj(const T qm[4], const T qp[4],
 template <typename T>
 __host__ __device__ __forceinline__ void sign_A2_adj(T u, T v, const T r[4], const Phys<T>& P,
                                                      const T lo[4], T& lu, T& lv, T lr[4]) {
+  if (sizeof(T) == 8 && abs_lt(v, P.c)) {
+    // FP64, as in xface_adj: the subsonic closed form of sign_A2: rr = rho0 r3, D = r0 - rr,
+    // Pk = (r2 - v r0) / c, o0 = Pk + s3 rr; out = (o0, u Pk + s3 (r1 - u D),
+    // v o0 + c D, s3 r3)
+    const T s3 = sgn_frozen(v);
+    const T rr = P.rho0 * r[3], D = r[0] - rr;
+    const T Pk = (r[2] - v * r[0]) * P.inv_c;
+    const T o0 = Pk + s3 * rr;
+    const T lo0 = lo[0] + lo[2] * v;
+    T lD = lo[2] * P.c;
+    lv += lo[2] * o0;
+    lu += lo[1] * Pk;
+    const T lt = lo[1] * s3;
+    lr[1] += lt;
+    lu -= lt * D;
+    lD -= lt * u;
+    const T lPk = lo[1] * u + lo0;
+    const T lrr = lo0 * s3 - lD;
+    lr[3] += lo[3] * s3 + lrr * P.rho0;
+    lr[2] += lPk * P.inv_c;
+    lv -= lPk * P.inv_c * r[0];
+    lr[0] += lD - lPk * P.inv_c * v;
+    return;
+  }
   const T vc = v * P.inv_c;
   const T w1 = T(0.5) * ((T(1) + vc) * r[0] - r[2] * P.inv_c - P.rho0 * r[3]);
   const T w5 = T(0.5) * ((T(1) - vc) * r[0] + r[2] * P.inv_c - P.rho0 * r[3]);

@@ -47,11 +47,31 @@ def face_state(rng):
     return q
 
 
+def supersonic_pair(rng):
+    """Two face states whose velocities are both supersonic in x and in y
+    (1.3 c .. 2 c, one sign per direction), so every path node is too: the
+    general branch of |A1| and sign(A2) rather than their subsonic closed
+    forms."""
+    c = math.sqrt(MODEL[1] / MODEL[0])
+    sx, sy = rng.choice([-1.0, 1.0], 2)
+    out = []
+    for _ in range(2):
+        m = rng.uniform(300, 1100)
+        q = np.array([m, sx * m * c * rng.uniform(1.3, 2.0), sy * m * c * rng.uniform(1.3, 2.0),
+                      m / rng.uniform(900, 1100)])
+        out.append(q)
+    return np.concatenate(out)
+
+
+@pytest.mark.parametrize("speed", ["subsonic", "supersonic"])
 @pytest.mark.parametrize("which", [0, 1])
-def test_face_adjoints_match_central_differences(which):
-    rng = np.random.default_rng(100 + which)
+def test_face_adjoints_match_central_differences(which, speed):
+    rng = np.random.default_rng(100 + which + (10 if speed == "supersonic" else 0))
     for _ in range(6):
-        x = np.concatenate([face_state(rng), face_state(rng)])
+        if speed == "subsonic":
+            x = np.concatenate([face_state(rng), face_state(rng)])
+        else:
+            x = supersonic_pair(rng)
         lout = rng.normal(size=8)
         _, lin = fv.fv_host_adj_check(which, MODEL, None, x, lout)
         g = central_fd(which, None, x, lout, 1e-6, np.ones(8))
