@@ -629,15 +629,24 @@ def conditioned_gradient(fv, cases_mod, nsteps=200, ndirs=32, h=1e-11):
     out = {"workload": "adjoint_dambreak_512x256_generic", "steps": nsteps, "cfl": c.cfl,
            "directions": ndirs, "fd_step_rel": h, "fd_seconds": fd_s,
            "reference": "central differences of the FP64 frozen-branch map (fv_step_frozen)"}
+    grads = {}
     for name, prec in (("f64", fv.FV_FP64), ("f32", fv.FV_FP32_DEV)):
         s = fv.Solver(c, prec)
         s.set_state(c.q)
         grad, info, _ = s.adjoint(nsteps, g, target, cfl=c.cfl)
         s.close()
+        grads[name] = np.asarray(grad)
         dd = np.array([float(np.sum(grad * d)) for d in dirs])
         err = np.abs(dd - fd) / np.max(np.abs(fd))
         out[name] = {"max_rel_err": float(err.max()), "median_rel_err": float(np.median(err)),
                      "loss": info.loss, "finite": bool(np.isfinite(grad).all())}
+    # where the FP32 gradient departs from the FP64 one: per field, the largest
+    # difference over the fluid cells relative to that field's largest value
+    fl = c.solid == 0
+    out["f32_vs_f64_by_field"] = {
+        k: float(np.abs(grads["f32"][v][fl] - grads["f64"][v][fl]).max()
+                 / np.abs(grads["f64"][v][fl]).max())
+        for v, k in enumerate(("alpha rho", "alpha rho u", "alpha rho v", "alpha"))}
     return out
 
 
