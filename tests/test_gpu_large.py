@@ -16,11 +16,22 @@ pytestmark = pytest.mark.gpu
 NX, NY = 32768, 16448
 
 
+HOST_BYTES = 80 * 2 ** 30      # the case, two states and the generator's temporaries
+DEVICE_BYTES = 60 * 2 ** 30    # the FP32 handle's state, staging and scratch, or the FP64 one's
+
+
 @pytest.fixture(scope="module")
 def fv():
+    import os
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
+    avail = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+    if avail < HOST_BYTES:
+        pytest.skip(f"needs {HOST_BYTES >> 30} GiB of free host memory, {avail >> 30} available")
+    free, _ = torch.cuda.mem_get_info()
+    if free < DEVICE_BYTES:
+        pytest.skip(f"needs {DEVICE_BYTES >> 30} GiB of free device memory, {free >> 30} available")
     from paper_1806_04960_gb300 import build
     build.build()
     from paper_1806_04960_gb300 import fv as mod
